@@ -1,0 +1,83 @@
+"""The seeded input generator: determinism and the structure the recipes promise."""
+import numpy as np
+
+from paper_2208_14567_gb300 import inputs as I
+
+
+def test_stream_is_counter_addressed():
+    s = I.Stream(7, 3)
+    a = s.u64(np.arange(100))
+    b = s.u64(np.arange(50, 100))
+    assert np.array_equal(a[50:], b)
+    assert not np.array_equal(I.Stream(7, 4).u64(np.arange(10)), a[:10])
+    u = s.uniform(np.arange(100000))
+    assert u.min() >= 0.0 and u.max() < 1.0 and abs(u.mean() - 0.5) < 0.01
+
+
+def test_splitmix64_reference_value():
+    # splitmix64 with state 0: first output of the published generator (Vigna).
+    z = I._mix(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))
+    assert int(z[0]) == 0xE220A8397B1DCDAF
+
+
+def test_dyad_batch_structure():
+    b = I.dyad_batch(4000, 6, 8, seed=0)
+    assert b.adj.dtype == np.uint8 and b.jtype.dtype == np.int8 and b.pos.dtype == np.float32
+    assert np.array_equal(b.adj, b.adj.transpose(0, 2, 1))
+    assert not b.adj[:, np.arange(8), np.arange(8)].any()
+    assert set(np.unique(b.n_joints)) == {6, 7, 8}
+    nfix = (b.jtype == 0).sum(1)
+    assert nfix.min() >= 2 and nfix.max() <= 3
+    assert ((b.jtype == 2).sum(1) == 1).all()
+    # every simple joint has exactly two links to lower-index joints (sequential dyad addition)
+    for m in range(200):
+        for k in range(3, b.n_joints[m]):
+            if b.jtype[m, k] == 1:
+                assert b.adj[m, k, :k].sum() == 2
+                par = np.nonzero(b.adj[m, k, :k])[0]
+                assert not (b.jtype[m, par] == 0).all()
+    pad = np.arange(8)[None, :] >= b.n_joints[:, None]
+    assert (b.jtype[pad] == -1).all() and (b.pos[pad] == 0).all()
+    live = ~pad
+    assert b.pos[live].min() >= 0.0 and b.pos[live].max() < 1.0
+
+
+def test_dyad_batch_deterministic_and_seeded():
+    a = I.dyad_batch(300, 6, 20, seed=3)
+    b = I.dyad_batch(300, 6, 20, seed=3)
+    c = I.dyad_batch(300, 6, 20, seed=4)
+    for x, y in ((a.adj, b.adj), (a.pos, b.pos), (a.jtype, b.jtype), (a.n_joints, b.n_joints)):
+        assert np.array_equal(x, y)
+    assert not np.array_equal(a.pos, c.pos)
+    # prefix property: the first rows do not depend on the batch size
+    d = I.dyad_batch(100, 6, 20, seed=3)
+    assert np.array_equal(d.adj, a.adj[:100]) and np.array_equal(d.pos, a.pos[:100])
+
+
+def test_permute_is_a_relabeling():
+    a = I.dyad_batch(50, 6, 10, seed=1)
+    p = I.dyad_batch(50, 6, 10, seed=1, permute=True)
+    for m in range(50):
+        n = a.n_joints[m]
+        # same multiset of degrees and types, same number of links
+        assert sorted(a.adj[m, :n, :n].sum(0)) == sorted(p.adj[m, :n, :n].sum(0))
+        assert sorted(a.jtype[m, :n]) == sorted(p.jtype[m, :n])
+        assert a.adj[m].sum() == p.adj[m].sum()
+
+
+def test_fourbar_batch():
+    f = I.fourbar_batch(16)
+    assert f.pos.dtype == np.float64 and f.adj.shape == (16, 5, 5)
+    assert list(f.jtype[0]) == [0, 2, 0, 1, 1]
+    assert f.adj[0, 1, 3] and f.adj[0, 2, 3] and f.adj[0, 1, 4] and f.adj[0, 3, 4] and f.adj[0, 0, 1]
+
+
+def test_perturb_and_requests():
+    c = np.zeros((100, 200, 2), np.float32)
+    q = I.perturb_curves(c, 0.02, seed=0)
+    assert abs(q.std() - 0.02) < 0.001 and abs(q.mean()) < 0.001
+    t, n = I.poisson_requests(20000, 2000.0, 65536, seed=0)
+    assert abs(t[-1] / 20000 - 1 / 2000) < 5e-5
+    assert n.min() >= 1 and n.max() <= 65536
+    # log-uniform: the median is near sqrt(65537)
+    assert 150 < np.median(n) < 350

@@ -1,0 +1,77 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and check that the
+pins of test_oracle_pins.py catch every one of them."""
+import os
+
+import numpy as np
+import pytest
+
+import test_oracle_pins as pins
+from oracle import oracle as O
+from paper_2208_14567_gb300 import inputs as I
+
+MUTANTS = {
+    "swapped lengths in e": ("double e = d2 + P->r1sq[d] - P->r2sq[d];", "double e = d2 - P->r1sq[d] + P->r2sq[d];"),
+    "wrong length in D": ("double D = 4.0 * d2 * P->r1sq[d] - e * e;", "double D = 4.0 * d2 * P->r2sq[d] - e * e;"),
+    "wrong branch": ("double sh = (double)P->s[d] * h;", "double sh = -(double)P->s[d] * h;"),
+    "dropped perpendicular term": ("out[2 * P->k[d]] = pi[0] + (e * dx - sh * dy) * inv;",
+                                   "out[2 * P->k[d]] = pi[0] + (e * dx) * inv;"),
+    "clockwise crank": ("out[2 * P->motor + 1] = pv[1] + (s * ux + c * uy);",
+                        "out[2 * P->motor + 1] = pv[1] + (-s * ux + c * uy);"),
+    "never locks": ("if (!(q > 0.0)) {", "if (q < -1e300) {"),
+    "branch sign flipped": ("P->s[nd] = cross < 0.0 ? -1 : 1;", "P->s[nd] = cross > 0.0 ? -1 : 1;"),
+    "highest ready joint first": ("if (cnt >= 2) { pick = a; break; }", "if (cnt >= 2) { pick = a; }"),
+    "no edge-count check": ("if (links != 2 * n_simple) return P->status = LO_OVERCONSTRAINED;", ""),
+    "normalise sign rule flipped": ("if (s3 < 0.0)", "if (s3 > 0.0)"),
+    "squared chamfer": ("double d = sqrt(sq_dist(P + 2 * a, Q + 2 * b));", "double d = sq_dist(P + 2 * a, Q + 2 * b);"),
+    "one-directional chamfer": ("return sp / tp + sq / tq;", "return sp / tp;"),
+}
+
+
+def run_pins(lib):
+    """Every pin of test_oracle_pins.py with this oracle build; returns the failures."""
+    saved = O._lib
+    O._lib = lib
+    failures = []
+    try:
+        f = I.fourbar_batch(400, seed=0)
+        d = I.dyad_batch(600, 6, 12, seed=1, permute=True)
+        fourbars = (f, O.simulate(f, pins.T))
+        dyads = (d, O.simulate(d, pins.T))
+        checks = [
+            lambda: pins.test_plan_fourbar(O),
+            lambda: pins.test_plan_solve_order_follows_lowest_ready_joint(O),
+            lambda: pins.test_extra_link_breaks_mobility_and_plan(O),
+            lambda: pins.test_step0_reproduces_initial_positions(fourbars, dyads),
+            lambda: pins.test_rigidity_every_link_keeps_its_length(dyads, fourbars),
+            lambda: pins.test_nan_from_lock_and_flags(dyads),
+            lambda: pins.test_closure_at_full_turn(O, dyads),
+            lambda: pins.test_fourbar_matches_trigonometric_solution(fourbars),
+            lambda: pins.test_full_rotation_criterion(fourbars),
+            lambda: pins.test_brute_force_branches(O),
+            lambda: pins.test_special_cases(O),
+            lambda: pins.test_normalize_properties_and_invariance(O, fourbars),
+            lambda: pins.test_normalize_ellipse_and_degenerate(O),
+            lambda: pins.test_chamfer_against_cdist(O),
+        ]
+        for i, c in enumerate(checks):
+            try:
+                c()
+            except (AssertionError, ValueError, IndexError, ZeroDivisionError, TypeError):
+                failures.append(i)
+    finally:
+        O._lib = saved
+    return failures
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = O.source()
+    assert src.count(old) == 1, f"mutation site not found: {old}"
+    lib = O.compile_variant(src.replace(old, new), os.path.join(str(tmp_path), "mutant.so"))
+    assert run_pins(lib), f"no pin caught the mutant '{name}'"
+
+
+def test_unmutated_oracle_passes_all(tmp_path):
+    lib = O.compile_variant(O.source(), os.path.join(str(tmp_path), "same.so"))
+    assert run_pins(lib) == []

@@ -1,0 +1,428 @@
+"""Pins of the FP64 oracle against what the paper and the mathematics fix.
+
+None of these re-types the oracle's formulas: they use identities of the
+construction (step 0, rigidity, closure), an independent trigonometric solution
+of the four-bar, the Grashof-type full-rotation condition, brute force over both
+circle-intersection branches, the mobility equation (Eq. 1) on the joint graph,
+and library routines (scipy cdist, numpy sorting, SVD).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial.distance import cdist
+
+from conftest import bbox_diag
+from paper_2208_14567_gb300 import inputs as I
+
+T = 200
+
+
+# ----------------------------------------------------------------------------- plans
+
+def mech(n, edges, types, pos=None, nmax=None):
+    nmax = nmax or n
+    adj = np.zeros((nmax, nmax), np.uint8)
+    for a, b in edges:
+        adj[a, b] = adj[b, a] = 1
+    jt = np.full(nmax, -1, np.int8)
+    jt[:n] = types
+    if pos is None:
+        pos = np.random.default_rng(n).random((nmax, 2))
+    return adj, jt, np.asarray(pos, np.float64)
+
+
+FOURBAR_E = [(0, 1), (1, 3), (2, 3), (1, 4), (3, 4)]
+
+
+def test_plan_fourbar(oracle_lib):
+    adj, jt, pos = mech(5, FOURBAR_E, [0, 2, 0, 1, 1])
+    P = oracle_lib.plan(5, adj, jt, pos)
+    assert P.status == 0 and P.motor == 1 and P.pivot == 0 and P.n_dyads == 2 and P.coupler == 4
+    assert (P.k[0], P.i[0], P.j[0]) == (3, 1, 2)
+    assert (P.k[1], P.i[1], P.j[1]) == (4, 1, 3)
+    # lengths are the initial link lengths
+    assert P.r1sq[0] == pytest.approx(((pos[3] - pos[1]) ** 2).sum(), rel=1e-15)
+    assert P.r2sq[1] == pytest.approx(((pos[4] - pos[3]) ** 2).sum(), rel=1e-15)
+
+
+def test_plan_solve_order_follows_lowest_ready_joint(oracle_lib):
+    # joint 5 becomes solvable first (neighbours 1 and 2 known); joint 3 needs 5
+    edges = [(0, 1), (3, 5), (3, 1), (4, 3), (4, 2), (5, 1), (5, 2)]
+    adj, jt, pos = mech(6, edges, [0, 2, 0, 1, 1, 1])
+    P = oracle_lib.plan(6, adj, jt, pos)
+    assert P.status == 0
+    assert [P.k[d] for d in range(3)] == [5, 3, 4]
+    assert P.coupler == 4
+    # joints 3 (on 1, 2) and 4 (on 0, 1) are ready together: the lower index goes first
+    edges = [(0, 1), (1, 3), (2, 3), (0, 4), (1, 4), (3, 5), (4, 5)]
+    adj, jt, pos = mech(6, edges, [0, 2, 0, 1, 1, 1])
+    P = oracle_lib.plan(6, adj, jt, pos)
+    assert P.status == 0 and [P.k[d] for d in range(3)] == [3, 4, 5]
+    assert (P.i[1], P.j[1]) == (0, 1) and (P.i[2], P.j[2]) == (3, 4)
+
+
+@pytest.mark.parametrize("edges,types,n,status", [
+    (FOURBAR_E, [0, 1, 0, 1, 1], 5, 4),                       # no actuated joint
+    (FOURBAR_E, [0, 2, 0, 2, 1], 5, 4),                       # two actuated joints
+    ([(1, 3), (2, 3), (1, 4), (3, 4)], [0, 2, 0, 1, 1], 5, 5),  # crank not on a fixed joint
+    ([(0, 1), (1, 3), (3, 4), (2, 4)], [0, 2, 0, 1, 1], 5, 6),  # two joints each with one known neighbour
+    ([(0, 1), (1, 3), (2, 3), (0, 3)], [0, 2, 0, 1], 4, 7),   # three known neighbours
+    ([(0, 1), (1, 2), (1, 3), (2, 3)], [0, 2, 0, 1], 4, 7),   # crank also linked to another ground joint
+    (FOURBAR_E, [0, 2, 0, 3, 1], 5, 2),                       # bad type
+])
+def test_plan_statuses(oracle_lib, edges, types, n, status):
+    adj, jt, pos = mech(n, edges, types)
+    assert oracle_lib.plan(n, adj, jt, pos).status == status
+
+
+def test_plan_bad_adjacency_and_size(oracle_lib):
+    adj, jt, pos = mech(5, FOURBAR_E, [0, 2, 0, 1, 1])
+    a2 = adj.copy()
+    a2[3, 1] = 0
+    assert oracle_lib.plan(5, a2, jt, pos).status == 3
+    a3 = adj.copy()
+    a3[2, 2] = 1
+    assert oracle_lib.plan(5, a3, jt, pos).status == 3
+    assert oracle_lib.plan(1, adj, jt, pos).status == 1
+    assert oracle_lib.plan(6, adj, jt, pos).status == 1
+
+
+def mobility(adj, jt, n):
+    """Eq. 1 with j2 = 0 on the joint graph: bodies = ground + every link that is not
+    ground-to-ground; j1 = sum over joints of (bodies meeting there - 1)."""
+    fixed = jt[:n] == 0
+    bars = [(a, b) for a in range(n) for b in range(a + 1, n) if adj[a, b] and not (fixed[a] and fixed[b])]
+    bodies = 1 + len(bars)
+    j1 = 0
+    for a in range(n):
+        meet = sum(1 for (x, y) in bars if a in (x, y)) + (1 if fixed[a] else 0)
+        j1 += max(meet - 1, 0)
+    return 3 * (bodies - 1) - 2 * j1
+
+
+def test_generated_candidates_have_mobility_one_and_plan(oracle_lib):
+    b = I.dyad_batch(300, 6, 12, seed=5, permute=True)
+    for m in range(b.B):
+        n = b.n_joints[m]
+        assert mobility(b.adj[m], b.jtype[m], n) == 1
+        assert oracle_lib.plan(n, b.adj[m], b.jtype[m], b.pos[m].astype(np.float64)).status == 0
+
+
+def test_extra_link_breaks_mobility_and_plan(oracle_lib):
+    b = I.dyad_batch(100, 7, 10, seed=6)
+    rng = np.random.default_rng(0)
+    seen = 0
+    for m in range(b.B):
+        n = b.n_joints[m]
+        free = [(x, y) for x in range(n) for y in range(x + 1, n)
+                if not b.adj[m, x, y] and not (b.jtype[m, x] == 0 and b.jtype[m, y] == 0)]
+        x, y = free[rng.integers(len(free))]
+        adj = b.adj[m].copy()
+        adj[x, y] = adj[y, x] = 1
+        assert mobility(adj, b.jtype[m], n) == 0
+        st = oracle_lib.plan(n, adj, b.jtype[m], b.pos[m].astype(np.float64)).status
+        assert st in (6, 7)
+        seen += st == 7
+    assert seen > 50
+
+
+# ------------------------------------------------------------------------- simulation
+
+@pytest.fixture(scope="module")
+def fourbars(oracle_lib):
+    f = I.fourbar_batch(2048, seed=0)
+    return f, oracle_lib.simulate(f, T)
+
+
+@pytest.fixture(scope="module")
+def dyads(oracle_lib):
+    b = I.dyad_batch(3000, 6, 14, seed=1, permute=True)
+    return b, oracle_lib.simulate(b, T)
+
+
+def test_step0_reproduces_initial_positions(fourbars, dyads):
+    for batch, r in (fourbars, dyads):
+        L = bbox_diag(batch.pos, batch.n_joints)
+        ok = r.lock_step != 0
+        assert ok.mean() > 0.99
+        for m in np.nonzero(ok)[0]:
+            n = batch.n_joints[m]
+            err = np.abs(r.traj[m, :n, 0] - batch.pos[m, :n]).max()
+            # FP64 rounding is amplified by 1/sin(gamma) = q^-1/2 per dyad (q >= min_disc)
+            kappa = 1.0 / math.sqrt(min(1.0, max(r.min_disc[m], 1e-300)))
+            assert err <= 1e-13 * L[m] * kappa
+
+
+def test_rigidity_every_link_keeps_its_length(dyads, fourbars):
+    for batch, r in (fourbars, dyads):
+        for m in range(batch.B):
+            n = batch.n_joints[m]
+            stop = T if r.lock_step[m] < 0 else r.lock_step[m]
+            if stop == 0:
+                continue
+            a, b = np.nonzero(np.triu(batch.adj[m, :n, :n]))
+            tr = r.traj[m, :n, :stop]
+            l0 = np.linalg.norm(batch.pos[m, a].astype(np.float64) - batch.pos[m, b], axis=-1)
+            lt = np.linalg.norm(tr[a] - tr[b], axis=-1)
+            assert np.abs(lt - l0[:, None]).max() <= 1e-9 * max(1.0, l0.max())
+
+
+def test_nan_from_lock_and_flags(dyads):
+    batch, r = dyads
+    lk = r.lock_step
+    assert set(np.unique(r.valid)) <= {0, 1}
+    assert ((lk == -1) == (r.valid == 1)).all()
+    for m in np.nonzero(lk >= 0)[0][:200]:
+        n = batch.n_joints[m]
+        assert np.isnan(r.traj[m, :n, lk[m]:]).all()
+        assert not np.isnan(r.traj[m, :n, :lk[m]]).any()
+    assert np.isnan(r.traj[:, 14:]).all() if batch.nmax > 14 else True
+    # min_disc: q of the unlocked steps is a squared sine in (0, 1]
+    md = r.min_disc[lk != 0]
+    assert (md > 0).all() and (md <= 1 + 1e-12).all()
+
+
+def test_closure_at_full_turn(oracle_lib, dyads):
+    batch, r = dyads
+    L = bbox_diag(batch.pos, batch.n_joints)
+    for m in np.nonzero(r.valid)[0][:300]:
+        P = oracle_lib.plan(batch.n_joints[m], batch.adj[m], batch.jtype[m], batch.pos[m].astype(np.float64))
+        out, locked, *_ = oracle_lib.solve_at(P, batch.pos[m], 2 * math.pi)
+        assert not locked
+        n = batch.n_joints[m]
+        assert np.abs(out[:n] - batch.pos[m, :n]).max() <= 1e-10 * L[m]
+
+
+def fourbar_closed_form(p0, T):
+    """Four-bar positions by trigonometry (law of cosines at the rocker pivot and a
+    rigid rotation of the coupler triangle), independent of the oracle's algebra.
+    Returns (positions [T,5,2], acos argument [T])."""
+    A0, A, B0, B, P = p0
+    th = 2 * np.pi * np.arange(T) / T
+    u = A - A0
+    At = A0 + np.stack([np.cos(th) * u[0] - np.sin(th) * u[1], np.sin(th) * u[0] + np.cos(th) * u[1]], -1)
+    b = np.linalg.norm(B - A)   # coupler
+    c = np.linalg.norm(B - B0)  # rocker
+    w = At - B0
+    delta = np.linalg.norm(w, axis=-1)
+    arg = (c * c + delta * delta - b * b) / (2 * c * delta)
+    # branch: orientation of (A, B0, B) at t = 0
+    sgn = np.sign((A - B0)[0] * (B - B0)[1] - (A - B0)[1] * (B - B0)[0])
+    psi = np.arctan2(w[:, 1], w[:, 0]) + sgn * np.arccos(np.clip(arg, -1, 1))
+    Bt = B0 + c * np.stack([np.cos(psi), np.sin(psi)], -1)
+    ang = np.arctan2(*(Bt - At).T[::-1]) - math.atan2(*(B - A)[::-1])
+    v = P - A
+    Pt = At + np.stack([np.cos(ang) * v[0] - np.sin(ang) * v[1], np.sin(ang) * v[0] + np.cos(ang) * v[1]], -1)
+    X = np.stack([np.broadcast_to(A0, At.shape), At, np.broadcast_to(B0, At.shape), Bt, Pt], 1)
+    return X, arg
+
+
+def test_fourbar_matches_trigonometric_solution(fourbars):
+    f, r = fourbars
+    L = bbox_diag(f.pos, f.n_joints)
+    checked = 0
+    for m in range(f.B):
+        X, arg = fourbar_closed_form(f.pos[m], T)
+        bad = np.abs(arg) > 1
+        lock_cf = int(np.argmax(bad)) if bad.any() else -1
+        margin = np.min(np.abs(np.abs(arg) - 1)) < 1e-9
+        if not margin:
+            assert r.lock_step[m] == lock_cf
+        stop = T if r.lock_step[m] < 0 else r.lock_step[m]
+        good = np.abs(np.abs(arg[:stop]) - 1) > 1e-6
+        if good.any():
+            d = np.abs(r.traj[m].transpose(1, 0, 2)[:stop][good] - X[:stop][good]).max()
+            assert d <= 1e-9 * L[m]
+            checked += 1
+    assert checked > 0.9 * f.B
+
+
+def test_full_rotation_criterion(fourbars):
+    """Crank a, ground g, coupler b, rocker c: the crank turns fully iff the diagonal
+    range [|g - a|, g + a] lies inside [|b - c|, b + c].  Sampling at T steps can
+    only miss a lock window, never invent one."""
+    f, r = fourbars
+    agree = 0
+    for m in range(f.B):
+        A0, A, B0, B, _ = f.pos[m]
+        a, g = np.linalg.norm(A - A0), np.linalg.norm(B0 - A0)
+        b, c = np.linalg.norm(B - A), np.linalg.norm(B - B0)
+        full = (g + a <= b + c) and (abs(g - a) >= abs(b - c))
+        if full:
+            assert r.valid[m] == 1
+        agree += int(full) == int(r.valid[m])
+    assert agree >= 0.995 * f.B
+    assert 0.05 < r.valid.mean() < 0.95
+
+
+def solve_branch(p0, i_j_k, signs, theta, pivot, motor, fixed):
+    """Positions at crank angle theta for given branch signs, by trigonometry."""
+    pos = p0.copy()
+    u = p0[motor] - p0[pivot]
+    pos[motor] = p0[pivot] + [math.cos(theta) * u[0] - math.sin(theta) * u[1],
+                              math.sin(theta) * u[0] + math.cos(theta) * u[1]]
+    for (i, j, k), s in zip(i_j_k, signs):
+        r1 = np.linalg.norm(p0[k] - p0[i])
+        r2 = np.linalg.norm(p0[k] - p0[j])
+        w = pos[j] - pos[i]
+        d = np.linalg.norm(w)
+        cosb = (d * d + r1 * r1 - r2 * r2) / (2 * d * r1)
+        if not (-1 < cosb < 1):
+            return None
+        al = math.atan2(w[1], w[0]) + s * math.acos(cosb)
+        pos[k] = pos[i] + r1 * np.array([math.cos(al), math.sin(al)])
+    return pos
+
+
+def test_brute_force_branches(oracle_lib):
+    b = I.dyad_batch(400, 5, 7, seed=11)
+    checked = 0
+    for m in range(b.B):
+        n = b.n_joints[m]
+        p0 = b.pos[m].astype(np.float64)
+        P = oracle_lib.plan(n, b.adj[m], b.jtype[m], p0)
+        nd = P.n_dyads
+        if nd > 4:
+            continue
+        ijk = [(P.i[d], P.j[d], P.k[d]) for d in range(nd)]
+        fixed = [a for a in range(n) if b.jtype[m, a] == 0]
+        combos = [tuple(1 - 2 * ((c >> d) & 1) for d in range(nd)) for c in range(2 ** nd)]
+        hits = [s for s in combos
+                if (x := solve_branch(p0, ijk, s, 0.0, P.pivot, P.motor, fixed)) is not None
+                and np.abs(x[:n] - p0[:n]).max() < 1e-9]
+        assert len(hits) == 1
+        for t in range(1, 40):
+            th = 2 * math.pi * t / 40
+            out, locked, qmin, *_ = oracle_lib.solve_at(P, p0, th)
+            if locked:
+                break
+            mine = solve_branch(p0, ijk, hits[0], th, P.pivot, P.motor, fixed)
+            assert np.abs(out[:n] - mine[:n]).max() < 1e-9
+            if qmin > 1e-2:
+                # continuity: a small further turn lands on the branch nearest to this one
+                th2 = th + 1e-4
+                nxt, lk2, *_ = oracle_lib.solve_at(P, p0, th2)
+                assert not lk2
+                cands = [x for s in combos if (x := solve_branch(p0, ijk, s, th2, P.pivot, P.motor, fixed)) is not None]
+                dist = [np.abs(x[:n] - out[:n]).max() for x in cands]
+                assert np.abs(nxt[:n] - cands[int(np.argmin(dist))][:n]).max() < 1e-9
+            checked += 1
+    assert checked > 500
+
+
+def test_special_cases(oracle_lib):
+    rng = np.random.default_rng(3)
+    # joint 3 on two ground joints: stationary; joint 4 on pivot + crank: circle with the crank
+    edges = [(0, 1), (0, 3), (2, 3), (0, 4), (1, 4), (1, 5), (3, 5)]
+    for _ in range(20):
+        adj, jt, pos = mech(6, edges, [0, 2, 0, 1, 1, 1], pos=rng.random((6, 2)))
+        batch = I.MechBatch(np.array([6], np.int32), adj[None], jt[None], pos[None])
+        r = oracle_lib.simulate(batch, 64)
+        stop = 64 if r.lock_step[0] < 0 else r.lock_step[0]
+        tr = r.traj[0]
+        assert np.abs(tr[3, :stop] - pos[3]).max() < 1e-12
+        th = 2 * np.pi * np.arange(stop) / 64
+        v = pos[4] - pos[0]
+        circ = pos[0] + np.stack([np.cos(th) * v[0] - np.sin(th) * v[1], np.sin(th) * v[0] + np.cos(th) * v[1]], -1)
+        assert np.abs(tr[4, :stop] - circ).max() < 1e-12
+    # no simple joints: the crank alone never locks, the coupler is the actuated joint
+    adj, jt, pos = mech(3, [(0, 1)], [0, 2, 0])
+    batch = I.MechBatch(np.array([3], np.int32), adj[None], jt[None], pos[None])
+    r = oracle_lib.simulate(batch, 8)
+    assert r.valid[0] == 1 and np.allclose(r.path[0], r.traj[0, 1])
+
+
+def test_unsimulated_mechanisms(oracle_lib):
+    adj, jt, pos = mech(5, FOURBAR_E, [0, 1, 0, 1, 1])
+    batch = I.MechBatch(np.array([5], np.int32), adj[None], jt[None], pos[None])
+    r = oracle_lib.simulate(batch, 8)
+    assert r.status[0] == 4 and r.valid[0] == 0 and r.lock_step[0] == -2 and np.isnan(r.traj).all()
+
+
+def test_threads_do_not_change_results(oracle_lib):
+    b = I.dyad_batch(500, 6, 10, seed=2)
+    r1 = oracle_lib.simulate(b, 50, threads=1)
+    r8 = oracle_lib.simulate(b, 50, threads=8)
+    assert np.array_equal(r1.traj, r8.traj, equal_nan=True)
+    assert np.array_equal(r1.lock_step, r8.lock_step)
+
+
+# -------------------------------------------------------------------- normalisation
+
+def test_normalize_properties_and_invariance(oracle_lib, fourbars):
+    f, r = fourbars
+    curves = r.path[r.valid == 1][:300]
+    out = oracle_lib.normalize(curves)
+    x, y = out[..., 0], out[..., 1]
+    assert np.abs(x.mean(1)).max() < 1e-12 and np.abs(y.mean(1)).max() < 1e-12
+    assert np.abs(np.sqrt((x * x + y * y).mean(1)) - 1).max() < 1e-12
+    assert np.abs((x * y).mean(1)).max() < 1e-12
+    assert ((x * x).mean(1) >= (y * y).mean(1) - 1e-12).all()
+    assert ((x ** 3).sum(1) >= -1e-12).all()
+    # principal axis from a library SVD of the centred curve
+    for k in range(min(50, len(curves))):
+        c = curves[k] - curves[k].mean(0)
+        _, s, vt = np.linalg.svd(c, full_matrices=False)
+        if s[0] - s[1] > 1e-6 * s[0]:
+            ax = vt[0]
+            rot = np.stack([c @ ax, c @ np.array([-ax[1], ax[0]])], -1) / np.sqrt((c ** 2).sum(1).mean())
+            if (rot[:, 0] ** 3).sum() < 0:
+                rot = -rot
+            assert np.abs(rot - out[k]).max() < 1e-9
+    # similarity invariance
+    rng = np.random.default_rng(0)
+    for k in range(min(100, len(curves))):
+        a = rng.uniform(0, 2 * np.pi)
+        R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+        moved = rng.uniform(0.2, 5) * curves[k] @ R.T + rng.normal(size=2)
+        o2 = oracle_lib.normalize(moved[None])[0]
+        lam = np.linalg.eigvalsh(np.cov(out[k].T))
+        if lam[1] - lam[0] > 1e-6 and abs((out[k, :, 0] ** 3).sum()) > 1e-6:
+            assert np.abs(o2 - out[k]).max() < 1e-9
+
+
+def test_normalize_ellipse_and_degenerate(oracle_lib):
+    s = 2 * np.pi * np.arange(200) / 200
+    e = np.stack([3 * np.cos(s), 1 * np.sin(s)], -1)
+    a = 0.7
+    R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+    out = oracle_lib.normalize((e @ R.T + [4, -2])[None])[0]
+    rms = np.sqrt((e ** 2).sum(1).mean())
+    # an ellipse is symmetric: sum x^3 = 0 picks either orientation; compare up to sign
+    ref = e / rms
+    assert min(np.abs(out - ref).max(), np.abs(out + ref).max()) < 1e-12
+    z = oracle_lib.normalize(np.ones((1, 200, 2)))
+    assert (z == 0).all()
+
+
+# -------------------------------------------------------------------------- chamfer
+
+def test_chamfer_against_cdist(oracle_lib):
+    rng = np.random.default_rng(4)
+    for _ in range(20):
+        P = rng.normal(size=(rng.integers(1, 60), 2))
+        Q = rng.normal(size=(rng.integers(1, 60), 2))
+        D = cdist(P, Q)
+        ref = D.min(1).mean() + D.min(0).mean()
+        assert oracle_lib.chamfer(P, Q) == pytest.approx(ref, rel=1e-13)
+        assert oracle_lib.chamfer(P, Q) == pytest.approx(oracle_lib.chamfer(Q, P), rel=1e-13)
+        assert oracle_lib.chamfer(P, P) == 0.0
+
+
+def test_chamfer_topk_exact_copy_ranks_first(oracle_lib):
+    rng = np.random.default_rng(5)
+    db = rng.normal(size=(300, 50, 2))
+    q = db[[17, 200]].copy()
+    idx, dist = oracle_lib.chamfer_topk(q, db, 5)
+    assert idx[0, 0] == 17 and idx[1, 0] == 200 and dist[0, 0] == 0 and dist[1, 0] == 0
+    d = oracle_lib.chamfer_many(q[0], db)
+    ref = np.argsort(d, kind="stable")[:5]
+    assert np.array_equal(idx[0], ref)
+    assert (np.diff(dist, axis=1) >= 0).all()
+
+
+def test_topk_ties_go_to_lower_index(oracle_lib):
+    d = np.array([3.0, 1.0, 2.0, 1.0, 1.0, 0.5])
+    idx, dist = oracle_lib.topk(d, 4)
+    assert list(idx) == [5, 1, 3, 4]
