@@ -1,0 +1,185 @@
+/*
+ * links.h -- C ABI of the GB300 batched planar-linkage simulator.
+ *
+ * Method: LINKS (Nobari, Srivastava, Gutfreund, Ahmed; arXiv 2208.14567).
+ * A mechanism is an undirected graph over n joints given by an n x n 0/1
+ * adjacency matrix, a type per joint (0 fixed, 1 simple, 2 actuated) and the
+ * initial joint positions (Sec. "Mechanism Representation").  It is simulated
+ * over T equally spaced positions of one full actuator turn (Sec. "Dataset
+ * Features", item Simulation Data) with the graphical solver: from the known
+ * joints (fixed + actuated), repeatedly solve a joint with two known neighbours
+ * by intersecting two circles (Sec. "Graphical Simulator", Fig. "solver").  A
+ * candidate is valid when the actuator completes the turn without locking
+ * (Sec. "Finding Valid Initial Positions", Infeasibility rule).
+ *
+ * Conventions for every call:
+ *   - the return value is a LINKS_* status; 0 is success; no exception or
+ *     abort crosses this boundary; links_last_error() describes the last
+ *     failure of the calling thread;
+ *   - "device" pointers are CUDA device memory owned by the caller (any
+ *     allocator); "host" pointers are caller-owned host memory;
+ *   - calls taking device pointers are asynchronous on the context's stream
+ *     and make no allocation, so a sequence of them can be captured in a CUDA
+ *     graph between links_capture_begin and links_capture_end;
+ *   - the library owns contexts, plans and graphs and frees them in the
+ *     matching *_free / links_destroy call.
+ */
+#ifndef LINKS_H
+#define LINKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LINKS_API __attribute__((visibility("default")))
+#else
+#define LINKS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Call statuses. */
+#define LINKS_OK 0
+#define LINKS_EINVAL 1     /* bad argument: null pointer, size out of range, unknown enum */
+#define LINKS_ECUDA 2      /* a CUDA runtime call failed (text in links_last_error) */
+#define LINKS_ENOMEM 3     /* allocation failed */
+#define LINKS_ECAPACITY 4  /* a batch larger than the plan's capacity */
+#define LINKS_EBUSY 5      /* serving ring full; retry later */
+#define LINKS_ETIMEDOUT 6  /* a bounded wait ran out */
+#define LINKS_ESTATE 7     /* call not valid in the current state */
+#define LINKS_EDEVICE 8    /* a kernel raised its error word (see links_sync) */
+
+/* Per-mechanism plan statuses written by links_plan_build*.  A mechanism that
+ * is not OK is not simulated: valid = 0, lock_step = -2. */
+#define LINKS_MECH_OK 0
+#define LINKS_MECH_BAD_SIZE 1          /* n < 2 or n > n_max */
+#define LINKS_MECH_BAD_TYPE 2          /* a type outside {0,1,2} */
+#define LINKS_MECH_BAD_ADJ 3           /* adjacency not symmetric or a self-loop */
+#define LINKS_MECH_NO_MOTOR 4          /* not exactly one actuated joint */
+#define LINKS_MECH_NO_PIVOT 5          /* actuated joint has no fixed neighbour */
+#define LINKS_MECH_NOT_DYAD_SOLVABLE 6 /* complex loop or dangling joint: the solver stalls */
+#define LINKS_MECH_OVERCONSTRAINED 7   /* > 2 known neighbours, or links beyond 2 per simple joint */
+
+/* Position dtype, precision and output mode selectors. */
+#define LINKS_F32 0
+#define LINKS_F64 1
+#define LINKS_PLAIN_F64 0 /* one thread per mechanism, native FP64 throughout */
+#define LINKS_MIXED 1     /* FP32 screen with certified lock decisions; double-word
+                             FP32 where FP32 cannot certify; double-word trajectories */
+#define LINKS_OUT_FULL 0       /* rows = all B mechanisms */
+#define LINKS_OUT_VALID_ONLY 1 /* rows = valid mechanisms in index order, compacted */
+
+#define LINKS_MAX_JOINTS 32
+#define LINKS_MAX_T 32767
+
+typedef struct links_ctx_s* links_ctx;
+typedef struct links_plan_s* links_plan;
+typedef struct links_graph_s* links_graph;
+
+/* Text of the calling thread's last failure ("" if none).  Static storage. */
+LINKS_API const char* links_last_error(void);
+/* Name of a LINKS_* call status. */
+LINKS_API const char* links_strerror(int status);
+
+/* Context on CUDA device `device` issuing work on `cuda_stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  The library owns *out. */
+LINKS_API int links_create(links_ctx* out, int device, void* cuda_stream);
+LINKS_API int links_destroy(links_ctx ctx);
+/* Later calls on ctx issue work on this stream. */
+LINKS_API int links_set_stream(links_ctx ctx, void* cuda_stream);
+/* Waits for the stream, then reads and clears the device error word:
+ * LINKS_EDEVICE if a kernel raised it since the last links_sync. */
+LINKS_API int links_sync(links_ctx ctx);
+/* Allocates the per-T actuator tables (cos/sin of 2*pi*t/T in FP64 and as
+ * float pairs).  Called implicitly by links_simulate; call it before a graph
+ * capture that uses a T not simulated before. */
+LINKS_API int links_prepare(links_ctx ctx, int T);
+
+/* Plan storage for up to `capacity` mechanisms of at most n_max joints
+ * (2 <= n_max <= LINKS_MAX_JOINTS).  Allocates device memory; the library owns
+ * the plan. */
+LINKS_API int links_plan_create(links_ctx ctx, int64_t capacity, int n_max, links_plan* out);
+LINKS_API int links_plan_free(links_plan plan);
+
+/* Solve order of B mechanisms (Sec. "Graphical Simulator"; the found path is
+ * reused for every actuator position, Sec. "Graphical Simulator", last
+ * paragraph).  Device inputs, row-major, padded to the plan's n_max:
+ *   n_joints [B] int32, adj [B,n_max,n_max] uint8 (nonzero = link),
+ *   type [B,n_max] int8 (0 fixed, 1 simple, 2 actuated), pos0 [B,n_max,2]
+ *   float32 or float64 (pos_dtype).
+ * status_out [B] int32 (device, may be NULL) receives LINKS_MECH_*.
+ * Rules: the crank pivot is the lowest-index fixed neighbour of the actuated
+ * joint; the lowest-index unknown joint with >= 2 known neighbours is solved
+ * next, with the branch (orientation sign) of the initial positions.
+ * Asynchronous; inputs may be reused once the stream has passed this call. */
+LINKS_API int links_plan_build(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                     const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                     int32_t* status_out);
+
+/* Same rules, same result, computed by host threads from HOST inputs; the plan
+ * is uploaded on the context's stream.  status_out [B] is host memory.
+ * Synchronous (returns after the upload completed). */
+LINKS_API int links_plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                          const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                          int32_t* status_out);
+
+/* Mechanisms in the last build, the plan's n_max and its capacity. */
+LINKS_API int links_plan_info(links_plan plan, int64_t* B, int* n_max, int64_t* capacity);
+
+/* Copies the plans of mechanisms [b0, b0 + count) to HOST memory, for inspection:
+ *   topo [count, 6 + 3 (n_max - 2)] int32: status, n, motor joint, pivot joint,
+ *       coupler joint, dyad count nd, then per dyad (k, i, j) as joint indices with
+ *       (i, j) in the order that makes the solved branch the "+" one, i.e.
+ *       (p_j - p_i) x (p_k - p_i) >= 0 in the initial configuration;
+ *   lengths [count, 2 (n_max - 2)] float64 (may be NULL): r1^2 = |p_k - p_i|^2 and
+ *       r2^2 = |p_k - p_j|^2 per dyad (double-word values widened to FP64).
+ * Synchronous. */
+LINKS_API int links_plan_export(links_plan plan, int64_t b0, int64_t count, int32_t* topo,
+                                double* lengths);
+
+/* Simulate the planned mechanisms over T actuator steps, crank angle 2*pi*t/T
+ * counter-clockwise from the initial crank (t = 0..T-1).
+ * Device outputs (all caller-owned; any of traj, path may be NULL):
+ *   valid [B] uint8: 1 = no lock over the T steps;
+ *   lock_step [B] int16: first locking step, -1 none, -2 not simulated;
+ *   min_disc [B] float32: min over the dyads of the steps before the lock of
+ *       q = D / (4 r1^2 r2^2) = sin^2 of the angle at the solved joint, where
+ *       D = 4 d^2 r1^2 - (d^2 + r1^2 - r2^2)^2 (NaN if not simulated);
+ *   traj [rows,n_max,T,2] and path [rows,T,2] (coupler = last joint of the
+ *       solve order): float64 for LINKS_PLAIN_F64, float32 for LINKS_MIXED;
+ *       NaN from the locking step on and for joints >= n.
+ * out_mode LINKS_OUT_FULL: rows = B.  LINKS_OUT_VALID_ONLY: rows = valid
+ *   mechanisms in increasing index; out_index [out_capacity] int32 gets each
+ *   row's mechanism index, *n_out (device int32) the number of valid ones;
+ *   rows beyond out_capacity are not written.
+ * A step locks when a dyad has D <= 0 (no intersection) -- locking is a result,
+ * not an error.  Asynchronous. */
+LINKS_API int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out_mode,
+                   void* traj, void* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
+                   int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+
+/* Per-kernel timing for benchmarks: with enable = 1 (collection cleared), every
+ * kernel the library launches on ctx is bracketed by two CUDA events on the
+ * context's stream; enable = 0 stops.  Not for use inside a graph capture. */
+LINKS_API int links_profile(links_ctx ctx, int enable);
+/* Reads the collected timings (synchronizes the stream): up to max entries of
+ * kernel name (names [max][32], NUL-terminated), total milliseconds and launch
+ * count; *count receives the number of entries. */
+LINKS_API int links_profile_read(links_ctx ctx, int max, char* names, double* total_ms,
+                                 int64_t* launches, int* count);
+/* Number of kernels the library has launched through ctx since it was created. */
+LINKS_API int links_launch_count(links_ctx ctx, int64_t* out);
+
+/* Begin / end capturing the context's stream into a reusable graph. */
+LINKS_API int links_capture_begin(links_ctx ctx);
+LINKS_API int links_capture_end(links_ctx ctx, links_graph* out);
+LINKS_API int links_graph_launch(links_ctx ctx, links_graph graph);
+LINKS_API int links_graph_free(links_graph graph);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINKS_H */

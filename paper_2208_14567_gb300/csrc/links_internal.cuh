@@ -1,0 +1,276 @@
+// links_internal.cuh -- plan layout, double-word arithmetic and context state shared by
+// the library's translation units.  Not part of the public ABI (include/links.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/links.h"
+
+namespace links {
+
+constexpr int kMaxJ = LINKS_MAX_JOINTS;  // joints per mechanism (bit masks are uint32)
+constexpr float kU = 5.9604645e-08f;     // unit roundoff of float32, 2^-24
+constexpr float kLocalErr = 8.0f;        // local rounding-error multiplier of one FP32 dyad
+
+// ---------------------------------------------------------------------------------------
+// Plan layout (device, one record per mechanism, padded to n_max joints).
+//
+// Slots number the joints in solve order: slots [0, nf) are the fixed joints in
+// increasing joint index, slot nf is the actuated joint, slot nf+1+d is the joint
+// solved by dyad d.  All positions used by the mixed path are relative to the crank
+// pivot, kept as float pairs (hi, lo) whose sum carries ~48 bits.
+// ---------------------------------------------------------------------------------------
+struct __align__(16) MechHdr {
+  int32_t status;
+  uint8_t n, nd, nf, motor_joint;
+  uint8_t coupler_slot, pivot_joint, pad0, pad1;  // pad0 = pivot slot
+  float ux_h, ux_l, uy_h, uy_l;  // crank vector: actuated joint - pivot (initial)
+  float px_h, px_l, py_h, py_l;  // pivot (absolute)
+  float bmax;                    // bound of |p - pivot| of any joint during the turn
+  float e_motor;                 // FP32 error bound of the actuated joint position
+  float e_fixed;                 // FP32 error bound of a fixed joint position
+  float crank;                   // |u|
+};
+static_assert(sizeof(MechHdr) == 64, "MechHdr must be 64 bytes");
+
+// Dyad record: three float4 per dyad.
+//   r0 = {slots, R12_h, Rm_h, c_h}   slots = si | sj << 8 | k_joint << 16 | sk << 24
+//   r1 = {w2, locc, r1sq_h, r1sq_l}  w2 = 2 r1 r2, locc = local FP32 error constant
+//   r2 = {c_l, R12_l, Rm_l, 0}
+// with r1 = |p_k - p_i|, r2 = |p_k - p_j|, R12 = r1 + r2, Rm = |r1 - r2|,
+// c = r1^2 - r2^2, and (i, j) ordered so that the initial configuration has
+// (p_j - p_i) x (p_k - p_i) >= 0 (the solved branch is then always the "+" one).
+struct DyadRec {
+  float4 r0, r1, r2;
+};
+
+struct PlanDev {
+  MechHdr* hdr;          // [cap]
+  uint8_t* slot_joint;   // [cap][kMaxJ]
+  float4* fixpos;        // [cap][n_max]   fixed slots: (x_h, x_l, y_h, y_l) relative to pivot
+  double2* pos64;        // [cap][n_max]   absolute initial positions by slot (FP64 path)
+  DyadRec* dyad;         // [cap][n_max - 2]
+  int32_t* order;        // [cap]          OK mechanisms sorted by dyad count
+  int32_t* ctrs;         // [kCtrs]        histogram / cursors / work counters
+  int32_t* scan;         // [cap/1024 + 2] block sums of the valid-row scan
+  int32_t* row_of;       // [cap]          output row of each mechanism (VALID_ONLY), or -1
+  int n_max;
+  int max_dyads;
+  int64_t cap;
+};
+
+// Counter block layout (int32 words inside PlanDev::ctrs).
+constexpr int kHist = 0;          // [32] histogram of dyad counts (OK mechanisms)
+constexpr int kCursor = 32;       // [32] scatter cursors
+constexpr int kWork = 64;         // work counter of the screen / FP64 kernels
+constexpr int kWork2 = 65;        // work counter of the emit kernel
+constexpr int kNValid = 66;       // number of valid mechanisms (VALID_ONLY rows)
+constexpr int kCtrs = 80;
+
+struct TTable {
+  int T = 0;
+  float4* cs = nullptr;    // (cos_h, cos_l, sin_h, sin_l) of 2*pi*t/T
+  double2* cs64 = nullptr; // (cos, sin) in FP64
+};
+
+}  // namespace links
+
+struct links_ctx_s {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int32_t* d_err = nullptr;  // device error word
+  int num_sms = 0;
+  std::map<int, links::TTable> tables;
+  std::mutex mu;
+  // kernel timing (links_profile)
+  bool prof = false;
+  struct Rec {
+    const char* name;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, std::pair<double, int64_t>> acc;
+  int64_t launches = 0;
+};
+
+struct links_plan_s {
+  links_ctx ctx = nullptr;
+  links::PlanDev d{};
+  int64_t B = 0;  // mechanisms in the last build
+};
+
+struct links_graph_s {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
+namespace links {
+
+// Error plumbing (abi.cu).
+int set_error(int status, const std::string& msg);
+int cuda_status(cudaError_t e, const char* what);
+#define LINKS_CUDA(call)                                         \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return ::links::cuda_status(_e, #call); \
+  } while (0)
+
+const TTable* get_table(links_ctx ctx, int T, int* status);
+
+// Brackets one kernel launch: counts it and, while profiling, records events around it.
+struct KernelScope {
+  links_ctx ctx;
+  cudaEvent_t b = nullptr;
+  KernelScope(links_ctx c, const char* name);
+  ~KernelScope();
+};
+
+// Device error bits.
+constexpr int32_t kErrEmitLock = 1;   // emit found a lock in a mechanism the screen called valid
+constexpr int32_t kErrBadIndex = 2;   // an index outside its buffer was skipped
+
+// Entry points implemented per translation unit.
+int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                      const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                      int32_t* status_out);
+int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                    const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                    int32_t* status_out);
+int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, double* traj,
+                 double* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
+                 int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
+                   float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
+                   int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+// Shared by both precisions: rows of the valid mechanisms in index order.
+int compact_valid(links_ctx ctx, links_plan plan, const uint8_t* valid, int32_t* out_index,
+                  int64_t out_capacity, int32_t* n_out);
+int fill_unsimulated(links_ctx ctx, links_plan plan, uint8_t* valid, int16_t* lock_step,
+                     float* min_disc);
+
+// ---------------------------------------------------------------------------------------
+// Double-word ("float-float") arithmetic.  A value is hi + lo with |lo| <= ulp(hi)/2.
+// Building blocks: Knuth's TwoSum, Dekker's Fast2Sum, FMA-based TwoProd, and the
+// double-word add / multiply algorithms analysed by Joldes, Muller and Popescu,
+// "Tight and rigorous error bounds for basic building blocks of double-word
+// arithmetic", ACM TOMS 44(2), 2017.  The add is the "sloppy" variant: its error is
+// bounded by ~2^-48 (|x| + |y|) in absolute terms, which is what positions need.
+// Rounded intrinsics keep the compiler from contracting or reordering the steps.
+// ---------------------------------------------------------------------------------------
+struct dw {
+  float h, l;
+};
+
+#if defined(__CUDA_ARCH__)
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float ffma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float frsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ float fsqrt_rn(float x) { return __fsqrt_rn(x); }
+__device__ __forceinline__ float fdiv_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ float frcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+#else
+// Host code is compiled with -ffp-contract=off; fmaf is the correctly rounded C99 fma.
+inline float fadd(float a, float b) { return a + b; }
+inline float fsub(float a, float b) { return a - b; }
+inline float fmul(float a, float b) { return a * b; }
+inline float ffma(float a, float b, float c) { return std::fmaf(a, b, c); }
+inline float frsqrt(float x) { return 1.0f / std::sqrt(x); }
+inline float fsqrt_rn(float x) { return std::sqrt(x); }
+inline float fdiv_rn(float a, float b) { return a / b; }
+inline float frcp(float x) { return 1.0f / x; }
+#endif
+
+#define LINKS_HD __host__ __device__ __forceinline__
+
+LINKS_HD dw two_sum(float a, float b) {
+  float s = fadd(a, b);
+  float bb = fsub(s, a);
+  float e = fadd(fsub(a, fsub(s, bb)), fsub(b, bb));
+  return {s, e};
+}
+LINKS_HD dw fast_two_sum(float a, float b) {  // requires |a| >= |b| (or a == 0)
+  float s = fadd(a, b);
+  float e = fsub(b, fsub(s, a));
+  return {s, e};
+}
+LINKS_HD dw dw_make(float a) { return {a, 0.0f}; }
+LINKS_HD dw dw_from_double(double x) {
+  float h = (float)x;
+  float l = (float)(x - (double)h);
+  return {h, l};
+}
+LINKS_HD double dw_to_double(dw x) { return (double)x.h + (double)x.l; }
+LINKS_HD dw dw_neg(dw x) { return {-x.h, -x.l}; }
+LINKS_HD dw dw_add(dw x, dw y) {
+  dw s = two_sum(x.h, y.h);
+  float v = fadd(x.l, y.l);
+  float w = fadd(s.l, v);
+  return fast_two_sum(s.h, w);
+}
+LINKS_HD dw dw_sub(dw x, dw y) { return dw_add(x, dw_neg(y)); }
+LINKS_HD dw dw_mul(dw x, dw y) {
+  float p = fmul(x.h, y.h);
+  float e = ffma(x.h, y.h, -p);
+  e = ffma(x.h, y.l, e);
+  e = ffma(x.l, y.h, e);
+  return fast_two_sum(p, e);
+}
+LINKS_HD dw dw_mul_f(dw x, float y) {
+  float p = fmul(x.h, y);
+  float e = ffma(x.h, y, -p);
+  e = ffma(x.l, y, e);
+  return fast_two_sum(p, e);
+}
+LINKS_HD dw dw_sqr(dw x) {
+  float p = fmul(x.h, x.h);
+  float e = ffma(x.h, x.h, -p);
+  float t = fmul(x.h, x.l);
+  e = ffma(2.0f, t, e);
+  return fast_two_sum(p, e);
+}
+LINKS_HD dw dw_scale2(dw x, float pow2) { return {fmul(x.h, pow2), fmul(x.l, pow2)}; }  // exact
+// sqrt(x) for x > 0: FP32 seed from rsqrt, one Newton correction with an exact residual.
+LINKS_HD dw dw_sqrt(dw x) {
+  if (!(x.h > 0.0f)) return {0.0f, 0.0f};
+  float r = frsqrt(x.h);
+  float s = fmul(x.h, r);
+  float p = fmul(s, s);
+  float e = ffma(s, s, -p);
+  float res = fadd(fsub(fsub(x.h, p), e), x.l);
+  float corr = fmul(res, fmul(0.5f, r));
+  return fast_two_sum(s, corr);
+}
+// Same with correctly rounded seeds: bit-identical on host and device (plan builder).
+LINKS_HD dw dw_sqrt_exact(dw x) {
+  if (!(x.h > 0.0f)) return {0.0f, 0.0f};
+  float s = fsqrt_rn(x.h);
+  float p = fmul(s, s);
+  float e = ffma(s, s, -p);
+  float res = fadd(fsub(fsub(x.h, p), e), x.l);
+  return fast_two_sum(s, fdiv_rn(res, fadd(s, s)));
+}
+// 1/x: FP32 seed, one Newton correction with an exact residual.
+LINKS_HD dw dw_rcp(dw x) {
+  float y = frcp(x.h);
+  float p = fmul(x.h, y);
+  float e = ffma(x.h, y, -p);
+  float r = fsub(fsub(fsub(1.0f, p), e), fmul(x.l, y));
+  return fast_two_sum(y, fmul(y, r));
+}
+LINKS_HD float dw_sign(dw x) { return x.h != 0.0f ? x.h : x.l; }
+
+}  // namespace links

@@ -1,0 +1,363 @@
+// plan.cu -- solve-order builder (graphical solver of Baecher et al. as adopted by LINKS,
+// Sec. "Graphical Simulator", Fig. "solver").
+//
+// For each mechanism: start from the known joints (fixed + actuated), repeatedly take
+// the lowest-index unknown joint with at least two known neighbours and record the
+// dyad (joint, two parents); the path is found once and reused for every actuator
+// position (Sec. "Graphical Simulator", last paragraph; Sec. "Computational Cost of
+// Simulations").  The 1-DOF check counts links per Eq. 1 with the J-operator argument
+// (Sec. "1-DOF Operator"): apart from ground-ground links and the crank, every simple
+// joint owns exactly two links.
+//
+// The same builder runs as a CUDA kernel (one thread per mechanism) and on host
+// threads; both produce bit-identical plans.
+#include <algorithm>
+#include <thread>
+#include <vector>
+
+#include "links_internal.cuh"
+
+namespace links {
+namespace {
+
+struct BuildOut {
+  MechHdr* hdr;
+  uint8_t* slot_joint;
+  float4* fixpos;
+  double2* pos64;
+  DyadRec* dyad;
+};
+
+struct dw2 {
+  dw x, y;
+};
+
+LINKS_HD int popc32(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return __popc(v);
+#else
+  return __builtin_popcount(v);
+#endif
+}
+LINKS_HD int ffs32(uint32_t v) {  // index of the lowest set bit, v != 0
+#if defined(__CUDA_ARCH__)
+  return __ffs(v) - 1;
+#else
+  return __builtin_ctz(v);
+#endif
+}
+
+// p_a - p_b as a double-word pair: exact for float inputs, ~2^-48 relative for double.
+LINKS_HD dw2 rel(const float* pos, int a, int b) {
+  return {two_sum(pos[2 * a], -pos[2 * b]), two_sum(pos[2 * a + 1], -pos[2 * b + 1])};
+}
+LINKS_HD dw2 rel(const double* pos, int a, int b) {
+  return {dw_from_double(pos[2 * a] - pos[2 * b]), dw_from_double(pos[2 * a + 1] - pos[2 * b + 1])};
+}
+LINKS_HD dw abs_dw(const float* pos, int c) { return dw_make(pos[c]); }
+LINKS_HD dw abs_dw(const double* pos, int c) { return dw_from_double(pos[c]); }
+LINKS_HD dw norm2(dw2 v) { return dw_add(dw_sqr(v.x), dw_sqr(v.y)); }
+// |(x, y)| rounded up a little (a bound, identical on host and device).
+LINKS_HD float hyp_up(float x, float y) {
+  return fmul(fsqrt_rn(fadd(fmul(x, x), fmul(y, y))), 1.0f + 4.0f * kU);
+}
+
+template <typename PT>
+LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type, const PT* pos,
+                       BuildOut o) {
+  MechHdr h{};
+  h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
+  int status = LINKS_MECH_OK;
+  uint32_t nb[kMaxJ];
+  uint32_t fixm = 0, simm = 0, motm = 0;
+  int motor = -1, pivot = -1, nd = 0;
+  int dk[kMaxJ], di[kMaxJ], dj[kMaxJ];
+
+  if (n < 2 || n > n_max || n_max > kMaxJ) {
+    status = LINKS_MECH_BAD_SIZE;
+  } else {
+    for (int a = 0; a < n && status == LINKS_MECH_OK; ++a) {
+      int t = type[a];
+      if (t == 0) fixm |= 1u << a;
+      else if (t == 1) simm |= 1u << a;
+      else if (t == 2) motm |= 1u << a;
+      else status = LINKS_MECH_BAD_TYPE;
+    }
+  }
+  if (status == LINKS_MECH_OK) {
+    for (int a = 0; a < n; ++a) {
+      uint32_t m = 0;
+      const uint8_t* row = adj + (size_t)a * n_max;
+      for (int c = 0; c < n; ++c) m |= (row[c] != 0 ? 1u : 0u) << c;
+      nb[a] = m;
+    }
+    for (int a = 0; a < n && status == LINKS_MECH_OK; ++a) {
+      if (nb[a] & (1u << a)) status = LINKS_MECH_BAD_ADJ;
+      for (uint32_t m = nb[a]; m && status == LINKS_MECH_OK; m &= m - 1)
+        if (!((nb[ffs32(m)] >> a) & 1u)) status = LINKS_MECH_BAD_ADJ;
+    }
+  }
+  if (status == LINKS_MECH_OK && popc32(motm) != 1) status = LINKS_MECH_NO_MOTOR;
+  if (status == LINKS_MECH_OK) {
+    motor = ffs32(motm);
+    uint32_t pm = nb[motor] & fixm;
+    if (!pm) status = LINKS_MECH_NO_PIVOT;
+    else pivot = ffs32(pm);
+  }
+  if (status == LINKS_MECH_OK) {
+    uint32_t known = fixm | motm, unknown = simm;
+    while (unknown && status == LINKS_MECH_OK) {
+      int pick = -1, cnt = 0;
+      for (uint32_t u = unknown; u; u &= u - 1) {
+        int a = ffs32(u);
+        int c = popc32(nb[a] & known);
+        if (c >= 2) { pick = a; cnt = c; break; }
+      }
+      if (pick < 0) { status = LINKS_MECH_NOT_DYAD_SOLVABLE; break; }
+      if (cnt > 2) { status = LINKS_MECH_OVERCONSTRAINED; break; }
+      uint32_t par = nb[pick] & known;
+      dk[nd] = pick;
+      di[nd] = ffs32(par);
+      dj[nd] = ffs32(par & (par - 1));
+      ++nd;
+      known |= 1u << pick;
+      unknown &= ~(1u << pick);
+    }
+  }
+  if (status == LINKS_MECH_OK) {
+    int e2 = 0, ff2 = 0;
+    for (int a = 0; a < n; ++a) {
+      e2 += popc32(nb[a]);
+      if ((fixm >> a) & 1u) ff2 += popc32(nb[a] & fixm);
+    }
+    int links_ = (e2 - ff2) / 2 - 1;  // minus the crank
+    if (links_ != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
+  }
+  h.status = status;
+  if (status != LINKS_MECH_OK) {
+    h.nd = 0;
+    *o.hdr = h;
+    return status;
+  }
+
+  // Slots: fixed joints by index, then the actuated joint, then dyads in solve order.
+  int slot_of[kMaxJ];
+  int nf = 0;
+  for (uint32_t m = fixm; m; m &= m - 1) {
+    int a = ffs32(m);
+    slot_of[a] = nf;
+    o.slot_joint[nf] = (uint8_t)a;
+    ++nf;
+  }
+  slot_of[motor] = nf;
+  o.slot_joint[nf] = (uint8_t)motor;
+  for (int d = 0; d < nd; ++d) {
+    slot_of[dk[d]] = nf + 1 + d;
+    o.slot_joint[nf + 1 + d] = (uint8_t)dk[d];
+  }
+  for (int s = 0; s < n; ++s) {
+    int a = o.slot_joint[s];
+    o.pos64[s] = make_double2((double)pos[2 * a], (double)pos[2 * a + 1]);
+  }
+
+  float bound[kMaxJ];
+  float bmax = 0.0f;
+  for (int s = 0; s < nf; ++s) {
+    int a = o.slot_joint[s];
+    dw2 r = rel(pos, a, pivot);
+    o.fixpos[s] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
+    bound[s] = hyp_up(r.x.h, r.y.h);
+    bmax = fmaxf(bmax, bound[s]);
+  }
+  dw2 u = rel(pos, motor, pivot);
+  float crank = hyp_up(u.x.h, u.y.h);
+  bound[nf] = crank;
+  bmax = fmaxf(bmax, crank);
+
+  for (int d = 0; d < nd; ++d) {
+    int k = dk[d], i = di[d], j = dj[d];
+    dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
+    dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
+    if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
+      int t = i; i = j; j = t;
+      dw2 tv = vi; vi = vj; vj = tv;
+    }
+    dw r1sq = norm2(vi), r2sq = norm2(vj);
+    dw r1 = dw_sqrt_exact(r1sq), r2 = dw_sqrt_exact(r2sq);
+    dw R12 = dw_add(r1, r2);
+    dw Rm = dw_sub(r1, r2);
+    if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
+    dw c = dw_sub(r1sq, r2sq);
+    int si = slot_of[i], sj = slot_of[j], sk = nf + 1 + d;
+    float bi = bound[si], bj = bound[sj];
+    bound[sk] = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
+    bmax = fmaxf(bmax, bound[sk]);
+    float locc = fmul(kLocalErr * kU, fadd(fadd(R12.h, bi), bj));
+    uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
+    DyadRec rec;
+    union { uint32_t u; float f; } cv;
+    cv.u = slots;
+    rec.r0 = make_float4(cv.f, R12.h, Rm.h, c.h);
+    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), locc, r1sq.h, r1sq.l);
+    rec.r2 = make_float4(c.l, R12.l, Rm.l, 0.0f);
+    o.dyad[d] = rec;
+  }
+
+  h.nd = (uint8_t)nd;
+  h.nf = (uint8_t)nf;
+  h.motor_joint = (uint8_t)motor;
+  h.pivot_joint = (uint8_t)pivot;
+  h.pad0 = (uint8_t)slot_of[pivot];  // pivot slot
+  h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
+  h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
+  dw px = abs_dw(pos, 2 * pivot), py = abs_dw(pos, 2 * pivot + 1);
+  h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
+  h.bmax = bmax;
+  h.crank = crank;
+  h.e_motor = fmul(4.0f * kU, crank);
+  h.e_fixed = fmul(kU, bmax);
+  *o.hdr = h;
+  return status;
+}
+
+LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
+  BuildOut o;
+  o.hdr = p.hdr + b;
+  o.slot_joint = p.slot_joint + b * kMaxJ;
+  o.fixpos = p.fixpos + b * p.n_max;
+  o.pos64 = p.pos64 + b * p.n_max;
+  o.dyad = p.dyad + b * p.max_dyads;
+  return o;
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __restrict__ n_joints,
+                                                    const uint8_t* __restrict__ adj,
+                                                    const int8_t* __restrict__ type,
+                                                    const PT* __restrict__ pos, PlanDev p,
+                                                    int32_t* __restrict__ status_out) {
+  __shared__ int hist[32];
+  if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+  __syncthreads();
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < B) {
+    int n = n_joints[b];
+    int nm = p.n_max;
+    int st = build_one<PT>(n, nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2, out_of(p, b));
+    if (status_out) status_out[b] = st;
+    if (st == LINKS_MECH_OK) atomicAdd(&hist[p.hdr[b].nd], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
+}
+
+// Counting sort of the OK mechanisms by dyad count (a processing order only: warps then
+// meet mechanisms of equal length together).
+__global__ void __launch_bounds__(256) scatter_kernel(int64_t B, PlanDev p) {
+  __shared__ int off[32], cnt[32], base[32];
+  if (threadIdx.x < 32) {
+    int v = p.ctrs[kHist + threadIdx.x];
+    int incl = v;
+    for (int s = 1; s < 32; s <<= 1) {
+      int o = __shfl_up_sync(0xffffffffu, incl, s);
+      if ((int)threadIdx.x >= s) incl += o;
+    }
+    off[threadIdx.x] = incl - v;
+    cnt[threadIdx.x] = 0;
+  }
+  __syncthreads();
+  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int nd = -1, rank = 0;
+  if (b < B && p.hdr[b].status == LINKS_MECH_OK) {
+    nd = p.hdr[b].nd;
+    rank = atomicAdd(&cnt[nd], 1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && cnt[threadIdx.x]) base[threadIdx.x] = atomicAdd(&p.ctrs[kCursor + threadIdx.x], cnt[threadIdx.x]);
+  __syncthreads();
+  if (nd >= 0) p.order[off[nd] + base[nd] + rank] = (int32_t)b;
+}
+
+}  // namespace
+
+int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                      const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                      int32_t* status_out) {
+  PlanDev& p = plan->d;
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs, 0, kCtrs * sizeof(int32_t), ctx->stream));
+  plan->B = B;
+  if (B == 0) return LINKS_OK;
+  unsigned grid = (unsigned)((B + 255) / 256);
+  {
+  KernelScope ks(ctx, "plan_build");
+  if (pos_dtype == LINKS_F32)
+    build_kernel<float><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, (const float*)pos0, p, status_out);
+  else
+    build_kernel<double><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, (const double*)pos0, p, status_out);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  {
+    KernelScope ks(ctx, "plan_sort");
+    scatter_kernel<<<grid, 256, 0, ctx->stream>>>(B, p);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
+int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                    const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
+                    int32_t* status_out) {
+  PlanDev& p = plan->d;
+  const int nm = p.n_max;
+  std::vector<MechHdr> hdr(B);
+  std::vector<uint8_t> sj((size_t)B * kMaxJ, 0);
+  std::vector<float4> fix((size_t)B * nm, make_float4(0, 0, 0, 0));
+  std::vector<double2> p64((size_t)B * nm, make_double2(0, 0));
+  std::vector<DyadRec> dy((size_t)B * p.max_dyads, DyadRec{});
+  unsigned nth = std::max(1u, std::min(std::thread::hardware_concurrency(), 64u));
+  std::vector<std::thread> pool;
+  auto work = [&](int64_t lo, int64_t hi) {
+    for (int64_t b = lo; b < hi; ++b) {
+      BuildOut o{&hdr[b], &sj[b * kMaxJ], &fix[b * nm], &p64[b * nm], &dy[b * p.max_dyads]};
+      int st = pos_dtype == LINKS_F32
+                   ? build_one<float>(n_joints[b], nm, adj + b * nm * nm, type + b * nm,
+                                      (const float*)pos0 + b * nm * 2, o)
+                   : build_one<double>(n_joints[b], nm, adj + b * nm * nm, type + b * nm,
+                                       (const double*)pos0 + b * nm * 2, o);
+      if (status_out) status_out[b] = st;
+    }
+  };
+  int64_t chunk = (B + nth - 1) / nth;
+  for (unsigned t = 0; t < nth; ++t) {
+    int64_t lo = t * chunk, hi = std::min<int64_t>(B, lo + chunk);
+    if (lo < hi) pool.emplace_back(work, lo, hi);
+  }
+  for (auto& th : pool) th.join();
+  // Counting sort by dyad count (same property as the device scatter).
+  std::vector<int32_t> ctrs(kCtrs, 0), order;
+  for (int64_t b = 0; b < B; ++b)
+    if (hdr[b].status == LINKS_MECH_OK) ctrs[kHist + hdr[b].nd]++;
+  std::vector<int32_t> off(33, 0);
+  for (int i = 0; i < 32; ++i) off[i + 1] = off[i] + ctrs[kHist + i];
+  order.resize(off[32]);
+  std::vector<int32_t> cur(off.begin(), off.begin() + 32);
+  for (int64_t b = 0; b < B; ++b)
+    if (hdr[b].status == LINKS_MECH_OK) order[cur[hdr[b].nd]++] = (int32_t)b;
+  for (int i = 0; i < 32; ++i) ctrs[kCursor + i] = ctrs[kHist + i];
+  cudaStream_t s = ctx->stream;
+  plan->B = B;
+  if (B > 0) {
+    LINKS_CUDA(cudaMemcpyAsync(p.hdr, hdr.data(), B * sizeof(MechHdr), cudaMemcpyHostToDevice, s));
+    LINKS_CUDA(cudaMemcpyAsync(p.slot_joint, sj.data(), sj.size(), cudaMemcpyHostToDevice, s));
+    LINKS_CUDA(cudaMemcpyAsync(p.fixpos, fix.data(), fix.size() * sizeof(float4), cudaMemcpyHostToDevice, s));
+    LINKS_CUDA(cudaMemcpyAsync(p.pos64, p64.data(), p64.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+    LINKS_CUDA(cudaMemcpyAsync(p.dyad, dy.data(), dy.size() * sizeof(DyadRec), cudaMemcpyHostToDevice, s));
+    if (!order.empty())
+      LINKS_CUDA(cudaMemcpyAsync(p.order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  }
+  LINKS_CUDA(cudaMemcpyAsync(p.ctrs, ctrs.data(), kCtrs * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  LINKS_CUDA(cudaStreamSynchronize(s));
+  return LINKS_OK;
+}
+
+}  // namespace links

@@ -1,0 +1,311 @@
+// sim_mixed.cu -- mixed-precision simulation of planned mechanisms (LINKS_MIXED).
+//
+// What is computed (Sec. "Graphical Simulator"; Sec. "Finding Valid Initial Positions",
+// Infeasibility rule; Sec. "Dataset Features", item Simulation Data): at step t the
+// crank is turned by 2*pi*t/T about its pivot and each dyad joint k with parents i, j
+// is placed at the intersection of the circles |p - p_i| = r1 and |p - p_j| = r2 on the
+// branch of the initial configuration.  The step locks when a dyad has no
+// intersection.  Steps are independent of each other (the branch is fixed by the
+// initial positions), so lanes run different steps of the same mechanism.
+//
+// Two kernels:
+//   screen  FP32 dyads in product form, D = (d + R12)(R12 - d)(d - Rm)(d + Rm), with a
+//           per-joint forward error bound E (E_k = (E_i + E_j + local) / sin(gamma_k)).
+//           A step is certainly locked if some dyad has slack = min(R12 - d, d - Rm)
+//           < -(E_i + E_j + local), certainly free if every slack exceeds its bound; in
+//           between the lane recomputes the step in double-word arithmetic (~48 bits),
+//           which decides.  Groups of G lanes take consecutive steps of one mechanism,
+//           a ballot finds the first locking step, and the group moves on to the next
+//           mechanism of a work list sorted by dyad count.
+//   emit    every requested trajectory step in double-word arithmetic, written as
+//           float32 (one warp per output row, 32 consecutive steps per store).
+#include "links_internal.cuh"
+
+namespace links {
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
+constexpr int kBatch = 16;  // work items taken per atomic by a warp
+
+__device__ __forceinline__ float min_nan(float a, float b) {  // NaN-propagating min
+  float r;
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
+struct dwp {
+  dw x, y;
+};
+
+// Double-word chain of one step: positions relative to the pivot in loc[slot].
+// Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
+__device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* __restrict__ fix,
+                                      const DyadRec* __restrict__ dy, float4 csv, dwp* loc,
+                                      float* qmin) {
+  const int nf = h.nf, nd = h.nd;
+  for (int s = 0; s < nf; ++s) {
+    float4 f = __ldg(fix + s);
+    loc[s] = {{f.x, f.y}, {f.z, f.w}};
+  }
+  dw c = {csv.x, csv.y}, s = {csv.z, csv.w};
+  dw ux = {h.ux_h, h.ux_l}, uy = {h.uy_h, h.uy_l};
+  loc[nf] = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
+  float q = INFINITY;
+  for (int d = 0; d < nd; ++d) {
+    float4 r0 = __ldg(&dy[d].r0), r1 = __ldg(&dy[d].r1), r2 = __ldg(&dy[d].r2);
+    uint32_t sl = __float_as_uint(r0.x);
+    const dwp pi = loc[sl & 0xff], pj = loc[(sl >> 8) & 0xff];
+    dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
+    dw d2 = dw_add(dw_sqr(dx), dw_sqr(dy_));
+    dw e = dw_add(d2, dw{r0.w, r2.x});
+    dw D = dw_sub(dw_scale2(dw_mul(d2, dw{r1.z, r1.w}), 4.0f), dw_sqr(e));
+    if (!(dw_sign(D) > 0.0f)) {
+      *qmin = q;
+      return true;
+    }
+    q = fminf(q, __fdividef(D.h, r1.x * r1.x));
+    dw sq = dw_sqrt(D);
+    dw hinv = dw_scale2(dw_rcp(d2), 0.5f);
+    dw a = dw_mul(e, hinv), bq = dw_mul(sq, hinv);
+    dwp pk;
+    pk.x = dw_add(pi.x, dw_sub(dw_mul(a, dx), dw_mul(bq, dy_)));
+    pk.y = dw_add(pi.y, dw_add(dw_mul(a, dy_), dw_mul(bq, dx)));
+    loc[sl >> 24] = pk;
+  }
+  *qmin = q;
+  return false;
+}
+
+template <int G>
+__global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
+                                                        uint8_t* __restrict__ valid,
+                                                        int16_t* __restrict__ lock_step,
+                                                        float* __restrict__ min_disc) {
+  extern __shared__ float4 smem4[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ns = p.n_max;
+  float2* P = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384) + lane;
+  float* E = reinterpret_cast<float*>(reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384 + ns * 256) + lane;
+  const int g = lane / G, gl = lane % G;
+  const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
+
+  int n_ok = p.ctrs[kHist + lane];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(kFull, n_ok, o);
+
+  int qhead = 0, qend = 0;
+  bool exhausted = false;
+  int item = -1, chunk = 0;
+  int64_t b = 0;
+  MechHdr h{};
+  float qacc = INFINITY;
+
+  while (true) {
+    // Give every idle group the next mechanism of the work list.
+    unsigned need = __ballot_sync(kFull, gl == 0 && item < 0);
+    bool fresh = false;
+    while (need) {
+      if (qhead >= qend) {
+        if (exhausted) break;
+        int base = 0;
+        if (lane == 0) base = atomicAdd(&p.ctrs[kWork], kBatch);
+        base = __shfl_sync(kFull, base, 0);
+        if (base >= n_ok) { exhausted = true; break; }
+        qhead = base;
+        qend = min(base + kBatch, n_ok);
+      }
+      int leader = __ffs(need) - 1;
+      need &= need - 1;
+      if (g == leader / G) { item = qhead; fresh = true; }
+      ++qhead;
+    }
+    if (__ballot_sync(kFull, item >= 0) == 0) break;
+
+    if (fresh) {
+      b = p.order[item];
+      h = p.hdr[b];
+      chunk = 0;
+      qacc = INFINITY;
+      const float4* fix = p.fixpos + b * ns;
+      for (int s = 0; s < h.nf; ++s) {
+        float4 f = __ldg(fix + s);
+        P[s * 32] = make_float2(f.x, f.z);
+        E[s * 32] = h.e_fixed;
+      }
+    }
+    const bool has = item >= 0;
+    const int t = chunk * G + gl;
+    const bool act = has && t < T;
+    const int nd = has ? h.nd : 0;
+    const int nf = h.nf;
+    float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f;
+    if (has) {
+      float4 csv = __ldg(cs + min(t, T - 1));
+      P[nf * 32] = make_float2(csv.x * h.ux_h - csv.z * h.uy_h, csv.z * h.ux_h + csv.x * h.uy_h);
+      E[nf * 32] = h.e_motor;
+    }
+    const int ndw = __reduce_max_sync(kFull, (unsigned)nd);
+    const DyadRec* dy = p.dyad + b * p.max_dyads;
+    for (int d = 0; d < ndw; ++d) {
+      if (d < nd) {
+        float4 r0 = __ldg(&dy[d].r0), r1 = __ldg(&dy[d].r1);
+        uint32_t sl = __float_as_uint(r0.x);
+        int si = sl & 0xff, sj = (sl >> 8) & 0xff, sk = sl >> 24;
+        float2 pi = P[si * 32], pj = P[sj * 32];
+        float ei = E[si * 32], ej = E[sj * 32];
+        float dx = pj.x - pi.x, dy_ = pj.y - pi.y;
+        float d2 = fmaf(dx, dx, dy_ * dy_);
+        float rd = rsqrtf(d2);
+        float dd = d2 * rd;
+        float s2 = r0.y - dd, s3 = dd - r0.z;
+        float D = ((dd + r0.y) * s2) * (s3 * (dd + r0.z));
+        float rD = rsqrtf(D);
+        float isg = r1.x * rD;
+        float del = ei + ej + r1.y;
+        float slack = fminf(s2, s3);
+        lockw = fminf(lockw, slack + del);
+        zmin = min_nan(zmin, slack - del);
+        isgmax = fmaxf(isgmax, isg);
+        float hinv = 0.5f * (rd * rd);
+        float a = (d2 + r0.w) * hinv, bq = (D * rD) * hinv;
+        P[sk * 32] = make_float2(fmaf(a, dx, fmaf(-bq, dy_, pi.x)), fmaf(a, dy_, fmaf(bq, dx, pi.y)));
+        E[sk * 32] = del * isg;
+      }
+    }
+    const bool certain_lock = lockw < 0.0f;
+    const bool amb = act && !certain_lock && !(zmin >= 0.0f);
+    float qstep = __frcp_rn(isgmax * isgmax);
+    bool locked = act && certain_lock;
+    if (amb) {
+      dwp loc[kMaxJ];
+      float qd;
+      locked = dw_chain(h, p.fixpos + b * ns, dy, __ldg(cs + t), loc, &qd);
+      qstep = qd;
+    }
+    const unsigned lb = __ballot_sync(kFull, locked) & gmask;
+    const int first = lb ? (__ffs(lb) - 1 - g * G) : G;
+    if (act && gl < first) qacc = fminf(qacc, qstep);
+    const bool done = has && (lb != 0 || (chunk + 1) * G >= T);
+    if (done) {
+      float qr = qacc;
+#pragma unroll
+      for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(gmask, qr, o));
+      if (gl == 0) {
+        valid[b] = lb == 0;
+        lock_step[b] = (int16_t)(lb ? chunk * G + first : -1);
+        min_disc[b] = qr;
+      }
+      item = -1;
+    } else {
+      ++chunk;
+    }
+  }
+}
+
+// One warp per output row; 32 consecutive steps per pass.
+__global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int T, const float4* __restrict__ cs,
+                                                      int full, const int16_t* __restrict__ lock_step,
+                                                      const int32_t* __restrict__ out_index,
+                                                      int64_t out_capacity, float* __restrict__ traj,
+                                                      float* __restrict__ path, int32_t* err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int ns = p.n_max;
+  int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
+  const float nanf_ = __int_as_float(0x7fc00000);
+  for (int64_t r = gw; r < rows; r += nw) {
+    const int64_t b = full ? r : (int64_t)out_index[r];
+    if (b < 0 || b >= B) {
+      if (lane == 0) atomicOr(err, kErrBadIndex);
+      continue;
+    }
+    const MechHdr h = p.hdr[b];
+    const bool ok = h.status == LINKS_MECH_OK;
+    const int n = ok ? h.n : 0;
+    int lock = T;
+    if (full) lock = ok ? (lock_step[b] < 0 ? T : lock_step[b]) : 0;
+    const uint8_t* sj = p.slot_joint + b * kMaxJ;
+    float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
+    float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
+    const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
+    for (int t0 = 0; t0 < T; t0 += 32) {
+      const int t = t0 + lane;
+      if (t >= T) continue;
+      if (t < lock) {
+        dwp loc[kMaxJ];
+        float qd;
+        bool lk = dw_chain(h, p.fixpos + b * ns, p.dyad + b * p.max_dyads, __ldg(cs + t), loc, &qd);
+        if (lk) atomicOr(err, kErrEmitLock);
+        const int nslot = h.nf + 1 + h.nd;
+        for (int s = 0; s < nslot; ++s) {
+          float2 v = lk ? make_float2(nanf_, nanf_)
+                        : make_float2(dw_add(px, loc[s].x).h, dw_add(py, loc[s].y).h);
+          if (trow) trow[(int64_t)sj[s] * T + t] = v;
+          if (prow && s == h.coupler_slot) prow[t] = v;
+        }
+      } else {
+        for (int s = 0; s < n; ++s)
+          if (trow) trow[(int64_t)sj[s] * T + t] = make_float2(nanf_, nanf_);
+        if (prow) prow[t] = make_float2(nanf_, nanf_);
+      }
+      for (int j = n; j < ns; ++j)
+        if (trow) trow[(int64_t)j * T + t] = make_float2(nanf_, nanf_);
+    }
+  }
+}
+
+template <int G>
+int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
+                  int16_t* lock_step, float* min_disc) {
+  PlanDev& p = plan->d;
+  size_t smem = (size_t)kWarps * p.n_max * 384;
+  static bool attr_set = false;
+  if (!attr_set) {
+    LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    attr_set = true;
+  }
+  int per_sm = 0;
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G>, kBlock, smem));
+  if (per_sm < 1) per_sm = 1;
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
+  {
+    KernelScope ks(ctx, "mixed_screen");
+    screen_kernel<G><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(p, T, tab->cs, valid, lock_step, min_disc);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
+}  // namespace
+
+int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
+                   float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
+                   int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
+  const int64_t B = plan->B;
+  const int T = tab->T;
+  int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
+  if (st) return st;
+  st = launch_screen<8>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  if (st) return st;
+  const bool full = out_mode == LINKS_OUT_FULL;
+  if (!full) {
+    st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
+    if (st) return st;
+  }
+  if (traj || path) {
+    int per_sm = 0;
+    LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel, kBlock, 0));
+    if (per_sm < 1) per_sm = 1;
+    KernelScope ks(ctx, "mixed_emit");
+    emit_kernel<<<ctx->num_sms * per_sm, kBlock, 0, ctx->stream>>>(plan->d, B, T, tab->cs, full ? 1 : 0,
+                                                                   lock_step, out_index, out_capacity,
+                                                                   traj, path, ctx->d_err);
+    LINKS_CUDA(cudaGetLastError());
+  }
+  return LINKS_OK;
+}
+
+}  // namespace links

@@ -1,0 +1,248 @@
+"""Thin ctypes binding of the C ABI in include/links.h (same names, argument marshalling only).
+
+Device buffers are torch CUDA tensors (PyTorch provides memory and streams); every
+step of the computation runs in the library's CUDA kernels.  Importing this module
+does not load the library; the first call does, and raises if the library has not
+been built -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "liblinks.so")
+
+# Mirrors of the #defines in include/links.h.
+OK, EINVAL, ECUDA, ENOMEM, ECAPACITY, EBUSY, ETIMEDOUT, ESTATE, EDEVICE = range(9)
+MECH_OK, MECH_BAD_SIZE, MECH_BAD_TYPE, MECH_BAD_ADJ, MECH_NO_MOTOR, MECH_NO_PIVOT, \
+    MECH_NOT_DYAD_SOLVABLE, MECH_OVERCONSTRAINED = range(8)
+F32, F64 = 0, 1
+PLAIN_F64, MIXED = 0, 1
+OUT_FULL, OUT_VALID_ONLY = 0, 1
+MAX_JOINTS, MAX_T = 32, 32767
+
+_lib = None
+
+
+class LinksError(RuntimeError):
+    def __init__(self, status: int, what: str, detail: str):
+        super().__init__(f"{what} failed: {strerror(status)}: {detail}")
+        self.status = status
+
+
+def lib():
+    """The loaded CUDA library (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built ({LIB_PATH} missing): run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        sig = {
+            "links_last_error": ([], ctypes.c_char_p),
+            "links_strerror": ([i32], ctypes.c_char_p),
+            "links_create": ([P, i32, P], i32),
+            "links_destroy": ([P], i32),
+            "links_set_stream": ([P, P], i32),
+            "links_sync": ([P], i32),
+            "links_prepare": ([P, i32], i32),
+            "links_plan_create": ([P, i64, i32, P], i32),
+            "links_plan_free": ([P], i32),
+            "links_plan_build": ([P, P, i64, P, P, P, P, i32, P], i32),
+            "links_plan_build_host": ([P, P, i64, P, P, P, P, i32, P], i32),
+            "links_plan_info": ([P, P, P, P], i32),
+            "links_plan_export": ([P, i64, i64, P, P], i32),
+            "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
+            "links_profile": ([P, i32], i32),
+            "links_profile_read": ([P, i32, P, P, P, P], i32),
+            "links_launch_count": ([P, P], i32),
+            "links_capture_begin": ([P], i32),
+            "links_capture_end": ([P, P], i32),
+            "links_graph_launch": ([P, P], i32),
+            "links_graph_free": ([P], i32),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = args, res
+        _lib = L
+    return _lib
+
+
+def strerror(status: int) -> str:
+    return lib().links_strerror(int(status)).decode()
+
+
+def links_last_error() -> str:
+    return lib().links_last_error().decode()
+
+
+def _check(status: int, what: str):
+    if status != OK:
+        raise LinksError(status, what, links_last_error())
+
+
+def _dev(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (or None)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host(a, dtype=None, name="array"):
+    """Host pointer of a C-contiguous numpy array (or None)."""
+    import numpy as np
+    if a is None:
+        return None
+    if not (isinstance(a, np.ndarray) and a.flags.c_contiguous):
+        raise ValueError(f"{name} must be a C-contiguous numpy array")
+    if dtype is not None and a.dtype != dtype:
+        raise ValueError(f"{name} must be {np.dtype(dtype)}, got {a.dtype}")
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ----------------------------------------------------------------------- C-ABI calls
+
+def links_create(device: int = 0, stream=None):
+    out = ctypes.c_void_p()
+    _check(lib().links_create(ctypes.byref(out), int(device), _stream_handle(stream)), "links_create")
+    return out
+
+
+def links_destroy(ctx):
+    _check(lib().links_destroy(ctx), "links_destroy")
+
+
+def links_set_stream(ctx, stream):
+    _check(lib().links_set_stream(ctx, _stream_handle(stream)), "links_set_stream")
+
+
+def links_sync(ctx):
+    _check(lib().links_sync(ctx), "links_sync")
+
+
+def links_prepare(ctx, T: int):
+    _check(lib().links_prepare(ctx, int(T)), "links_prepare")
+
+
+def links_plan_create(ctx, capacity: int, n_max: int):
+    out = ctypes.c_void_p()
+    _check(lib().links_plan_create(ctx, int(capacity), int(n_max), ctypes.byref(out)), "links_plan_create")
+    return out
+
+
+def links_plan_free(plan):
+    _check(lib().links_plan_free(plan), "links_plan_free")
+
+
+def _pos_dtype(t):
+    import torch
+    import numpy as np
+    if t.dtype in (torch.float32, np.float32):
+        return F32
+    if t.dtype in (torch.float64, np.float64):
+        return F64
+    raise ValueError("pos0 must be float32 or float64")
+
+
+def links_plan_build(ctx, plan, n_joints, adj, jtype, pos0, status_out=None):
+    """Device build: torch CUDA tensors int32 [B], uint8 [B,n,n], int8 [B,n], float32|64 [B,n,2]."""
+    import torch
+    B = n_joints.shape[0]
+    _check(lib().links_plan_build(ctx, plan, int(B), _dev(n_joints, torch.int32, "n_joints"),
+                                  _dev(adj, torch.uint8, "adj"), _dev(jtype, torch.int8, "type"),
+                                  _dev(pos0, None, "pos0"), _pos_dtype(pos0),
+                                  _dev(status_out, torch.int32, "status_out")), "links_plan_build")
+
+
+def links_plan_build_host(ctx, plan, n_joints, adj, jtype, pos0, status_out=None):
+    """Host build: numpy arrays with the dtypes of links_plan_build."""
+    import numpy as np
+    B = n_joints.shape[0]
+    _check(lib().links_plan_build_host(ctx, plan, int(B), _host(n_joints, np.int32, "n_joints"),
+                                       _host(adj, np.uint8, "adj"), _host(jtype, np.int8, "type"),
+                                       _host(pos0, None, "pos0"), _pos_dtype(pos0),
+                                       _host(status_out, np.int32, "status_out")), "links_plan_build_host")
+
+
+def links_plan_info(plan):
+    B, nm, cap = ctypes.c_int64(), ctypes.c_int(), ctypes.c_int64()
+    _check(lib().links_plan_info(plan, ctypes.byref(B), ctypes.byref(nm), ctypes.byref(cap)), "links_plan_info")
+    return B.value, nm.value, cap.value
+
+
+def links_plan_export(plan, b0: int, count: int, with_lengths: bool = True):
+    """-> (topo int32 [count, 6 + 3 (n_max-2)], lengths float64 [count, 2 (n_max-2)] or None)."""
+    import numpy as np
+    _, nm, _ = links_plan_info(plan)
+    md = max(nm - 2, 0)
+    topo = np.empty((count, 6 + 3 * md), np.int32)
+    lengths = np.empty((count, 2 * md), np.float64) if with_lengths else None
+    _check(lib().links_plan_export(plan, int(b0), int(count), _host(topo), _host(lengths)), "links_plan_export")
+    return topo, lengths
+
+
+def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path, valid, lock_step, min_disc,
+                   out_index=None, out_capacity: int = 0, n_out=None):
+    import torch
+    fdt = torch.float64 if precision == PLAIN_F64 else torch.float32
+    _check(lib().links_simulate(ctx, plan, int(T), int(precision), int(out_mode), _dev(traj, fdt, "traj"),
+                                _dev(path, fdt, "path"), _dev(valid, torch.uint8, "valid"),
+                                _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
+                                _dev(out_index, torch.int32, "out_index"), int(out_capacity),
+                                _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_profile(ctx, enable: bool):
+    _check(lib().links_profile(ctx, 1 if enable else 0), "links_profile")
+
+
+def links_profile_read(ctx, max_entries: int = 64):
+    """-> {kernel name: (total milliseconds, launches)}."""
+    import numpy as np
+    names = ctypes.create_string_buffer(32 * max_entries)
+    ms = np.zeros(max_entries, np.float64)
+    nl = np.zeros(max_entries, np.int64)
+    cnt = ctypes.c_int()
+    _check(lib().links_profile_read(ctx, max_entries, names, _host(ms), _host(nl), ctypes.byref(cnt)),
+           "links_profile_read")
+    raw = names.raw
+    return {raw[32 * i: 32 * i + 32].split(b"\0")[0].decode(): (float(ms[i]), int(nl[i])) for i in range(cnt.value)}
+
+
+def links_launch_count(ctx) -> int:
+    out = ctypes.c_int64()
+    _check(lib().links_launch_count(ctx, ctypes.byref(out)), "links_launch_count")
+    return out.value
+
+
+def links_capture_begin(ctx):
+    _check(lib().links_capture_begin(ctx), "links_capture_begin")
+
+
+def links_capture_end(ctx):
+    out = ctypes.c_void_p()
+    _check(lib().links_capture_end(ctx, ctypes.byref(out)), "links_capture_end")
+    return out
+
+
+def links_graph_launch(ctx, graph):
+    _check(lib().links_graph_launch(ctx, graph), "links_graph_launch")
+
+
+def links_graph_free(graph):
+    _check(lib().links_graph_free(graph), "links_graph_free")

@@ -1,0 +1,316 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances (restated in the design doc):
+  * plan: statuses, solve order and parents bit-exact; lengths within 1e-14 relative;
+    host and device builders bit-identical;
+  * valid / lock_step: identical, except mechanisms whose oracle margin indicator
+    min |q| over the evaluated dyads is <= MARGIN (counted and printed);
+  * positions: LINKS_MIXED within 1e-5 of the bounding-box diagonal L at every step
+    both sides simulated; LINKS_PLAIN_F64 within 1e-9 L where the oracle's
+    min_disc > 1e-8 and within 1e-5 L elsewhere;
+  * NaN exactly from the locking step on and for padding joints.
+"""
+import numpy as np
+import pytest
+
+from conftest import bbox_diag
+from oracle import oracle as O
+from paper_2208_14567_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MARGIN = 1e-9
+TOL_MIXED = 1e-5
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_14567_gb300 import links
+    links.lib()
+    return links
+
+
+def sim_for(batch, L):
+    from paper_2208_14567_gb300.api import Simulator
+    return Simulator(max(batch.B, 1), batch.nmax)
+
+
+def run(batch, T, precision, out_mode, L, host_build=False, out_capacity=None):
+    from paper_2208_14567_gb300.api import to_device
+    s = sim_for(batch, L)
+    try:
+        if host_build:
+            st = s.build_host(batch)
+        else:
+            st = s.build(to_device(batch)).cpu().numpy()
+        o = s.simulate(T, precision, out_mode, out_capacity=out_capacity)
+        s.sync()
+        if out_mode == L.OUT_VALID_ONLY:  # copy back only the written rows
+            rows = min(int(o.n_out[0]), o.traj.shape[0])
+            o.traj, o.path = o.traj[:rows], o.path[:rows]
+        res = {k: (None if v is None else v.cpu().numpy()) for k, v in o.__dict__.items()}
+        res["status"] = st
+        return res
+    finally:
+        s.close()
+
+
+def check_flags(res, ref, label):
+    margin = ~(ref.min_abs_q > MARGIN)
+    mism = (res["valid"] != ref.valid) | (res["lock_step"] != ref.lock_step)
+    bad = mism & ~margin
+    print(f"[{label}] mechanisms {len(ref.valid)} valid {ref.valid.mean():.4f} margin cases {int(margin.sum())} "
+          f"flag mismatches in margin {int((mism & margin).sum())}")
+    assert not bad.any(), f"{int(bad.sum())} flag mismatches outside the margin, e.g. {np.nonzero(bad)[0][:5]}"
+    return mism
+
+
+def check_positions(batch, traj, path, ref, lock_gpu, tol, label, tight=None):
+    Ld = bbox_diag(batch.pos, batch.n_joints)
+    T = traj.shape[2]
+    B, nm = batch.B, batch.nmax
+    lr = np.where(ref.lock_step < 0, T, np.maximum(ref.lock_step, 0))
+    lg = np.where(lock_gpu < 0, T, np.maximum(lock_gpu, 0))
+    stop = np.minimum(lr, lg)
+    tmask = np.arange(T)[None, :] < stop[:, None]
+    jmask = np.arange(nm)[None, :] < batch.n_joints[:, None]
+    ok = ref.status == 0
+    err = np.abs(traj.astype(np.float64) - ref.traj).max(-1)  # [B, nm, T]
+    m = ok[:, None, None] & jmask[:, :, None] & tmask[:, None, :]
+    e = np.where(ok, np.where(m, err, 0.0).max((1, 2)) / np.where(ok, Ld, 1.0), 0.0)
+    assert np.isfinite(e[ok]).all()
+    print(f"[{label}] max position error / L = {e.max():.3e}")
+    lim = np.full(B, tol) if tight is None else tight
+    assert (e <= lim).all(), f"worst mechanism {int(e.argmax())}: {e.max():.3e}"
+    # NaN from the GPU's lock step on (its own flags), and for padding joints
+    gl = np.where(lock_gpu < 0, T, np.maximum(lock_gpu, 0))
+    after = np.arange(T)[None, :] >= gl[:, None]
+    nanm = (after[:, None, :] & jmask[:, :, None]) | ~jmask[:, :, None] | ~ok[:, None, None]
+    assert np.isnan(traj[nanm]).all()
+    assert not np.isnan(traj[~nanm]).any()
+    # the path is the coupler joint's trajectory
+    perr = np.abs(path.astype(np.float64) - ref.path).max(-1)
+    pm = ok[:, None] & tmask
+    assert (np.where(ok, np.where(pm, perr, 0).max(1) / np.where(ok, Ld, 1.0), 0.0) <= lim).all()
+
+
+def tight_f64(ref, B):
+    return np.where(ref.min_disc > 1e-8, 1e-9, TOL_MIXED)
+
+
+# ------------------------------------------------------------------------------- plan
+
+def planted_bad(batch):
+    """Copy of a batch with every status code planted in the first rows."""
+    b = I.MechBatch(batch.n_joints.copy(), batch.adj.copy(), batch.jtype.copy(), batch.pos.copy())
+    b.n_joints[0] = 1                       # BAD_SIZE
+    b.jtype[1, 3] = 5                       # BAD_TYPE
+    b.adj[2, 3, 4] = 1 - b.adj[2, 3, 4]     # BAD_ADJ (asymmetric)
+    b.jtype[3, b.jtype[3] == 2] = 1         # NO_MOTOR
+    m = int(np.nonzero(b.jtype[4] == 2)[0][0])
+    for a in range(b.nmax):
+        if b.jtype[4, a] == 0:
+            b.adj[4, m, a] = b.adj[4, a, m] = 0  # NO_PIVOT
+    b.adj[5, :, :] = 0                       # every simple joint dangling -> NOT_DYAD_SOLVABLE
+    m = int(np.nonzero(b.jtype[5] == 2)[0][0])
+    f = int(np.nonzero(b.jtype[5] == 0)[0][0])
+    b.adj[5, m, f] = b.adj[5, f, m] = 1
+    n = b.n_joints[6]                        # extra link -> OVERCONSTRAINED
+    for x in range(n):
+        for y in range(x + 1, n):
+            if not b.adj[6, x, y] and not (b.jtype[6, x] == 0 and b.jtype[6, y] == 0):
+                b.adj[6, x, y] = b.adj[6, y, x] = 1
+                break
+        else:
+            continue
+        break
+    return b
+
+
+def test_plan_matches_oracle_device_and_host(L):
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = planted_bad(I.dyad_batch(3000, 6, 16, seed=2, permute=True, nmax=20))
+    with Simulator(batch.B, batch.nmax) as s:
+        st_dev = s.build(to_device(batch)).cpu().numpy()
+        topo_d, len_d = L.links_plan_export(s.plan, 0, batch.B)
+        st_host = s.build_host(batch)
+        topo_h, len_h = L.links_plan_export(s.plan, 0, batch.B)
+    assert np.array_equal(st_dev, st_host)
+    assert np.array_equal(topo_d, topo_h)
+    assert np.array_equal(len_d, len_h, equal_nan=True)
+    seen = set()
+    for m in range(batch.B):
+        P = O.plan(batch.n_joints[m], batch.adj[m], batch.jtype[m], batch.pos[m].astype(np.float64))
+        assert st_dev[m] == P.status
+        seen.add(P.status)
+        if P.status:
+            continue
+        t = topo_d[m]
+        assert (t[2], t[3], t[4], t[5]) == (P.motor, P.pivot, P.coupler, P.n_dyads)
+        for d in range(P.n_dyads):
+            k, i, j = t[6 + 3 * d: 9 + 3 * d]
+            exp = (P.i[d], P.j[d]) if P.s[d] > 0 else (P.j[d], P.i[d])
+            assert (k, i, j) == (P.k[d], *exp)
+            r1, r2 = (P.r1sq[d], P.r2sq[d]) if P.s[d] > 0 else (P.r2sq[d], P.r1sq[d])
+            assert abs(len_d[m, 2 * d] - r1) <= 1e-14 * r1 and abs(len_d[m, 2 * d + 1] - r2) <= 1e-13 * max(r2, r1)
+    assert seen == set(range(8))
+
+
+# ------------------------------------------------------------------------ simulation
+
+def test_plain_f64_fourbars_full(L):
+    """4096 random four-bars, FP64 inputs, FULL output (the plain-method configuration)."""
+    batch = I.fourbar_batch(4096, seed=0)
+    ref = O.simulate(batch, 200)
+    res = run(batch, 200, L.PLAIN_F64, L.OUT_FULL, L)
+    check_flags(res, ref, "f64 four-bars")
+    check_positions(batch, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, "f64 four-bars",
+                    tight=tight_f64(ref, batch.B))
+    assert np.abs(res["min_disc"][ref.valid == 1] - ref.min_disc[ref.valid == 1]).max() < 1e-6
+
+
+@pytest.mark.parametrize("case", ["fourbar", "dyad6-8", "dyad6-20-permuted", "dyad-host-build"])
+def test_mixed_full_matches_oracle(L, case):
+    if case == "fourbar":
+        batch = I.fourbar_batch(4096, seed=1)
+    elif case == "dyad6-8":
+        batch = I.dyad_batch(6000, 6, 8, seed=3)
+    else:
+        batch = I.dyad_batch(4000, 6, 20, seed=4, permute=True)
+    T = 200
+    ref = O.simulate(batch, T)
+    res = run(batch, T, L.MIXED, L.OUT_FULL, L, host_build=case == "dyad-host-build")
+    check_flags(res, ref, case)
+    check_positions(batch, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, case)
+    # min_disc comes from the FP32 screen (double-word on rescued steps): absolute error
+    ok = (ref.status == 0) & (ref.lock_step != 0) & (res["lock_step"] == ref.lock_step)
+    dq = np.abs(res["min_disc"][ok] - ref.min_disc[ok])
+    print(f"[{case}] max |min_disc - oracle| = {dq.max():.3e}")
+    assert (dq <= 1e-4 + 1e-3 * ref.min_disc[ok]).all()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_valid_only_rows(L, precision):
+    p = L.MIXED if precision == "mixed" else L.PLAIN_F64
+    batch = I.dyad_batch(5000, 6, 10, seed=5)
+    full = run(batch, 128, p, L.OUT_FULL, L)
+    vo = run(batch, 128, p, L.OUT_VALID_ONLY, L)
+    idx = np.nonzero(full["valid"])[0]
+    n = int(vo["n_out"][0])
+    assert n == len(idx) and np.array_equal(vo["out_index"][:n], idx)
+    assert np.array_equal(vo["traj"][:n], full["traj"][idx], equal_nan=True)
+    assert np.array_equal(vo["path"][:n], full["path"][idx], equal_nan=True)
+    assert np.array_equal(vo["valid"], full["valid"]) and np.array_equal(vo["lock_step"], full["lock_step"])
+    # capacity below the number of valid rows: only the first rows are written
+    cap = max(1, n // 3)
+    part = run(batch, 128, p, L.OUT_VALID_ONLY, L, out_capacity=cap)
+    assert int(part["n_out"][0]) == n
+    assert np.array_equal(part["out_index"][:cap], idx[:cap])
+    assert np.array_equal(part["traj"][:cap], full["traj"][idx[:cap]], equal_nan=True)
+
+
+@pytest.mark.parametrize("T", [1, 7, 33, 64])
+def test_ragged_steps_and_statuses(L, T):
+    batch = planted_bad(I.dyad_batch(700, 6, 12, seed=6, permute=True))
+    ref = O.simulate(batch, T)
+    for p in (L.MIXED, L.PLAIN_F64):
+        res = run(batch, T, p, L.OUT_FULL, L)
+        assert np.array_equal(res["status"], ref.status)
+        bad = ref.status != 0
+        assert (res["valid"][bad] == 0).all() and (res["lock_step"][bad] == -2).all()
+        assert np.isnan(res["min_disc"][bad]).all()
+        check_flags(res, ref, f"T={T}")
+        check_positions(batch, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, f"T={T}")
+
+
+def test_empty_single_and_largest_mechanisms(L):
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    empty = I.dyad_batch(1, 6, 6, seed=0).slice(0, 0)
+    with Simulator(4, 6) as s:
+        s.build(to_device(empty))
+        o = s.simulate(16, L.MIXED, L.OUT_VALID_ONLY)
+        s.sync()
+        assert int(o.n_out[0]) == 0
+    one = I.dyad_batch(1, 7, 7, seed=9)
+    ref = O.simulate(one, 50)
+    res = run(one, 50, L.MIXED, L.OUT_FULL, L)
+    check_positions(one, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, "B=1")
+    big = I.dyad_batch(200, 32, 32, seed=10, nmax=32)   # n_max = LINKS_MAX_JOINTS
+    ref = O.simulate(big, 40)
+    for p in (L.MIXED, L.PLAIN_F64):
+        res = run(big, 40, p, L.OUT_FULL, L)
+        check_flags(res, ref, "n=32")
+        check_positions(big, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, "n=32")
+    # only the crank: never locks, the coupler is the actuated joint
+    adj = np.zeros((1, 3, 3), np.uint8)
+    adj[0, 0, 1] = adj[0, 1, 0] = 1
+    crank = I.MechBatch(np.array([3], np.int32), adj, np.array([[0, 2, 0]], np.int8),
+                        np.array([[[0.5, 0.5], [0.6, 0.5], [0.1, 0.9]]], np.float32))
+    ref = O.simulate(crank, 20)
+    res = run(crank, 20, L.MIXED, L.OUT_FULL, L)
+    assert res["valid"][0] == 1 and np.abs(res["path"][0] - ref.path[0]).max() < 1e-6
+
+
+def test_too_large_batch_is_rejected(L):
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.dyad_batch(10, 6, 6, seed=0)
+    with Simulator(5, 6) as s:
+        with pytest.raises(L.LinksError) as e:
+            s.build(to_device(batch))
+        assert e.value.status == L.ECAPACITY
+
+
+def test_graph_replay_and_determinism(L):
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    a = I.dyad_batch(3000, 6, 8, seed=11)
+    b = I.dyad_batch(3000, 6, 8, seed=12)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with Simulator(3000, 8, stream=stream) as s:
+            db = to_device(a)
+            out = s.alloc(200, L.MIXED, L.OUT_VALID_ONLY)
+            status = torch.empty(3000, dtype=torch.int32, device="cuda")
+            L.links_prepare(s.ctx, 200)
+            L.links_capture_begin(s.ctx)
+            s.build(db, status)
+            s.simulate(200, L.MIXED, L.OUT_VALID_ONLY, out=out)
+            g = L.links_capture_end(s.ctx)
+            results = []
+            for src in (a, b, a):
+                for dst, x in zip((db.n_joints, db.adj, db.jtype, db.pos), (src.n_joints, src.adj, src.jtype, src.pos)):
+                    dst.copy_(torch.from_numpy(np.ascontiguousarray(x)))
+                L.links_graph_launch(s.ctx, g)
+                s.sync()
+                n = int(out.n_out[0])
+                results.append((out.valid.cpu().numpy(), out.traj[:n].cpu().numpy()))
+            L.links_graph_free(g)
+    direct = run(b, 200, L.MIXED, L.OUT_VALID_ONLY, L)
+    n = int(direct["n_out"][0])
+    assert np.array_equal(results[1][0], direct["valid"])
+    assert np.array_equal(results[1][1], direct["traj"][:n], equal_nan=True)
+    assert np.array_equal(results[0][0], results[2][0])
+    assert np.array_equal(results[0][1], results[2][1], equal_nan=True)
+
+
+@pytest.mark.slow
+def test_full_size_one_million_candidates(L):
+    """1M candidates of 6-8 joints, T = 200, LINKS_MIXED with VALID_ONLY rows: the
+    launch configuration bench.py times.  Flags of all 1M against the oracle,
+    trajectories of 3000 sampled valid rows."""
+    batch = I.dyad_batch(1 << 20, 6, 8, seed=0)
+    ref = O.simulate(batch, 200, traj=False, path=False)
+    res = run(batch, 200, L.MIXED, L.OUT_VALID_ONLY, L)
+    check_flags(res, ref, "1M mixed")
+    n = int(res["n_out"][0])
+    assert np.array_equal(res["out_index"][:n], np.nonzero(res["valid"])[0])
+    rng = np.random.default_rng(0)
+    rows = np.sort(rng.choice(n, size=min(3000, n), replace=False))
+    sub = batch.take(res["out_index"][rows])
+    rs = O.simulate(sub, 200)
+    check_positions(sub, res["traj"][rows], res["path"][rows], rs, np.full(len(rows), -1, np.int16),
+                    TOL_MIXED, "1M sampled rows")
+    f64 = run(batch, 200, L.PLAIN_F64, L.OUT_VALID_ONLY, L)
+    check_flags(f64, ref, "1M f64")
