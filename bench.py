@@ -200,7 +200,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
     sim = Simulator(B, nmax, device=local, stream=stream)
     status = torch.empty(B, dtype=torch.int32, device=dev)
-    out = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY)
+    # size the valid rows from a flags-only pass (the same inputs are reused every step)
+    sim.build(db, status)
+    probe = sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+    sim.sync()
+    out = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=int(probe.n_out[0]) + 1024)
+    del probe
 
     def step():
         sim.build(db, status)
