@@ -172,6 +172,24 @@ LINKS_API int links_profile_read(links_ctx ctx, int max, char* names, double* to
 /* Number of kernels the library has launched through ctx since it was created. */
 LINKS_API int links_launch_count(links_ctx ctx, int64_t* out);
 
+/* Valid-row compaction that allocates nothing (no counterpart in the paper; it
+ * serves callers that cannot call cudaMalloc, e.g. code running inside a framework
+ * that owns the device memory pool, or on a latency budget where an allocation may
+ * block).  From valid [B] uint8 (device) it writes the indices of the nonzero
+ * entries in increasing order to out_index [out_capacity] int32 (device; entries
+ * beyond out_capacity are dropped) and their count to *n_out (device int32) -- the
+ * same rows links_simulate writes in LINKS_OUT_VALID_ONLY mode.  Its scratch is a
+ * static device array inside the library sized for B <= 4194304 (4096 x 1024
+ * flags); a larger B returns LINKS_EINVAL.  It needs no context and runs on the
+ * calling thread's current device and on cuda_stream (a cudaStream_t of that
+ * device).  Its first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call on a device shares the array: calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Asynchronous. */
+LINKS_API int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_t* out_index,
+                                         int64_t out_capacity, int32_t* n_out, void* cuda_stream);
+
 /* Begin / end capturing the context's stream into a reusable graph. */
 LINKS_API int links_capture_begin(links_ctx ctx);
 LINKS_API int links_capture_end(links_ctx ctx, links_graph* out);

@@ -1,0 +1,129 @@
+// compact_static.cu -- valid-row compaction whose scratch lives in static device memory,
+// for callers that cannot allocate device memory.
+//
+// Some callers cannot call cudaMalloc: code that runs while another framework owns the
+// device memory pool (an embedding host that forbids foreign allocations), callers
+// on a latency budget where an allocation may block on the driver, and code issued
+// between other work that must not trigger an implicit device synchronisation.  For
+// them this entry point takes the block sums of its scan from a file-scope static
+// array instead of the context's plan, so it needs no context and allocates nothing.
+// The array is sized for kStaticMaxRows flags; every GPU that loads the library holds
+// it (16 KB) until the process exits.
+#include <mutex>
+
+#include "links_internal.cuh"
+
+namespace links {
+namespace {
+
+constexpr int kBlockRows = 1024;
+constexpr int kStaticBlocks = 4096;
+constexpr int64_t kStaticMaxRows = (int64_t)kStaticBlocks * kBlockRows;  // 4,194,304 flags
+constexpr int kMaxDevices = 64;
+
+// Block sums of the scan.  Host code must not pass this name to a kernel: it only
+// stands for the symbol; the device address comes from cudaGetSymbolAddress below.
+__device__ __align__(256) int32_t g_block_sums[kStaticBlocks];
+
+std::mutex g_mu;
+int32_t* g_sums_addr[kMaxDevices] = {};
+
+__device__ int static_block_scan(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) ws[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    int s = ws[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    ws[lane] = s;
+  }
+  __syncthreads();
+  int excl = x - v + (w ? ws[w - 1] : 0);
+  if (total) *total = ws[31];
+  __syncthreads();
+  return excl;
+}
+
+__global__ void __launch_bounds__(kBlockRows) static_scan_count(int64_t B, const uint8_t* valid, int32_t* sums) {
+  int64_t b = (int64_t)blockIdx.x * kBlockRows + threadIdx.x;
+  int v = (b < B && valid[b]) ? 1 : 0;
+  int tot;
+  static_block_scan(v, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Exclusive offsets of the nblk block sums (every entry read here was written by
+// static_scan_count of the same call, so nothing needs clearing between calls).
+__global__ void __launch_bounds__(kBlockRows) static_scan_top(int nblk, int32_t* sums, int32_t* n_out) {
+  int carry = 0;
+  for (int base = 0; base < nblk; base += kBlockRows) {
+    int i = base + threadIdx.x;
+    int v = i < nblk ? sums[i] : 0;
+    int tot;
+    int ex = static_block_scan(v, &tot);
+    if (i < nblk) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0 && n_out) *n_out = carry;
+}
+
+__global__ void __launch_bounds__(kBlockRows) static_scan_write(int64_t B, const uint8_t* valid, const int32_t* sums,
+                                                                int32_t* out_index, int64_t cap) {
+  int64_t b = (int64_t)blockIdx.x * kBlockRows + threadIdx.x;
+  int v = (b < B && valid[b]) ? 1 : 0;
+  int ex = static_block_scan(v, nullptr) + sums[blockIdx.x];
+  if (v && ex < cap && out_index) out_index[ex] = (int32_t)b;
+}
+
+// Device address of g_block_sums on the current device, looked up once per device.
+int static_sums(int32_t** out) {
+  int dev = 0;
+  LINKS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return set_error(LINKS_EINVAL, "links_compact_valid_static: device index >= 64");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_sums_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_block_sums);
+    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_block_sums)");
+    g_sums_addr[dev] = static_cast<int32_t*>(p);
+  }
+  *out = g_sums_addr[dev];
+  return LINKS_OK;
+}
+
+}  // namespace
+}  // namespace links
+
+using namespace links;
+
+extern "C" int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_t* out_index,
+                                          int64_t out_capacity, int32_t* n_out, void* cuda_stream) {
+  if (B < 0 || out_capacity < 0) return set_error(LINKS_EINVAL, "links_compact_valid_static: negative size");
+  if (B > kStaticMaxRows)
+    return set_error(LINKS_EINVAL, "links_compact_valid_static: B exceeds the static maximum of 4194304 flags");
+  if ((B > 0 && !valid) || !n_out || (out_capacity > 0 && !out_index))
+    return set_error(LINKS_EINVAL, "links_compact_valid_static: NULL pointer");
+  int32_t* sums = nullptr;
+  int st = static_sums(&sums);
+  if (st) return st;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  const int nblk = (int)((B + kBlockRows - 1) / kBlockRows);
+  if (nblk > 0) static_scan_count<<<nblk, kBlockRows, 0, s>>>(B, valid, sums);
+  LINKS_CUDA(cudaGetLastError());
+  static_scan_top<<<1, kBlockRows, 0, s>>>(nblk, sums, n_out);
+  LINKS_CUDA(cudaGetLastError());
+  if (nblk > 0) static_scan_write<<<nblk, kBlockRows, 0, s>>>(B, valid, sums, out_index, out_capacity);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}

@@ -57,6 +57,7 @@ def lib():
             "links_profile": ([P, i32], i32),
             "links_profile_read": ([P, i32, P, P, P, P], i32),
             "links_launch_count": ([P, P], i32),
+            "links_compact_valid_static": ([P, i64, P, i64, P, P], i32),
             "links_capture_begin": ([P], i32),
             "links_capture_end": ([P, P], i32),
             "links_graph_launch": ([P, P], i32),
@@ -228,6 +229,16 @@ def links_launch_count(ctx) -> int:
     out = ctypes.c_int64()
     _check(lib().links_launch_count(ctx, ctypes.byref(out)), "links_launch_count")
     return out.value
+
+
+def links_compact_valid_static(valid, out_index, n_out, stream=None):
+    """Allocation-free valid-row compaction on the current device (see include/links.h)."""
+    import torch
+    cap = 0 if out_index is None else out_index.shape[0]
+    _check(lib().links_compact_valid_static(_dev(valid, torch.uint8, "valid"), int(valid.shape[0]),
+                                            _dev(out_index, torch.int32, "out_index"), int(cap),
+                                            _dev(n_out, torch.int32, "n_out"), _stream_handle(stream)),
+           "links_compact_valid_static")
 
 
 def links_capture_begin(ctx):
