@@ -152,6 +152,73 @@ def cpu_baseline(T, seconds=12.0, sample=20000):
                       f"{el:.1f} s on the host cores"}
 
 
+def path_stage(args, local, stream):
+    """Normalisation of M simulated coupler curves and chamfer top-k of Q noisy held-out
+    queries against them (the retrieval workload).  The curves are coupler paths of
+    valid random four-bars simulated by the library itself."""
+    import numpy as np
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    M, Q, k, T = args.path_db, args.path_queries, 10, args.T
+    need = M + Q
+    B4 = int(need / 0.24) + 4096
+    fb = I.fourbar_batch(B4, seed=777)
+    fb.pos = fb.pos.astype(np.float32)
+    dev = torch.device("cuda", local)
+    with Simulator(B4, 5, device=local, stream=stream) as s:
+        s.build(to_device(fb, dev))
+        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=True)
+        s.sync()
+        n = int(o.n_out[0])
+        if n < need:
+            raise RuntimeError(f"only {n} valid four-bars for {need} curves")
+        db = o.path[:M].clone()
+        held = o.path[M:need].cpu().numpy()
+        del o
+    torch.cuda.empty_cache()
+    ctx = L.links_create(local, stream)
+    try:
+        out = torch.empty_like(db)
+        L.links_normalize(ctx, db, out)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 5
+        e0.record(stream)
+        for _ in range(reps):
+            L.links_normalize(ctx, db, out)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        nms = e0.elapsed_time(e1) / reps
+        db_n = out
+        qn = torch.from_numpy(I.perturb_curves(held, 0.02, seed=778)).to(dev)
+        L.links_normalize(ctx, qn, qn)
+        idx = torch.empty((Q, k), dtype=torch.int32, device=dev)
+        dist = torch.empty((Q, k), dtype=torch.float32, device=dev)
+        L.links_chamfer_topk(ctx, qn[:8], db_n, k, idx[:8], dist[:8])  # warm-up (workspace)
+        L.links_workspace_reserve(ctx, Q * 64 * k * 8)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        L.links_chamfer_topk(ctx, qn, db_n, k, idx, dist)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        cms = e0.elapsed_time(e1)
+        pairs = Q * M * T * T
+        hbm = peaks()["hbm_gbs"]
+        nbytes = 2 * M * T * 8
+        return {
+            "normalize": {"curves": M, "T": T, "ms": nms, "curves_per_s": M / (nms * 1e-3),
+                          "GB_per_s": nbytes / (nms * 1e-3) / 1e9, "hbm_frac": nbytes / (nms * 1e-3) / 1e9 / hbm},
+            "chamfer_topk": {"queries": Q, "database": M, "T": T, "k": k, "ms": cms,
+                             "queries_per_s": Q / (cms * 1e-3), "point_pairs_per_s": pairs / (cms * 1e-3),
+                             "median_top1": float(dist[:, 0].median().item())},
+        }
+    finally:
+        L.links_destroy(ctx)
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -177,6 +244,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--path-db", type=int, default=1_000_000)
+    ap.add_argument("--path-queries", type=int, default=1024)
+    ap.add_argument("--no-path-stage", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -320,6 +390,7 @@ def main():
 
     if rank != 0:
         return
+    ps = None if args.no_path_stage or world > 1 else path_stage(args, local, stream)
     cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -334,6 +405,7 @@ def main():
         "kernels": kernels,
         "roofline": roof,
         "cpu_baseline": cb,
+        "path_stage": ps,
         "e2e": e2e,
         "gpu_launches": int(launches * args.steps),
         "clocks": clk.summary(),

@@ -160,6 +160,28 @@ LINKS_API int links_simulate(links_ctx ctx, links_plan plan, int T, int precisio
                    void* traj, void* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
 
+/* Path normalisation (Sec. "Dataset Curation & Processing"; the configured variant):
+ * for each of M curves of T points (device float32 [M,T,2] in, [M,T,2] out, may
+ * alias): subtract the centroid, scale to unit RMS radius, rotate the major axis of
+ * the 2x2 covariance onto +x, choosing of the two such rotations the one with
+ * sum(x^3) >= 0; an isotropic covariance is not rotated; equal points give zeros.
+ * 1 <= T <= 1024.  Asynchronous. */
+LINKS_API int links_normalize(links_ctx ctx, int64_t M, int T, const float* curves, float* out);
+
+/* Bidirectional chamfer retrieval (Sec. "A Case Study of Mechanism Retrieval"):
+ * CD(P, C) = mean over p in P of min_c |p - c| + mean over c in C of min_p |c - p|
+ * (Euclidean), for Q query curves against M database curves of T points each
+ * (device float32 [Q,T,2] and [M,T,2]; 1 <= T <= 256).  Writes the k smallest per
+ * query (1 <= k <= 32), ascending, ties to the lower database index: idx [Q,k]
+ * int32 (-1 past M) and dist [Q,k] float32 (device).  Uses the context's workspace
+ * (Q x chunks x k x 8 bytes, grown on demand; reserve it with
+ * links_workspace_reserve before a graph capture).  Asynchronous. */
+LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
+                                 const float* db, int k, int32_t* idx, float* dist);
+/* Makes the context's workspace at least `bytes` large (allocates; not inside a
+ * capture). */
+LINKS_API int links_workspace_reserve(links_ctx ctx, size_t bytes);
+
 /* Per-kernel timing for benchmarks: with enable = 1 (collection cleared), every
  * kernel the library launches on ctx is bracketed by two CUDA events on the
  * context's stream; enable = 0 stops.  Not for use inside a graph capture. */

@@ -62,6 +62,21 @@ KernelScope::~KernelScope() {
   if (b) cudaEventRecord(b, ctx->stream);
 }
 
+int ensure_workspace(links_ctx ctx, size_t bytes) {
+  if (bytes <= ctx->ws_bytes) return LINKS_OK;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(ctx->stream, &cap);
+  if (cap != cudaStreamCaptureStatusNone)
+    return set_error(LINKS_ESTATE, "workspace too small inside a graph capture: call links_workspace_reserve first");
+  LINKS_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  LINKS_CUDA(cudaMalloc(&ctx->ws, bytes));
+  ctx->ws_bytes = bytes;
+  return LINKS_OK;
+}
+
 const TTable* get_table(links_ctx ctx, int T, int* status) {
   std::lock_guard<std::mutex> lk(ctx->mu);
   auto it = ctx->tables.find(T);
@@ -153,6 +168,7 @@ int links_destroy(links_ctx ctx) {
     cudaEventDestroy(r.b);
   }
   for (auto e : ctx->pool) cudaEventDestroy(e);
+  if (ctx->ws) cudaFree(ctx->ws);
   cudaFree(ctx->d_err);
   delete ctx;
   return LINKS_OK;
@@ -352,6 +368,32 @@ int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out
                         out_index, out_capacity, n_out);
   return simulate_mixed(ctx, plan, tab, out_mode, (float*)traj, (float*)path, valid, lock_step, min_disc,
                         out_index, out_capacity, n_out);
+}
+
+int links_normalize(links_ctx ctx, int64_t M, int T, const float* curves, float* out) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_normalize: NULL ctx");
+  if (M < 0 || T < 1 || T > 1024) return set_error(LINKS_EINVAL, "links_normalize: need M >= 0 and 1 <= T <= 1024");
+  if (M > 0 && (!curves || !out)) return set_error(LINKS_EINVAL, "links_normalize: NULL pointer");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  return normalize_paths(ctx, M, T, curves, out);
+}
+
+int links_workspace_reserve(links_ctx ctx, size_t bytes) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_workspace_reserve: NULL ctx");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  return ensure_workspace(ctx, bytes);
+}
+
+int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* queries, const float* db, int k,
+                       int32_t* idx, float* dist) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_chamfer_topk: NULL ctx");
+  if (Q < 0 || M < 0 || M > INT32_MAX) return set_error(LINKS_EINVAL, "links_chamfer_topk: Q or M out of range");
+  if (T < 1 || T > 256) return set_error(LINKS_EINVAL, "links_chamfer_topk: T must be in [1, 256]");
+  if (k < 1 || k > 32) return set_error(LINKS_EINVAL, "links_chamfer_topk: k must be in [1, 32]");
+  if (Q > 0 && (!queries || !idx || !dist || (M > 0 && !db)))
+    return set_error(LINKS_EINVAL, "links_chamfer_topk: NULL pointer");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  return chamfer_topk(ctx, Q, M, T, queries, db, k, idx, dist);
 }
 
 int links_profile(links_ctx ctx, int enable) {

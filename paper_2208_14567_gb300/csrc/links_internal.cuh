@@ -99,6 +99,9 @@ struct links_ctx_s {
   std::vector<cudaEvent_t> pool;
   std::map<std::string, std::pair<double, int64_t>> acc;
   int64_t launches = 0;
+  // scratch of the retrieval kernels (grown outside graph capture)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
 };
 
 struct links_plan_s {
@@ -124,6 +127,10 @@ int cuda_status(cudaError_t e, const char* what);
   } while (0)
 
 const TTable* get_table(links_ctx ctx, int T, int* status);
+int ensure_workspace(links_ctx ctx, size_t bytes);
+int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out);
+int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,
+                 float* dist);
 
 // Brackets one kernel launch: counts it and, while profiling, records events around it.
 struct KernelScope {

@@ -54,6 +54,9 @@ def lib():
             "links_plan_info": ([P, P, P, P], i32),
             "links_plan_export": ([P, i64, i64, P, P], i32),
             "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
+            "links_normalize": ([P, i64, i32, P, P], i32),
+            "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
+            "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
             "links_profile": ([P, i32], i32),
             "links_profile_read": ([P, i32, P, P, P, P], i32),
             "links_launch_count": ([P, P], i32),
@@ -206,6 +209,28 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
                                 _dev(out_index, torch.int32, "out_index"), int(out_capacity),
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_normalize(ctx, curves, out):
+    """curves, out: float32 CUDA tensors [M, T, 2] (may be the same tensor)."""
+    import torch
+    M, T = curves.shape[0], curves.shape[1]
+    _check(lib().links_normalize(ctx, int(M), int(T), _dev(curves, torch.float32, "curves"),
+                                 _dev(out, torch.float32, "out")), "links_normalize")
+
+
+def links_chamfer_topk(ctx, queries, db, k: int, idx, dist):
+    """queries [Q,T,2], db [M,T,2] float32; idx [Q,k] int32 and dist [Q,k] float32 outputs (CUDA)."""
+    import torch
+    Q, T = queries.shape[0], queries.shape[1]
+    M = db.shape[0]
+    _check(lib().links_chamfer_topk(ctx, int(Q), int(M), int(T), _dev(queries, torch.float32, "queries"),
+                                    _dev(db, torch.float32, "db"), int(k), _dev(idx, torch.int32, "idx"),
+                                    _dev(dist, torch.float32, "dist")), "links_chamfer_topk")
+
+
+def links_workspace_reserve(ctx, nbytes: int):
+    _check(lib().links_workspace_reserve(ctx, int(nbytes)), "links_workspace_reserve")
 
 
 def links_profile(ctx, enable: bool):

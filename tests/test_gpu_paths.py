@@ -1,0 +1,168 @@
+"""Parity of the path stage (normalisation, chamfer top-k) with the FP64 oracle.
+
+Curves are coupler paths of valid four-bars simulated by the oracle (never by the
+CUDA path), under random similarity transforms, plus degenerate cases.
+
+Tolerances (restated in the design doc):
+  * normalise: |gpu - oracle| <= 2e-5 (curves have unit RMS radius) where the
+    oracle's principal-axis gap (lambda1 - lambda2)/(lambda1 + lambda2) >= 1e-3 and
+    |mean x^3| >= 1e-3; otherwise (axis or sign ill-determined) the per-point radii
+    must agree to 2e-5 (the rotation-invariant content);
+  * chamfer top-k: every returned distance equals the oracle's CD of that pair to
+    1e-5 relative; the returned set is the oracle's top-k up to near-ties at the
+    boundary (a returned index's oracle CD <= the oracle's k-th CD + 1e-5 rel).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2208_14567_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2208_14567_gb300 import links
+    links.lib()
+    return links
+
+
+@pytest.fixture(scope="module")
+def ctx(L):
+    c = L.links_create(0, torch.cuda.current_stream())
+    yield c
+    L.links_destroy(c)
+
+
+def coupler_curves(n, T, seed):
+    f = I.fourbar_batch(5 * n + 64, seed=seed)
+    r = O.simulate(f, T, traj=False, path=True)
+    return r.path[r.valid == 1][:n]
+
+
+def transformed(curves, seed):
+    rng = np.random.default_rng(seed)
+    out = np.empty_like(curves)
+    for m in range(len(curves)):
+        a = rng.uniform(0, 2 * np.pi)
+        R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+        out[m] = rng.uniform(0.3, 3) * curves[m] @ R.T + rng.normal(size=2)
+    return out
+
+
+def gpu_normalize(L, ctx, curves32):
+    x = torch.from_numpy(np.ascontiguousarray(curves32)).cuda()
+    y = torch.empty_like(x)
+    L.links_normalize(ctx, x, y)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def margin_mask(ref):
+    x, y = ref[..., 0], ref[..., 1]
+    sxx, syy = (x * x).mean(1), (y * y).mean(1)
+    gap = (sxx - syy) / np.maximum(sxx + syy, 1e-300)
+    s3 = np.abs((x ** 3).mean(1))
+    return (gap < 1e-3) | (s3 < 1e-3)
+
+
+@pytest.mark.parametrize("T", [200, 7, 33, 256, 1000])
+def test_normalize_matches_oracle(L, ctx, T):
+    base = coupler_curves(400, T, seed=T)
+    curves = transformed(base, seed=T).astype(np.float32)
+    s = np.linspace(0, 2 * np.pi, T, endpoint=False)
+    special = np.stack([
+        np.stack([np.cos(s), np.sin(s)], -1) * 2 + 1,            # circle: isotropic
+        np.stack([3 * np.cos(s), np.sin(s)], -1),                 # ellipse: sum x^3 = 0
+        np.full((T, 2), 0.25),                                    # one point: zeros
+    ]).astype(np.float32)
+    curves = np.concatenate([curves, special])
+    ref = O.normalize(curves.astype(np.float64))
+    out = gpu_normalize(L, ctx, curves)
+    mg = margin_mask(ref)
+    mg[-1] = False
+    ok = ~mg
+    err = np.abs(out[ok] - ref[ok]).max()
+    print(f"[T={T}] curves {len(curves)} margin {int(mg.sum())} max |gpu - oracle| {err:.2e}")
+    assert err <= 2e-5
+    assert mg.sum() <= 0.05 * len(curves) + 2
+    rad_g = np.linalg.norm(out[mg], axis=-1)
+    rad_r = np.linalg.norm(ref[mg], axis=-1)
+    assert np.abs(rad_g - rad_r).max() <= 2e-5
+    assert (out[-1] == 0).all()
+
+
+def test_normalize_in_place_and_empty(L, ctx):
+    curves = transformed(coupler_curves(50, 200, 3), 4).astype(np.float32)
+    x = torch.from_numpy(curves).cuda()
+    ref = gpu_normalize(L, ctx, curves)
+    L.links_normalize(ctx, x, x)
+    torch.cuda.synchronize()
+    assert np.array_equal(x.cpu().numpy(), ref)
+    e = torch.empty((0, 200, 2), dtype=torch.float32, device="cuda")
+    L.links_normalize(ctx, e, e)
+
+
+def gpu_topk(L, ctx, q32, db32, k):
+    q = torch.from_numpy(np.ascontiguousarray(q32)).cuda()
+    d = torch.from_numpy(np.ascontiguousarray(db32)).cuda()
+    idx = torch.empty((q.shape[0], k), dtype=torch.int32, device="cuda")
+    dist = torch.empty((q.shape[0], k), dtype=torch.float32, device="cuda")
+    L.links_chamfer_topk(ctx, q, d, k, idx, dist)
+    torch.cuda.synchronize()
+    return idx.cpu().numpy(), dist.cpu().numpy()
+
+
+def check_topk(q, db, idx, dist, k, label):
+    rel = 1e-5
+    worst = 0.0
+    for a in range(len(q)):
+        ref = O.chamfer_many(q[a].astype(np.float64), db.astype(np.float64))
+        ridx, rd = O.topk(ref, k)
+        got = idx[a]
+        assert (got >= 0).all()
+        assert (np.diff(dist[a]) >= 0).all()
+        worst = max(worst, float(np.abs(dist[a] - ref[got]).max() / max(rd[-1], 1e-12)))
+        assert np.allclose(dist[a], ref[got], rtol=rel, atol=1e-7)
+        assert (ref[got] <= rd[-1] * (1 + rel) + 1e-7).all()
+        assert len(set(got.tolist())) == k
+    print(f"[{label}] queries {len(q)} db {len(db)} max relative distance error {worst:.2e}")
+
+
+@pytest.mark.parametrize("T,M,Q,k", [(200, 3000, 24, 10), (37, 1500, 9, 5), (64, 100, 17, 32), (256, 700, 5, 1)])
+def test_chamfer_topk_matches_oracle(L, ctx, T, M, Q, k):
+    curves = O.normalize(coupler_curves(M + Q, T, seed=100 + T)).astype(np.float32)
+    db, held = curves[:M], curves[M:M + Q]
+    q = I.perturb_curves(held, 0.02, seed=T)
+    q = O.normalize(q.astype(np.float64)).astype(np.float32)
+    q[0] = db[M // 2]  # an exact copy must come first, at distance 0
+    idx, dist = gpu_topk(L, ctx, q, db, k)
+    assert idx[0, 0] == M // 2 and dist[0, 0] == 0.0
+    check_topk(q, db, idx, dist, k, f"T={T} M={M} Q={Q} k={k}")
+
+
+def test_chamfer_ties_and_small_database(L, ctx):
+    T = 50
+    base = O.normalize(coupler_curves(6, T, seed=7)).astype(np.float32)
+    db = np.concatenate([base, base[:3]])  # indices 6, 7, 8 duplicate 0, 1, 2
+    idx, dist = gpu_topk(L, ctx, base[:3], db, 12)
+    for a in range(3):
+        assert idx[a, 0] == a and idx[a, 1] == a + 6 and dist[a, 1] == 0.0  # tie -> lower index first
+        assert (idx[a, 9:] == -1).all() and np.isinf(dist[a, 9:]).all()    # only 9 curves exist
+    idx, dist = gpu_topk(L, ctx, base[:2], db[:0], 4)
+    assert (idx == -1).all() and np.isinf(dist).all()
+
+
+def test_chamfer_rejects_bad_sizes(L, ctx):
+    q = torch.zeros((2, 300, 2), dtype=torch.float32, device="cuda")
+    idx = torch.empty((2, 4), dtype=torch.int32, device="cuda")
+    dist = torch.empty((2, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(L.LinksError):
+        L.links_chamfer_topk(ctx, q, q, 4, idx, dist)  # T > 256
+    q = torch.zeros((2, 200, 2), dtype=torch.float32, device="cuda")
+    with pytest.raises(L.LinksError):
+        L.links_chamfer_topk(ctx, q, q, 33, idx, dist)  # k > 32
