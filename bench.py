@@ -219,6 +219,105 @@ def path_stage(args, local, stream):
         L.links_destroy(ctx)
 
 
+def serve_stage(args, local, stream):
+    """Poisson arrivals of requests of log-uniform size on [1, 65536] candidates of
+    6-20 joints, served by the continuous-batching loop; p50/p99 latency (submit to
+    results in host memory) and throughput, beside the plain FP64 batch path on the
+    same candidate mix."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T, NM = args.T, 20
+    pool = I.dyad_batch(args.serve_pool, 6, 20, seed=4242, nmax=NM)
+    host = {k: torch.from_numpy(np.ascontiguousarray(getattr(pool, k))).pin_memory().numpy()
+            for k in ("n_joints", "adj", "jtype", "pos")}
+    times, counts = I.poisson_requests(args.serve_requests, args.serve_rate, 65536, seed=4243)
+    rng = np.random.default_rng(4244)
+    starts = np.array([rng.integers(0, pool.B - c + 1) for c in counts])
+    nslot, cap_rows = 64, 8192
+    slots = [dict(valid=torch.empty(65536, dtype=torch.uint8).pin_memory().numpy(),
+                  lock=torch.empty(65536, dtype=torch.int16).pin_memory().numpy(),
+                  md=torch.empty(65536, dtype=torch.float32).pin_memory().numpy(),
+                  idx=torch.empty(cap_rows, dtype=torch.int32).pin_memory().numpy(),
+                  paths=torch.empty((cap_rows, T, 2), dtype=torch.float32).pin_memory().numpy())
+             for _ in range(nslot)]
+    free = threading.Semaphore(nslot)
+    tickets = [None] * len(counts)
+    lat, res_all = [], []
+    ctx = L.links_create(local, stream)
+    L.links_serve_start(ctx, args.serve_budget << 30, 256, NM, T)
+    done_evt = threading.Event()
+
+    def poller():
+        for i in range(len(counts)):
+            while tickets[i] is None:
+                time.sleep(2e-5)
+            while True:
+                r = L.links_serve_poll(ctx, tickets[i], 100000)
+                if r is not None:
+                    break
+            res_all.append(r)
+            lat.append(r.done_ms - r.submit_ms)
+            free.release()
+        done_evt.set()
+
+    th = threading.Thread(target=poller)
+    th.start()
+    t0 = time.perf_counter()
+    for i, (t, c, s0) in enumerate(zip(times, counts, starts)):
+        free.acquire()
+        sl = slots[i % nslot]
+        req = L.Request(int(c), host["n_joints"][s0:].ctypes.data, host["adj"][s0:].ctypes.data,
+                        host["jtype"][s0:].ctypes.data, host["pos"][s0:].ctypes.data, sl["valid"].ctypes.data,
+                        sl["lock"].ctypes.data, sl["md"].ctypes.data, cap_rows, sl["idx"].ctypes.data,
+                        sl["paths"].ctypes.data, None)
+        while time.perf_counter() - t0 < t:
+            pass
+        while True:
+            try:
+                tickets[i] = L.links_serve_submit(ctx, req)
+                break
+            except L.LinksError as e:
+                if e.status != L.EBUSY:
+                    raise
+                time.sleep(5e-5)
+    done_evt.wait(300)
+    th.join()
+    L.links_serve_stop(ctx)
+    L.links_destroy(ctx)
+    first = min(r.submit_ms for r in res_all)
+    last = max(r.done_ms for r in res_all)
+    cand = int(counts.sum())
+    lat = np.array(lat)
+    # plain FP64 batch path (and the mixed batch path) on a slice of the same pool
+    nb = min(200_000, pool.B)
+    sub = pool.slice(0, nb)
+    batch_rates = {}
+    with Simulator(nb, NM, device=local, stream=stream) as sim:
+        sim.build(to_device(sub, torch.device("cuda", local)))
+        for name, prec in (("plain_f64", L.PLAIN_F64), ("mixed", L.MIXED)):
+            o = sim.simulate(T, prec, L.OUT_VALID_ONLY, traj=False, path=True)
+            sim.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.simulate(T, prec, L.OUT_VALID_ONLY, out=o)
+            e1.record(stream)
+            sim.sync()
+            batch_rates[name] = nb * T / (e0.elapsed_time(e1) * 1e-3)
+            del o
+    return {"requests": len(counts), "candidates": cand, "offered_req_per_s": args.serve_rate,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "max_ms": float(lat.max()), "mechanism_steps_per_s": cand * T / ((last - first) * 1e-3),
+            "wall_s": (last - first) * 1e-3, "batch_plain_f64_mech_steps_per_s": batch_rates["plain_f64"],
+            "batch_mixed_mech_steps_per_s": batch_rates["mixed"], "joints": "6-20", "T": T,
+            "budget_GiB": args.serve_budget}
+
+
 def run_reference(args, world, rank):
     if rank != 0:
         return
@@ -247,6 +346,11 @@ def main():
     ap.add_argument("--path-db", type=int, default=1_000_000)
     ap.add_argument("--path-queries", type=int, default=1024)
     ap.add_argument("--no-path-stage", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=4000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
+    ap.add_argument("--serve-pool", type=int, default=600_000)
+    ap.add_argument("--serve-budget", type=int, default=8, help="GiB of device arena")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
@@ -391,6 +495,7 @@ def main():
     if rank != 0:
         return
     ps = None if args.no_path_stage or world > 1 else path_stage(args, local, stream)
+    sv = None if args.no_serve or world > 1 else serve_stage(args, local, stream)
     cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -406,6 +511,7 @@ def main():
         "roofline": roof,
         "cpu_baseline": cb,
         "path_stage": ps,
+        "serve": sv,
         "e2e": e2e,
         "gpu_launches": int(launches * args.steps),
         "clocks": clk.summary(),

@@ -182,6 +182,59 @@ LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const f
  * capture). */
 LINKS_API int links_workspace_reserve(links_ctx ctx, size_t bytes);
 
+/* ---- Serving: continuous batching of candidate batches (no counterpart in the paper;
+ * the form in which the simulation path is offered as a service).
+ * A request is a batch of `count` candidates in the layout of links_plan_build,
+ * padded to the serving n_max, positions float32, all in HOST memory (pinned for
+ * full overlap) that stays valid until the ticket completes.  Its outputs are
+ * written to the request's host buffers before completion:
+ *   valid [count] u8, lock_step [count] i16, min_disc [count] f32 (may be NULL);
+ *   for the valid candidates in increasing index, up to out_capacity rows:
+ *   valid_index [out_capacity] i32 (index within the request), paths
+ *   [out_capacity, T, 2] f32 normalised coupler paths (may be NULL) and traj
+ *   [out_capacity, n_max, T, 2] f32 (may be NULL; needs with_traj at start). */
+typedef struct {
+  int64_t count;
+  const int32_t* n_joints;
+  const uint8_t* adj;
+  const int8_t* type;
+  const float* pos0;
+  uint8_t* valid;
+  int16_t* lock_step;
+  float* min_disc;
+  int64_t out_capacity;
+  int32_t* valid_index;
+  float* paths;
+  float* traj;
+} links_request;
+
+typedef struct {
+  int status;        /* LINKS_OK or the failure of the request's pass */
+  int64_t n_valid;   /* valid candidates (rows beyond out_capacity were not written) */
+  double submit_ms;  /* steady-clock timestamps in milliseconds */
+  double admit_ms;
+  double done_ms;
+} links_result;
+
+/* Starts the scheduler thread.  The device arena holds the candidates of every
+ * admitted request (inputs, plans, flags, paths): mem_budget_bytes bounds it, and a
+ * request is admitted only when its candidates fit (memory-bounded admission).  Up
+ * to max_pending requests may wait for admission; T <= 1024 steps; with_traj != 0
+ * also returns trajectories.  Work runs on the library's own streams. */
+LINKS_API int links_serve_start(links_ctx ctx, size_t mem_budget_bytes, int max_pending, int n_max, int T,
+                                int with_traj);
+/* Enqueues a request (non-blocking): LINKS_EBUSY when max_pending requests already
+ * wait, LINKS_ECAPACITY when the request can never fit the memory budget. */
+LINKS_API int links_serve_submit(links_ctx ctx, const links_request* req, uint64_t* ticket);
+/* Waits up to timeout_us for the ticket: LINKS_ETIMEDOUT if not finished (the ticket
+ * stays valid); otherwise fills *res, releases the ticket and returns its status. */
+LINKS_API int links_serve_poll(links_ctx ctx, uint64_t ticket, int timeout_us, links_result* res);
+/* Holds (paused = 1) or resumes (0) admission of new requests; admitted work
+ * continues.  For host-side fault-injection tests. */
+LINKS_API int links_serve_pause(links_ctx ctx, int paused);
+/* Finishes all submitted requests, stops the scheduler and frees the arena. */
+LINKS_API int links_serve_stop(links_ctx ctx);
+
 /* Per-kernel timing for benchmarks: with enable = 1 (collection cleared), every
  * kernel the library launches on ctx is bracketed by two CUDA events on the
  * context's stream; enable = 0 stops.  Not for use inside a graph capture. */

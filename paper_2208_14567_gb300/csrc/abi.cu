@@ -157,6 +157,7 @@ int links_create(links_ctx* out, int device, void* cuda_stream) {
 
 int links_destroy(links_ctx ctx) {
   if (!ctx) return set_error(LINKS_EINVAL, "links_destroy: NULL ctx");
+  if (ctx->serve) links_serve_stop(ctx);
   cudaSetDevice(ctx->device);
   cudaStreamSynchronize(ctx->stream);
   for (auto& kv : ctx->tables) {

@@ -80,6 +80,8 @@ struct TTable {
   double2* cs64 = nullptr; // (cos, sin) in FP64
 };
 
+struct ServeState;
+void serve_free(ServeState* s);
 }  // namespace links
 
 struct links_ctx_s {
@@ -102,6 +104,7 @@ struct links_ctx_s {
   // scratch of the retrieval kernels (grown outside graph capture)
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  links::ServeState* serve = nullptr;
 };
 
 struct links_plan_s {
@@ -129,6 +132,8 @@ int cuda_status(cudaError_t e, const char* what);
 const TTable* get_table(links_ctx ctx, int T, int* status);
 int ensure_workspace(links_ctx ctx, size_t bytes);
 int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out);
+// Same, for the first *M_dev of at most M_cap curves (count read on the device).
+int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, int T, const float* in, float* out);
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,
                  float* dist);
 

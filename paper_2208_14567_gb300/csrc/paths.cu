@@ -32,8 +32,9 @@ __device__ __forceinline__ float warp_sum(float v) {
 
 template <int PL>
 __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const float2* __restrict__ in,
-                                                        float2* __restrict__ out) {
+                                                        float2* __restrict__ out, const int32_t* __restrict__ M_dev) {
   const int lane = threadIdx.x & 31;
+  if (M_dev) M = min(M, (int64_t)*M_dev);
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const float invT = 1.0f / (float)T;
@@ -327,18 +328,26 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
 
 }  // namespace
 
-int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out) {
+static int normalize_launch(links_ctx ctx, int64_t M, const int32_t* M_dev, int T, const float* in, float* out) {
   if (M == 0) return LINKS_OK;
   int per_sm = 8;
   unsigned grid = (unsigned)std::min<int64_t>((M + 7) / 8, (int64_t)ctx->num_sms * per_sm);
   KernelScope ks(ctx, "normalize");
   const float2* i2 = reinterpret_cast<const float2*>(in);
   float2* o2 = reinterpret_cast<float2*>(out);
-  if (T <= 64) normalize_kernel<2><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2);
-  else if (T <= 256) normalize_kernel<8><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2);
-  else normalize_kernel<32><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2);
+  if (T <= 64) normalize_kernel<2><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
+  else if (T <= 256) normalize_kernel<8><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
+  else normalize_kernel<32><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
+}
+
+int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out) {
+  return normalize_launch(ctx, M, nullptr, T, in, out);
+}
+
+int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, int T, const float* in, float* out) {
+  return normalize_launch(ctx, M_cap, M_dev, T, in, out);
 }
 
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,

@@ -25,6 +25,20 @@ MAX_JOINTS, MAX_T = 32, 32767
 _lib = None
 
 
+class Request(ctypes.Structure):
+    """Mirror of links_request (host buffers)."""
+    _fields_ = [("count", ctypes.c_int64), ("n_joints", ctypes.c_void_p), ("adj", ctypes.c_void_p),
+                ("type", ctypes.c_void_p), ("pos0", ctypes.c_void_p), ("valid", ctypes.c_void_p),
+                ("lock_step", ctypes.c_void_p), ("min_disc", ctypes.c_void_p), ("out_capacity", ctypes.c_int64),
+                ("valid_index", ctypes.c_void_p), ("paths", ctypes.c_void_p), ("traj", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    """Mirror of links_result."""
+    _fields_ = [("status", ctypes.c_int), ("n_valid", ctypes.c_int64), ("submit_ms", ctypes.c_double),
+                ("admit_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
+
+
 class LinksError(RuntimeError):
     def __init__(self, status: int, what: str, detail: str):
         super().__init__(f"{what} failed: {strerror(status)}: {detail}")
@@ -57,6 +71,11 @@ def lib():
             "links_normalize": ([P, i64, i32, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
+            "links_serve_start": ([P, ctypes.c_size_t, i32, i32, i32, i32], i32),
+            "links_serve_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], i32),
+            "links_serve_poll": ([P, ctypes.c_uint64, i32, ctypes.POINTER(Result)], i32),
+            "links_serve_pause": ([P, i32], i32),
+            "links_serve_stop": ([P], i32),
             "links_profile": ([P, i32], i32),
             "links_profile_read": ([P, i32, P, P, P, P], i32),
             "links_launch_count": ([P, P], i32),
@@ -231,6 +250,47 @@ def links_chamfer_topk(ctx, queries, db, k: int, idx, dist):
 
 def links_workspace_reserve(ctx, nbytes: int):
     _check(lib().links_workspace_reserve(ctx, int(nbytes)), "links_workspace_reserve")
+
+
+def links_serve_start(ctx, mem_budget_bytes: int, max_pending: int, n_max: int, T: int, with_traj: bool = False):
+    _check(lib().links_serve_start(ctx, int(mem_budget_bytes), int(max_pending), int(n_max), int(T),
+                                   1 if with_traj else 0), "links_serve_start")
+
+
+def links_serve_submit(ctx, req: Request) -> int:
+    """Returns the ticket; raises LinksError (status EBUSY / ECAPACITY / EINVAL) on refusal."""
+    t = ctypes.c_uint64()
+    _check(lib().links_serve_submit(ctx, ctypes.byref(req), ctypes.byref(t)), "links_serve_submit")
+    return t.value
+
+
+def links_serve_poll(ctx, ticket: int, timeout_us: int):
+    """-> Result, or None if the ticket did not finish within timeout_us."""
+    res = Result()
+    st = lib().links_serve_poll(ctx, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(res))
+    if st == ETIMEDOUT:
+        return None
+    _check(st, "links_serve_poll")
+    return res
+
+
+def links_serve_pause(ctx, paused: bool):
+    _check(lib().links_serve_pause(ctx, 1 if paused else 0), "links_serve_pause")
+
+
+def links_serve_stop(ctx):
+    _check(lib().links_serve_stop(ctx), "links_serve_stop")
+
+
+def make_request(n_joints, adj, jtype, pos0, valid, lock_step, min_disc=None, valid_index=None, paths=None,
+                 traj=None) -> Request:
+    """A Request over numpy host arrays (kept alive by the caller until completion)."""
+    import numpy as np
+    cap = 0 if valid_index is None else valid_index.shape[0]
+    return Request(int(n_joints.shape[0]), _host(n_joints, np.int32), _host(adj, np.uint8), _host(jtype, np.int8),
+                   _host(pos0, np.float32), _host(valid, np.uint8), _host(lock_step, np.int16),
+                   _host(min_disc, np.float32), cap, _host(valid_index, np.int32), _host(paths, np.float32),
+                   _host(traj, np.float32))
 
 
 def links_profile(ctx, enable: bool):
