@@ -265,6 +265,16 @@ LINKS_API int links_launch_count(links_ctx ctx, int64_t* out);
 LINKS_API int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_t* out_index,
                                          int64_t out_capacity, int32_t* n_out, void* cuda_stream);
 
+/* Autotuner of the mixed-precision screen: times it with 8, 16 and 32 lanes per
+ * mechanism (consecutive steps of one mechanism per lane group) on the plan as last
+ * built, over T steps, and keeps the fastest for plans of this n_max on this
+ * context (*lanes receives it; may be NULL).  Allocates scratch and synchronizes:
+ * call it before capturing a graph.  Without it the screen uses 8 lanes. */
+LINKS_API int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes);
+
+/* Sets the screen's lanes per mechanism (8, 16 or 32) for plans of this n_max. */
+LINKS_API int links_set_screen_lanes(links_ctx ctx, int n_max, int lanes);
+
 /* Begin / end capturing the context's stream into a reusable graph. */
 LINKS_API int links_capture_begin(links_ctx ctx);
 LINKS_API int links_capture_end(links_ctx ctx, links_graph* out);

@@ -444,6 +444,24 @@ int links_launch_count(links_ctx ctx, int64_t* out) {
   return LINKS_OK;
 }
 
+int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes) {
+  if (!ctx || !plan) return set_error(LINKS_EINVAL, "links_autotune: NULL ctx or plan");
+  if (plan->ctx != ctx) return set_error(LINKS_EINVAL, "links_autotune: plan belongs to another context");
+  if (T < 1 || T > LINKS_MAX_T) return set_error(LINKS_EINVAL, "links_autotune: T out of [1, 32767]");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  int st = LINKS_OK;
+  const TTable* tab = get_table(ctx, T, &st);
+  if (!tab) return st;
+  return autotune_screen(ctx, plan, tab, lanes);
+}
+
+int links_set_screen_lanes(links_ctx ctx, int n_max, int lanes) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_set_screen_lanes: NULL ctx");
+  if (lanes != 8 && lanes != 16 && lanes != 32) return set_error(LINKS_EINVAL, "links_set_screen_lanes: lanes must be 8, 16 or 32");
+  ctx->screen_lanes[n_max] = lanes;
+  return LINKS_OK;
+}
+
 int links_capture_begin(links_ctx ctx) {
   if (!ctx) return set_error(LINKS_EINVAL, "links_capture_begin: NULL ctx");
   if (!ctx->stream) return set_error(LINKS_ESTATE, "links_capture_begin: the legacy default stream cannot be captured");

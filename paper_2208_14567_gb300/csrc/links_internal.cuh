@@ -105,6 +105,7 @@ struct links_ctx_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   links::ServeState* serve = nullptr;
+  std::map<int, int> screen_lanes;  // autotuned lanes per mechanism, by n_max
 };
 
 struct links_plan_s {
@@ -162,6 +163,9 @@ int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+// Times the screen with 8, 16 and 32 lanes per mechanism on the built plan and keeps
+// the fastest for this n_max (allocates scratch; not inside a capture).
+int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes);
 // Shared by both precisions: rows of the valid mechanisms in index order.
 int compact_valid(links_ctx ctx, links_plan plan, const uint8_t* valid, int32_t* out_index,
                   int64_t out_capacity, int32_t* n_out);

@@ -39,19 +39,26 @@ struct dwp {
   dw x, y;
 };
 
-// Double-word chain of one step: positions relative to the pivot in loc[slot].
+// Double-word chain of one step into loc[slot].  fix holds the fixed slots as
+// (x_h, x_l, y_h, y_l); with ABS the positions are absolute (fix absolute, the
+// actuated joint offset by the pivot), otherwise relative to the pivot.
 // Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
-__device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* __restrict__ fix,
-                                      const DyadRec* __restrict__ dy, float4 csv, dwp* loc,
-                                      float* qmin) {
+template <bool ABS>
+__device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
+                                      float4 csv, dwp* loc, float* qmin) {
   const int nf = h.nf, nd = h.nd;
   for (int s = 0; s < nf; ++s) {
-    float4 f = __ldg(fix + s);
+    float4 f = fix[s];
     loc[s] = {{f.x, f.y}, {f.z, f.w}};
   }
   dw c = {csv.x, csv.y}, s = {csv.z, csv.w};
   dw ux = {h.ux_h, h.ux_l}, uy = {h.uy_h, h.uy_l};
-  loc[nf] = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
+  dwp m = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
+  if (ABS) {
+    m.x = dw_add(m.x, dw{h.px_h, h.px_l});
+    m.y = dw_add(m.y, dw{h.py_h, h.py_l});
+  }
+  loc[nf] = m;
   float q = INFINITY;
   for (int d = 0; d < nd; ++d) {
     float4 r0 = __ldg(&dy[d].r0), r1 = __ldg(&dy[d].r1), r2 = __ldg(&dy[d].r2);
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
     if (amb) {
       dwp loc[kMaxJ];
       float qd;
-      locked = dw_chain(h, p.fixpos + b * ns, dy, __ldg(cs + t), loc, &qd);
+      locked = dw_chain<false>(h, p.fixpos + b * ns, dy, __ldg(cs + t), loc, &qd);
       qstep = qd;
     }
     const unsigned lb = __ballot_sync(kFull, locked) & gmask;
@@ -230,19 +237,28 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     const uint8_t* sj = p.slot_joint + b * kMaxJ;
     float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
     float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
-    const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
+    // fixed joints in absolute coordinates, once per row
+    float4 fabs[kMaxJ];
+    {
+      const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
+      const float4* fr = p.fixpos + b * ns;
+      for (int s = 0; s < (ok ? h.nf : 0); ++s) {
+        float4 f = __ldg(fr + s);
+        dw x = dw_add(px, dw{f.x, f.y}), y = dw_add(py, dw{f.z, f.w});
+        fabs[s] = make_float4(x.h, x.l, y.h, y.l);
+      }
+    }
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;
       if (t >= T) continue;
       if (t < lock) {
         dwp loc[kMaxJ];
         float qd;
-        bool lk = dw_chain(h, p.fixpos + b * ns, p.dyad + b * p.max_dyads, __ldg(cs + t), loc, &qd);
+        bool lk = dw_chain<true>(h, fabs, p.dyad + b * p.max_dyads, __ldg(cs + t), loc, &qd);
         if (lk) atomicOr(err, kErrEmitLock);
         const int nslot = h.nf + 1 + h.nd;
         for (int s = 0; s < nslot; ++s) {
-          float2 v = lk ? make_float2(nanf_, nanf_)
-                        : make_float2(dw_add(px, loc[s].x).h, dw_add(py, loc[s].y).h);
+          float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(loc[s].x.h, loc[s].y.h);
           if (trow) trow[(int64_t)sj[s] * T + t] = v;
           if (prow && s == h.coupler_slot) prow[t] = v;
         }
@@ -279,7 +295,62 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   return LINKS_OK;
 }
 
+int launch_screen_lanes(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
+                        int16_t* lock_step, float* min_disc, int lanes) {
+  if (lanes == 32) return launch_screen<32>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  if (lanes == 16) return launch_screen<16>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  return launch_screen<8>(ctx, plan, T, tab, valid, lock_step, min_disc);
+}
+
+int screen_lanes(links_ctx ctx, links_plan plan) {
+  auto it = ctx->screen_lanes.find(plan->d.n_max);
+  return it == ctx->screen_lanes.end() ? 8 : it->second;
+}
+
 }  // namespace
+
+int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) {
+  const int64_t B = plan->B;
+  uint8_t* v = nullptr;
+  int16_t* l = nullptr;
+  float* q = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int best = 8, st = LINKS_OK;
+  float best_ms = 1e30f;
+  cudaError_t e = cudaMalloc(&v, std::max<int64_t>(B, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&l, 2 * std::max<int64_t>(B, 1));
+  if (e == cudaSuccess) e = cudaMalloc(&q, 4 * std::max<int64_t>(B, 1));
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) st = cuda_status(e, "autotune_screen");
+  for (int lanes : {8, 16, 32}) {
+    if (st) break;
+    float total = 0.f;
+    for (int rep = 0; rep < 3 && !st; ++rep) {
+      cudaEventRecord(e0, ctx->stream);
+      st = launch_screen_lanes(ctx, plan, tab->T, tab, v, l, q, lanes);
+      cudaEventRecord(e1, ctx->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(LINKS_ECUDA, "autotune_screen: run failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) total += ms;  // the first run warms up
+    }
+    if (!st && total < best_ms) {
+      best_ms = total;
+      best = lanes;
+    }
+  }
+  if (!st) {
+    ctx->screen_lanes[plan->d.n_max] = best;
+    if (lanes_out) *lanes_out = best;
+  }
+  cudaFree(v);
+  cudaFree(l);
+  cudaFree(q);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
+}
 
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
@@ -288,7 +359,7 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
   const int T = tab->T;
   int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
   if (st) return st;
-  st = launch_screen<8>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  st = launch_screen_lanes(ctx, plan, T, tab, valid, lock_step, min_disc, screen_lanes(ctx, plan));
   if (st) return st;
   const bool full = out_mode == LINKS_OUT_FULL;
   if (!full) {

@@ -149,42 +149,46 @@ def dyad_batch(B: int, n_lo: int, n_hi: int, seed: int = 0, *, ground_max: int =
 
     jt = np.full((B, nmax), PAD, dtype=np.int8)
     jt[:, 0], jt[:, 1], jt[:, 2] = FIXED, MOTOR, FIXED
+    isfix = np.zeros((B, nmax), dtype=bool)
+    isfix[:, 0] = isfix[:, 2] = True
     adj = np.zeros((B, nmax, nmax), dtype=np.uint8)
     adj[:, 0, 1] = adj[:, 1, 0] = 1
     nfix = np.full(B, 2, dtype=np.int32)
-    rows = np.arange(B)
     max_attempts = 64
+    flat = adj.reshape(-1)
     for k in range(3, n_hi):
-        live = k < n
-        if not live.any():
+        live = np.nonzero(k < n)[0]
+        if live.size == 0:
             break
-        ug = st_g.uniform(bidx * np.uint64(64) + np.uint64(k))
-        ground = live & (k < n - 1) & (nfix < ground_max) & (ug < p_ground)
-        jt[ground, k] = FIXED
-        nfix += ground
-        simple = live & ~ground
-        jt[simple, k] = SIMPLE
-        isfix = jt[:, :k] == FIXED
-        pi = np.zeros(B, dtype=np.int64)
-        pj = np.zeros(B, dtype=np.int64)
-        todo = simple.copy()
+        ul = live.astype(np.uint64)
+        ug = st_g.uniform(ul * np.uint64(64) + np.uint64(k))
+        ground = (k < n[live] - 1) & (nfix[live] < ground_max) & (ug < p_ground)
+        g_idx, s_idx = live[ground], live[~ground]
+        jt[g_idx, k] = FIXED
+        isfix[g_idx, k] = True
+        nfix[g_idx] += 1
+        jt[s_idx, k] = SIMPLE
+        pi = np.zeros(s_idx.size, dtype=np.int64)
+        pj = np.zeros(s_idx.size, dtype=np.int64)
+        todo = np.arange(s_idx.size)
         for att in range(max_attempts):
-            if not todo.any():
+            if todo.size == 0:
                 break
-            ctr = (bidx * np.uint64(64) + np.uint64(k)) * np.uint64(2 * max_attempts) + np.uint64(2 * att)
-            i = np.floor(st_p.uniform(ctr) * k).astype(np.int64)
-            j = np.floor(st_p.uniform(ctr + np.uint64(1)) * (k - 1)).astype(np.int64)
-            i = np.minimum(i, k - 1)
-            j = np.minimum(j, k - 2)
+            rows_t = s_idx[todo]
+            ctr = (rows_t.astype(np.uint64) * np.uint64(64) + np.uint64(k)) * np.uint64(2 * max_attempts) \
+                + np.uint64(2 * att)
+            i = np.minimum(np.floor(st_p.uniform(ctr) * k).astype(np.int64), k - 1)
+            j = np.minimum(np.floor(st_p.uniform(ctr + np.uint64(1)) * (k - 1)).astype(np.int64), k - 2)
             j = j + (j >= i)
-            ok = todo & ~(isfix[rows, i] & isfix[rows, j])
-            pi[ok], pj[ok] = i[ok], j[ok]
-            todo &= ~ok
+            ok = ~(isfix[rows_t, i] & isfix[rows_t, j])
+            pi[todo[ok]], pj[todo[ok]] = i[ok], j[ok]
+            todo = todo[~ok]
         # Deterministic fallback (probability < 3^-64): link to the actuated joint 1 and joint 0.
         pi[todo], pj[todo] = 0, 1
-        s = rows[simple]
-        adj[s, k, pi[simple]] = adj[s, pi[simple], k] = 1
-        adj[s, k, pj[simple]] = adj[s, pj[simple], k] = 1
+        rowbase = s_idx.astype(np.int64) * nmax * nmax
+        for a, c in ((k, pi), (k, pj)):
+            flat[rowbase + a * nmax + c] = 1
+            flat[rowbase + c * nmax + a] = 1
 
     pos = _positions(st_pos, B, nmax, n, np.float64).astype(pos_dtype)
     batch = MechBatch(n, adj, jt, pos)

@@ -80,6 +80,8 @@ def lib():
             "links_profile_read": ([P, i32, P, P, P, P], i32),
             "links_launch_count": ([P, P], i32),
             "links_compact_valid_static": ([P, i64, P, i64, P, P], i32),
+            "links_autotune": ([P, P, i32, P], i32),
+            "links_set_screen_lanes": ([P, i32, i32], i32),
             "links_capture_begin": ([P], i32),
             "links_capture_end": ([P, P], i32),
             "links_graph_launch": ([P, P], i32),
@@ -324,6 +326,17 @@ def links_compact_valid_static(valid, out_index, n_out, stream=None):
                                             _dev(out_index, torch.int32, "out_index"), int(cap),
                                             _dev(n_out, torch.int32, "n_out"), _stream_handle(stream)),
            "links_compact_valid_static")
+
+
+def links_autotune(ctx, plan, T: int) -> int:
+    """Tunes the screen's lanes per mechanism on the built plan; returns the choice."""
+    lanes = ctypes.c_int()
+    _check(lib().links_autotune(ctx, plan, int(T), ctypes.byref(lanes)), "links_autotune")
+    return lanes.value
+
+
+def links_set_screen_lanes(ctx, n_max: int, lanes: int):
+    _check(lib().links_set_screen_lanes(ctx, int(n_max), int(lanes)), "links_set_screen_lanes")
 
 
 def links_capture_begin(ctx):

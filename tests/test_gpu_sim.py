@@ -314,3 +314,65 @@ def test_full_size_one_million_candidates(L):
                     TOL_MIXED, "1M sampled rows")
     f64 = run(batch, 200, L.PLAIN_F64, L.OUT_VALID_ONLY, L)
     check_flags(f64, ref, "1M f64")
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_every_screen_lane_count_matches_oracle(L, lanes):
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.dyad_batch(3000, 6, 20, seed=40 + lanes, permute=True)
+    ref = O.simulate(batch, 200)
+    with Simulator(batch.B, batch.nmax) as s:
+        L.links_set_screen_lanes(s.ctx, batch.nmax, lanes)
+        s.build(to_device(batch))
+        o = s.simulate(200, L.MIXED, L.OUT_FULL)
+        s.sync()
+        res = {"valid": o.valid.cpu().numpy(), "lock_step": o.lock_step.cpu().numpy()}
+        traj, path = o.traj.cpu().numpy(), o.path.cpu().numpy()
+    check_flags(res, ref, f"lanes={lanes}")
+    check_positions(batch, traj, path, ref, res["lock_step"], TOL_MIXED, f"lanes={lanes}")
+
+
+@pytest.mark.slow
+def test_config3_four_million_graph_autotuned(L):
+    """4M dyad-built candidates of 6-20 joints in one persistent screen launch under a
+    captured CUDA graph (plan build + simulate), lanes per mechanism autotuned; flags
+    of all 4M against the oracle and the plain FP64 kernel, 2000 sampled valid rows
+    against the oracle."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    B, T = 4 * 1024 * 1024, 200
+    batch = I.dyad_batch(B, 6, 20, seed=3, nmax=20)
+    ref = O.simulate(batch, T, traj=False, path=False)
+    n_valid = int(ref.valid.sum())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        with Simulator(B, 20, stream=stream) as s:
+            db = to_device(batch)
+            status = torch.empty(B, dtype=torch.int32, device="cuda")
+            s.build(db, status)
+            lanes = L.links_autotune(s.ctx, s.plan, T)
+            out = s.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=n_valid + 4096)
+            L.links_prepare(s.ctx, T)
+            L.links_capture_begin(s.ctx)
+            s.build(db, status)
+            s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=out)
+            g = L.links_capture_end(s.ctx)
+            L.links_graph_launch(s.ctx, g)
+            s.sync()
+            L.links_graph_free(g)
+            res = {"valid": out.valid.cpu().numpy(), "lock_step": out.lock_step.cpu().numpy()}
+            n = int(out.n_out[0])
+            idx = out.out_index[:n].cpu().numpy()
+            rows = np.sort(np.random.default_rng(1).choice(n, size=min(2000, n), replace=False))
+            traj = out.traj[torch.from_numpy(rows).cuda()].cpu().numpy()
+            path = out.path[torch.from_numpy(rows).cuda()].cpu().numpy()
+            del out
+            f = s.simulate(T, L.PLAIN_F64, L.OUT_VALID_ONLY, traj=False, path=False)
+            s.sync()
+            f64 = {"valid": f.valid.cpu().numpy(), "lock_step": f.lock_step.cpu().numpy()}
+    print(f"[config 3] lanes per mechanism chosen by the autotuner: {lanes}")
+    check_flags(res, ref, "4M mixed (graph)")
+    check_flags(f64, ref, "4M plain f64")
+    assert np.array_equal(idx, np.nonzero(res["valid"])[0])
+    sub = batch.take(idx[rows])
+    rs = O.simulate(sub, T)
+    check_positions(sub, traj, path, rs, np.full(len(rows), -1, np.int16), TOL_MIXED, "4M sampled rows")
