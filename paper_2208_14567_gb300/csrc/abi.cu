@@ -328,13 +328,13 @@ int links_plan_export(links_plan plan, int64_t b0, int64_t count, int32_t* topo,
     for (int q = 0; q < h.nd && q < md; ++q) {
       const DyadRec& r = dy[m * d.max_dyads + q];
       uint32_t sl;
-      memcpy(&sl, &r.r0.x, 4);
+      memcpy(&sl, &r.r2.w, 4);
       o[6 + 3 * q] = (sl >> 16) & 0xff;
       o[7 + 3 * q] = s2j[sl & 0xff];
       o[8 + 3 * q] = s2j[(sl >> 8) & 0xff];
       if (L) {
-        double r1sq = (double)r.r1.z + (double)r.r1.w;
-        double c = (double)r.r0.w + (double)r.r2.x;
+        double r1sq = (double)r.r2.x + (double)r.r2.y;
+        double c = (double)r.r0.w + (double)r.r2.z;
         L[2 * q] = r1sq;
         L[2 * q + 1] = r1sq - c;
       }

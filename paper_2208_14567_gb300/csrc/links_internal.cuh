@@ -41,12 +41,16 @@ struct __align__(16) MechHdr {
 static_assert(sizeof(MechHdr) == 64, "MechHdr must be 64 bytes");
 
 // Dyad record: three float4 per dyad.
-//   r0 = {slots, R12_h, Rm_h, c_h}   slots = si | sj << 8 | k_joint << 16 | sk << 24
-//   r1 = {w2, locc, r1sq_h, r1sq_l}  w2 = 2 r1 r2, locc = local FP32 error constant
-//   r2 = {c_l, R12_l, Rm_l, 0}
+//   r0 = {offPij, R12_h, Rm_h, c_h}     FP32 screen
+//   r1 = {w2, locc, offK, offEij}       FP32 screen
+//   r2 = {r1sq_h, r1sq_l, c_l, slots}   double-word chain, FP64 kernel, export
 // with r1 = |p_k - p_i|, r2 = |p_k - p_j|, R12 = r1 + r2, Rm = |r1 - r2|,
-// c = r1^2 - r2^2, and (i, j) ordered so that the initial configuration has
-// (p_j - p_i) x (p_k - p_i) >= 0 (the solved branch is then always the "+" one).
+// c = r1^2 - r2^2, w2 = 2 r1 r2, locc = local FP32 error constant, and (i, j) ordered
+// so that the initial configuration has (p_j - p_i) x (p_k - p_i) >= 0 (the solved
+// branch is then always the "+" one).  The off* words hold byte offsets into a
+// lane's slot arrays of the screen (positions 256 B per slot, bounds 128 B per slot)
+// as two 16-bit halves: offPij = P(i) | P(j) << 16, offK = P(k) | E(k) << 16,
+// offEij = E(i) | E(j) << 16; slots = i | j << 8 | k_joint << 16 | k << 24.
 struct DyadRec {
   float4 r0, r1, r2;
 };

@@ -57,6 +57,11 @@ LINKS_HD dw2 rel(const double* pos, int a, int b) {
 LINKS_HD dw abs_dw(const float* pos, int c) { return dw_make(pos[c]); }
 LINKS_HD dw abs_dw(const double* pos, int c) { return dw_from_double(pos[c]); }
 LINKS_HD dw norm2(dw2 v) { return dw_add(dw_sqr(v.x), dw_sqr(v.y)); }
+LINKS_HD float u2f(uint32_t u) {
+  union { uint32_t u; float f; } cv;
+  cv.u = u;
+  return cv.f;
+}
 // |(x, y)| rounded up a little (a bound, identical on host and device).
 LINKS_HD float hyp_up(float x, float y) {
   return fmul(fsqrt_rn(fadd(fmul(x, x), fmul(y, y))), 1.0f + 4.0f * kU);
@@ -193,13 +198,15 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
     bound[sk] = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
     bmax = fmaxf(bmax, bound[sk]);
     float locc = fmul(kLocalErr * kU, fadd(fadd(R12.h, bi), bj));
-    uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
+    const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
+    // byte offsets into a lane's slot arrays: positions 256 B per slot, bounds 128 B
+    const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
+    const uint32_t offK = ((uint32_t)sk * 256u) | (((uint32_t)sk * 128u) << 16);
+    const uint32_t offEij = ((uint32_t)si * 128u) | (((uint32_t)sj * 128u) << 16);
     DyadRec rec;
-    union { uint32_t u; float f; } cv;
-    cv.u = slots;
-    rec.r0 = make_float4(cv.f, R12.h, Rm.h, c.h);
-    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), locc, r1sq.h, r1sq.l);
-    rec.r2 = make_float4(c.l, R12.l, Rm.l, 0.0f);
+    rec.r0 = make_float4(u2f(offPij), R12.h, Rm.h, c.h);
+    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), locc, u2f(offK), u2f(offEij));
+    rec.r2 = make_float4(r1sq.h, r1sq.l, c.l, u2f(slots));
     o.dyad[d] = rec;
   }
 

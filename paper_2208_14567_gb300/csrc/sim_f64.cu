@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kBlock) f64_kernel(PlanDev p, int64_t B, int T
   int si[kMaxJ], sjx[kMaxJ];
   for (int s = 0; s < n; ++s) pos[s] = p0[s];
   for (int d = 0; d < nd; ++d) {
-    uint32_t sl = __float_as_uint(__ldg(&dy[d].r0.x));
+    uint32_t sl = __float_as_uint(__ldg(&dy[d].r2.w));
     si[d] = sl & 0xff;
     sjx[d] = (sl >> 8) & 0xff;
     const int k = nf + 1 + d;

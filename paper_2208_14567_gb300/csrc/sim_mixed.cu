@@ -29,12 +29,6 @@ constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kBatch = 16;  // work items taken per atomic by a warp
 
-__device__ __forceinline__ float min_nan(float a, float b) {  // NaN-propagating min
-  float r;
-  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
-  return r;
-}
-
 struct dwp {
   dw x, y;
 };
@@ -61,18 +55,19 @@ __device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const
   loc[nf] = m;
   float q = INFINITY;
   for (int d = 0; d < nd; ++d) {
-    float4 r0 = __ldg(&dy[d].r0), r1 = __ldg(&dy[d].r1), r2 = __ldg(&dy[d].r2);
-    uint32_t sl = __float_as_uint(r0.x);
+    const float c_h = __ldg(&dy[d].r0.w), w2 = __ldg(&dy[d].r1.x);
+    const float4 r2 = __ldg(&dy[d].r2);
+    uint32_t sl = __float_as_uint(r2.w);
     const dwp pi = loc[sl & 0xff], pj = loc[(sl >> 8) & 0xff];
     dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
     dw d2 = dw_add(dw_sqr(dx), dw_sqr(dy_));
-    dw e = dw_add(d2, dw{r0.w, r2.x});
-    dw D = dw_sub(dw_scale2(dw_mul(d2, dw{r1.z, r1.w}), 4.0f), dw_sqr(e));
+    dw e = dw_add(d2, dw{c_h, r2.z});
+    dw D = dw_sub(dw_scale2(dw_mul(d2, dw{r2.x, r2.y}), 4.0f), dw_sqr(e));
     if (!(dw_sign(D) > 0.0f)) {
       *qmin = q;
       return true;
     }
-    q = fminf(q, __fdividef(D.h, r1.x * r1.x));
+    q = fminf(q, __fdividef(D.h, w2 * w2));
     dw sq = dw_sqrt(D);
     dw hinv = dw_scale2(dw_rcp(d2), 0.5f);
     dw a = dw_mul(e, hinv), bq = dw_mul(sq, hinv);
@@ -85,6 +80,49 @@ __device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const
   return false;
 }
 
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-propagating
+  float r;
+  asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
+// One FP32 dyad of the screen for this lane.  Pb / Eb point at the lane's column of
+// the warp's slot arrays (positions, error bounds); the record holds byte offsets.
+// lockw = min over dyads of slack + bound (< 0: certainly locked), zmin = min of
+// slack - bound (>= 0 everywhere: certainly free; NaN propagates), isgmax = max
+// 1/sin(gamma).
+__device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
+                                          float& zmin, float& isgmax) {
+  const float4 r0 = __ldg(&rec->r0), r1 = __ldg(&rec->r1);
+  const uint32_t oij = __float_as_uint(r0.x), oe = __float_as_uint(r1.w), ok = __float_as_uint(r1.z);
+  const float2 pi = *reinterpret_cast<const float2*>(Pb + (oij & 0xffffu));
+  const float2 pj = *reinterpret_cast<const float2*>(Pb + (oij >> 16));
+  const float ei = *reinterpret_cast<const float*>(Eb + (oe & 0xffffu));
+  const float ej = *reinterpret_cast<const float*>(Eb + (oe >> 16));
+  const float dx = pj.x - pi.x, dy = pj.y - pi.y;
+  const float d2 = fmaf(dx, dx, dy * dy);
+  const float rd = rsqrtf(d2);
+  const float dd = d2 * rd;
+  const float s2 = r0.y - dd, s3 = dd - r0.z;
+  const float D = ((dd + r0.y) * s2) * (s3 * (dd + r0.z));
+  const float rD = rsqrtf(D);
+  const float isg = r1.x * rD;
+  const float del = ei + ej + r1.y;
+  lockw = min3(lockw, s2 + del, s3 + del);
+  zmin = min3_nan(zmin, s2 - del, s3 - del);
+  isgmax = fmaxf(isgmax, isg);
+  const float hinv = 0.5f * (rd * rd);
+  const float a = (d2 + r0.w) * hinv, bq = (D * rD) * hinv;
+  *reinterpret_cast<float2*>(Pb + (ok & 0xffffu)) =
+      make_float2(fmaf(a, dx, fmaf(-bq, dy, pi.x)), fmaf(a, dy, fmaf(bq, dx, pi.y)));
+  *reinterpret_cast<float*>(Eb + (ok >> 16)) = del * isg;
+}
+
 template <int G>
 __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
                                                         uint8_t* __restrict__ valid,
@@ -93,8 +131,9 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
-  float2* P = reinterpret_cast<float2*>(reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384) + lane;
-  float* E = reinterpret_cast<float*>(reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384 + ns * 256) + lane;
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384;
+  char* const Pb = region + lane * 8;
+  char* const Eb = region + ns * 256 + lane * 4;
   const int g = lane / G, gl = lane % G;
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
 
@@ -106,7 +145,9 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
   bool exhausted = false;
   int item = -1, chunk = 0;
   int64_t b = 0;
-  MechHdr h{};
+  int nd = 0, nf = 0;
+  float ux = 0.f, uy = 0.f, e_motor = 0.f;
+  const DyadRec* rec = p.dyad;
   float qacc = INFINITY;
 
   while (true) {
@@ -132,63 +173,45 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
 
     if (fresh) {
       b = p.order[item];
-      h = p.hdr[b];
+      const MechHdr* hp = p.hdr + b;
+      const int4 w0 = __ldg(reinterpret_cast<const int4*>(hp));
+      nd = (w0.y >> 8) & 0xff;
+      nf = (w0.y >> 16) & 0xff;
+      ux = __ldg(&hp->ux_h);
+      uy = __ldg(&hp->uy_h);
+      e_motor = __ldg(&hp->e_motor);
+      const float e_fixed = __ldg(&hp->e_fixed);
+      rec = p.dyad + b * p.max_dyads;
       chunk = 0;
       qacc = INFINITY;
       const float4* fix = p.fixpos + b * ns;
-      for (int s = 0; s < h.nf; ++s) {
+      for (int s = 0; s < nf; ++s) {
         float4 f = __ldg(fix + s);
-        P[s * 32] = make_float2(f.x, f.z);
-        E[s * 32] = h.e_fixed;
+        *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
+        *reinterpret_cast<float*>(Eb + s * 128) = e_fixed;
       }
     }
     const bool has = item >= 0;
     const int t = chunk * G + gl;
     const bool act = has && t < T;
-    const int nd = has ? h.nd : 0;
-    const int nf = h.nf;
     float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f;
     if (has) {
       float4 csv = __ldg(cs + min(t, T - 1));
-      P[nf * 32] = make_float2(csv.x * h.ux_h - csv.z * h.uy_h, csv.z * h.ux_h + csv.x * h.uy_h);
-      E[nf * 32] = h.e_motor;
+      *reinterpret_cast<float2*>(Pb + nf * 256) = make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
+      *reinterpret_cast<float*>(Eb + nf * 128) = e_motor;
     }
-    const int ndw = __reduce_max_sync(kFull, (unsigned)nd);
-    const DyadRec* dy = p.dyad + b * p.max_dyads;
-    for (int d = 0; d < ndw; ++d) {
-      if (d < nd) {
-        float4 r0 = __ldg(&dy[d].r0), r1 = __ldg(&dy[d].r1);
-        uint32_t sl = __float_as_uint(r0.x);
-        int si = sl & 0xff, sj = (sl >> 8) & 0xff, sk = sl >> 24;
-        float2 pi = P[si * 32], pj = P[sj * 32];
-        float ei = E[si * 32], ej = E[sj * 32];
-        float dx = pj.x - pi.x, dy_ = pj.y - pi.y;
-        float d2 = fmaf(dx, dx, dy_ * dy_);
-        float rd = rsqrtf(d2);
-        float dd = d2 * rd;
-        float s2 = r0.y - dd, s3 = dd - r0.z;
-        float D = ((dd + r0.y) * s2) * (s3 * (dd + r0.z));
-        float rD = rsqrtf(D);
-        float isg = r1.x * rD;
-        float del = ei + ej + r1.y;
-        float slack = fminf(s2, s3);
-        lockw = fminf(lockw, slack + del);
-        zmin = min_nan(zmin, slack - del);
-        isgmax = fmaxf(isgmax, isg);
-        float hinv = 0.5f * (rd * rd);
-        float a = (d2 + r0.w) * hinv, bq = (D * rD) * hinv;
-        P[sk * 32] = make_float2(fmaf(a, dx, fmaf(-bq, dy_, pi.x)), fmaf(a, dy_, fmaf(bq, dx, pi.y)));
-        E[sk * 32] = del * isg;
-      }
-    }
+    const int ndl = has ? nd : 0;
+    const int ndw = __reduce_max_sync(kFull, (unsigned)ndl);
+    for (int d = 0; d < ndw; ++d)
+      if (d < ndl) fp32_dyad(rec + d, Pb, Eb, lockw, zmin, isgmax);
     const bool certain_lock = lockw < 0.0f;
     const bool amb = act && !certain_lock && !(zmin >= 0.0f);
-    float qstep = __frcp_rn(isgmax * isgmax);
+    float qstep = __fdividef(1.0f, isgmax * isgmax);
     bool locked = act && certain_lock;
     if (amb) {
       dwp loc[kMaxJ];
       float qd;
-      locked = dw_chain<false>(h, p.fixpos + b * ns, dy, __ldg(cs + t), loc, &qd);
+      locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), loc, &qd);
       qstep = qd;
     }
     const unsigned lb = __ballot_sync(kFull, locked) & gmask;
