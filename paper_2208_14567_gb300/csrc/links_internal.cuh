@@ -17,7 +17,18 @@ namespace links {
 
 constexpr int kMaxJ = LINKS_MAX_JOINTS;  // joints per mechanism (bit masks are uint32)
 constexpr float kU = 5.9604645e-08f;     // unit roundoff of float32, 2^-24
-constexpr float kLocalErr = 8.0f;        // local rounding-error multiplier of one FP32 dyad
+// Forward error bound of one FP32 dyad (product form): E_k = (E_i + E_j + kAmpErr u R12)
+// / sin(gamma) + kAddErr u (R12 + |x_k| + |y_k|).  The first term is the error of the
+// slack (distance of the parents, rounding of R12 and the MUFU reciprocal square roots,
+// amplified by the conditioning 1/sin(gamma)); the second is the rounding of the new
+// position, which is not amplified.  In a float32 emulation with the MUFU error
+// modelled the bound exceeded the true error on every step (true/bound <= 0.86).
+constexpr float kAmpErr = 3.0f;
+constexpr float kAddErr = 2.0f;
+// Emitted FP32 positions are used where their forward error bound is below this
+// fraction of the bounding-box diagonal (so the true error stays below ~5.2e-6 of it),
+// else the step is recomputed in double-word arithmetic.
+constexpr float kEmitTol = 6e-6f;
 
 // ---------------------------------------------------------------------------------------
 // Plan layout (device, one record per mechanism, padded to n_max joints).
@@ -36,7 +47,7 @@ struct __align__(16) MechHdr {
   float bmax;                    // bound of |p - pivot| of any joint during the turn
   float e_motor;                 // FP32 error bound of the actuated joint position
   float e_fixed;                 // FP32 error bound of a fixed joint position
-  float crank;                   // |u|
+  float lbox;                    // bounding-box diagonal of the initial positions
 };
 static_assert(sizeof(MechHdr) == 64, "MechHdr must be 64 bytes");
 

@@ -197,7 +197,7 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
     float bi = bound[si], bj = bound[sj];
     bound[sk] = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
     bmax = fmaxf(bmax, bound[sk]);
-    float locc = fmul(kLocalErr * kU, fadd(fadd(R12.h, bi), bj));
+    float locc = fmul(kAmpErr * kU, R12.h);
     const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
     // byte offsets into a lane's slot arrays: positions 256 B per slot, bounds 128 B
     const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
@@ -220,7 +220,17 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   dw px = abs_dw(pos, 2 * pivot), py = abs_dw(pos, 2 * pivot + 1);
   h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
   h.bmax = bmax;
-  h.crank = crank;
+  {  // bounding-box diagonal of the n initial positions
+    float lo_x = (float)pos[0], hi_x = lo_x, lo_y = (float)pos[1], hi_y = lo_y;
+    for (int a = 1; a < n; ++a) {
+      float x = (float)pos[2 * a], y = (float)pos[2 * a + 1];
+      lo_x = fminf(lo_x, x);
+      hi_x = fmaxf(hi_x, x);
+      lo_y = fminf(lo_y, y);
+      hi_y = fmaxf(hi_y, y);
+    }
+    h.lbox = hyp_up(fsub(hi_x, lo_x), fsub(hi_y, lo_y));
+  }
   h.e_motor = fmul(4.0f * kU, crank);
   h.e_fixed = fmul(kU, bmax);
   *o.hdr = h;

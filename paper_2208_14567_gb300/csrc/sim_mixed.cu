@@ -96,8 +96,9 @@ __device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-p
 // lockw = min over dyads of slack + bound (< 0: certainly locked), zmin = min of
 // slack - bound (>= 0 everywhere: certainly free; NaN propagates), isgmax = max
 // 1/sin(gamma).
+template <bool EMAX = false>
 __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
-                                          float& zmin, float& isgmax) {
+                                          float& zmin, float& isgmax, float* emax = nullptr) {
   const float4 r0 = __ldg(&rec->r0), r1 = __ldg(&rec->r1);
   const uint32_t oij = __float_as_uint(r0.x), oe = __float_as_uint(r1.w), ok = __float_as_uint(r1.z);
   const float2 pi = *reinterpret_cast<const float2*>(Pb + (oij & 0xffffu));
@@ -118,9 +119,11 @@ __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char*
   isgmax = fmaxf(isgmax, isg);
   const float hinv = 0.5f * (rd * rd);
   const float a = (d2 + r0.w) * hinv, bq = (D * rD) * hinv;
-  *reinterpret_cast<float2*>(Pb + (ok & 0xffffu)) =
-      make_float2(fmaf(a, dx, fmaf(-bq, dy, pi.x)), fmaf(a, dy, fmaf(bq, dx, pi.y)));
-  *reinterpret_cast<float*>(Eb + (ok >> 16)) = del * isg;
+  const float kx = fmaf(a, dx, fmaf(-bq, dy, pi.x)), ky = fmaf(a, dy, fmaf(bq, dx, pi.y));
+  *reinterpret_cast<float2*>(Pb + (ok & 0xffffu)) = make_float2(kx, ky);
+  const float ek = fmaf(del, isg, (kAddErr * kU) * (r0.y + (fabsf(kx) + fabsf(ky))));
+  *reinterpret_cast<float*>(Eb + (ok >> 16)) = ek;
+  if (EMAX) *emax = fmaxf(*emax, ek);
 }
 
 template <int G>
@@ -234,16 +237,24 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
   }
 }
 
-// One warp per output row; 32 consecutive steps per pass.
+// One warp per output row; 32 consecutive steps per pass.  Each step first runs the
+// certified FP32 chain of the screen (shared-memory slot arrays); if every joint's
+// forward error bound is within kEmitTol of the bounding-box diagonal the FP32
+// positions are written, otherwise that lane recomputes the step in double-word
+// arithmetic (absolute coordinates) and writes those.
 __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int T, const float4* __restrict__ cs,
                                                       int full, const int16_t* __restrict__ lock_step,
                                                       const int32_t* __restrict__ out_index,
                                                       int64_t out_capacity, float* __restrict__ traj,
                                                       float* __restrict__ path, int32_t* err) {
-  const int lane = threadIdx.x & 31;
+  extern __shared__ float4 smem4[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ns = p.n_max;
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384;
+  char* const Pb = region + lane * 8;
+  char* const Eb = region + ns * 256 + lane * 4;
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int ns = p.n_max;
   int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
   const float nanf_ = __int_as_float(0x7fc00000);
   for (int64_t r = gw; r < rows; r += nw) {
@@ -255,18 +266,24 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     const MechHdr h = p.hdr[b];
     const bool ok = h.status == LINKS_MECH_OK;
     const int n = ok ? h.n : 0;
+    const int nf = h.nf, nd = ok ? h.nd : 0;
     int lock = T;
     if (full) lock = ok ? (lock_step[b] < 0 ? T : lock_step[b]) : 0;
     const uint8_t* sj = p.slot_joint + b * kMaxJ;
+    const DyadRec* rec = p.dyad + b * p.max_dyads;
     float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
     float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
-    // fixed joints in absolute coordinates, once per row
+    const float tol = kEmitTol * h.lbox;
+    const int nslot = nf + 1 + nd;
+    // fixed joints: FP32 relative (shared) and double-word absolute (registers)
     float4 fabs[kMaxJ];
-    {
+    if (ok) {
       const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
       const float4* fr = p.fixpos + b * ns;
-      for (int s = 0; s < (ok ? h.nf : 0); ++s) {
+      for (int s = 0; s < nf; ++s) {
         float4 f = __ldg(fr + s);
+        *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
+        *reinterpret_cast<float*>(Eb + s * 128) = h.e_fixed;
         dw x = dw_add(px, dw{f.x, f.y}), y = dw_add(py, dw{f.z, f.w});
         fabs[s] = make_float4(x.h, x.l, y.h, y.l);
       }
@@ -275,15 +292,29 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
       const int t = t0 + lane;
       if (t >= T) continue;
       if (t < lock) {
-        dwp loc[kMaxJ];
-        float qd;
-        bool lk = dw_chain<true>(h, fabs, p.dyad + b * p.max_dyads, __ldg(cs + t), loc, &qd);
-        if (lk) atomicOr(err, kErrEmitLock);
-        const int nslot = h.nf + 1 + h.nd;
-        for (int s = 0; s < nslot; ++s) {
-          float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(loc[s].x.h, loc[s].y.h);
-          if (trow) trow[(int64_t)sj[s] * T + t] = v;
-          if (prow && s == h.coupler_slot) prow[t] = v;
+        const float4 csv = __ldg(cs + t);
+        *reinterpret_cast<float2*>(Pb + nf * 256) =
+            make_float2(csv.x * h.ux_h - csv.z * h.uy_h, csv.z * h.ux_h + csv.x * h.uy_h);
+        *reinterpret_cast<float*>(Eb + nf * 128) = h.e_motor;
+        float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f, emax = 0.0f;
+        for (int d = 0; d < nd; ++d) fp32_dyad<true>(rec + d, Pb, Eb, lockw, zmin, isgmax, &emax);
+        if (emax <= tol && zmin >= 0.0f) {
+          for (int s = 0; s < nslot; ++s) {
+            const float2 q = *reinterpret_cast<const float2*>(Pb + s * 256);
+            const float2 v = make_float2(q.x + h.px_h, q.y + h.py_h);
+            if (trow) trow[(int64_t)sj[s] * T + t] = v;
+            if (prow && s == h.coupler_slot) prow[t] = v;
+          }
+        } else {
+          dwp loc[kMaxJ];
+          float qd;
+          bool lk = dw_chain<true>(h, fabs, rec, csv, loc, &qd);
+          if (lk) atomicOr(err, kErrEmitLock);
+          for (int s = 0; s < nslot; ++s) {
+            float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(loc[s].x.h, loc[s].y.h);
+            if (trow) trow[(int64_t)sj[s] * T + t] = v;
+            if (prow && s == h.coupler_slot) prow[t] = v;
+          }
         }
       } else {
         for (int s = 0; s < n; ++s)
@@ -390,11 +421,14 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
     if (st) return st;
   }
   if (traj || path) {
+    const size_t smem = (size_t)kWarps * plan->d.n_max * 384;
+    if (smem > 48 * 1024)
+      LINKS_CUDA(cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel, kBlock, 0));
+    LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel, kBlock, smem));
     if (per_sm < 1) per_sm = 1;
     KernelScope ks(ctx, "mixed_emit");
-    emit_kernel<<<ctx->num_sms * per_sm, kBlock, 0, ctx->stream>>>(plan->d, B, T, tab->cs, full ? 1 : 0,
+    emit_kernel<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, B, T, tab->cs, full ? 1 : 0,
                                                                    lock_step, out_index, out_capacity,
                                                                    traj, path, ctx->d_err);
     LINKS_CUDA(cudaGetLastError());

@@ -119,11 +119,15 @@ def test_alone_equals_mix_equals_batch_path(L):
     x = refp[same]
     g = paths[(ref.valid == 1)[valid == 1]] if valid.sum() == ref.valid.sum() else None
     if g is not None:
+        # normalisation amplifies the (<= 1e-5 L) position error by about 1/gap of the
+        # principal axes: compare points where axis and sign are well determined, and
+        # the rotation-invariant radii everywhere
         sxx, syy = (x[..., 0] ** 2).mean(1), (x[..., 1] ** 2).mean(1)
-        ok = ((sxx - syy) / (sxx + syy) > 1e-3) & (np.abs((x[..., 0] ** 3).mean(1)) > 1e-3)
+        ok = ((sxx - syy) / (sxx + syy) > 0.1) & (np.abs((x[..., 0] ** 3).mean(1)) > 0.05)
         assert np.abs(g[ok] - x[ok]).max() <= 1e-4
+        assert np.abs(np.linalg.norm(g, axis=-1) - np.linalg.norm(x, axis=-1)).max() <= 1e-4
         print(f"serve: {len(reqs)} requests, {allb.B} candidates, {int(valid.sum())} valid, "
-              f"max normalised path error {np.abs(g[ok] - x[ok]).max():.2e}")
+              f"max normalised path error {np.abs(g[ok] - x[ok]).max():.2e} ({int(ok.sum())} well-conditioned)")
 
 
 def test_admission_timeout_and_refusals(L):
