@@ -203,13 +203,22 @@ def path_stage(args, local, stream):
         idx = torch.empty((Q, k), dtype=torch.int32, device=dev)
         dist = torch.empty((Q, k), dtype=torch.float32, device=dev)
         L.links_chamfer_topk(ctx, qn[:8], db_n, k, idx[:8], dist[:8])  # warm-up (workspace)
-        L.links_workspace_reserve(ctx, Q * 64 * k * 8)
+        L.links_workspace_reserve(ctx, Q * 64 * k * 8 + Q * 7220 + 256)
         torch.cuda.synchronize(dev)
         e0.record(stream)
         L.links_chamfer_topk(ctx, qn, db_n, k, idx, dist)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         cms = e0.elapsed_time(e1)
+        # the exhaustive search (pruning off) on a slice of the queries, for comparison
+        Qx = min(Q, 64)
+        L.links_set_chamfer_prune(ctx, False)
+        e0.record(stream)
+        L.links_chamfer_topk(ctx, qn[:Qx], db_n, k, idx[:Qx], dist[:Qx])
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        L.links_set_chamfer_prune(ctx, True)
+        xms = e0.elapsed_time(e1) * Q / Qx
         pairs = Q * M * T * T
         hbm = peaks()["hbm_gbs"]
         nbytes = 2 * M * T * 8
@@ -217,7 +226,9 @@ def path_stage(args, local, stream):
             "normalize": {"curves": M, "T": T, "ms": nms, "curves_per_s": M / (nms * 1e-3),
                           "GB_per_s": nbytes / (nms * 1e-3) / 1e9, "hbm_frac": nbytes / (nms * 1e-3) / 1e9 / hbm},
             "chamfer_topk": {"queries": Q, "database": M, "T": T, "k": k, "ms": cms,
-                             "queries_per_s": Q / (cms * 1e-3), "point_pairs_per_s": pairs / (cms * 1e-3),
+                             "queries_per_s": Q / (cms * 1e-3),
+                             "exhaustive_ms": xms, "exhaustive_sample_queries": Qx,
+                             "exhaustive_point_pairs_per_s": pairs / (xms * 1e-3),
                              "median_top1": float(dist[:, 0].median().item())},
         }
     finally:

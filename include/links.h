@@ -174,10 +174,20 @@ LINKS_API int links_normalize(links_ctx ctx, int64_t M, int T, const float* curv
  * (device float32 [Q,T,2] and [M,T,2]; 1 <= T <= 256).  Writes the k smallest per
  * query (1 <= k <= 32), ascending, ties to the lower database index: idx [Q,k]
  * int32 (-1 past M) and dist [Q,k] float32 (device).  Uses the context's workspace
- * (Q x chunks x k x 8 bytes, grown on demand; reserve it with
+ * (Q x chunks x k x 8 bytes, plus Q x 7220 bytes of distance tables with pruning on,
+ * chunks <= 8 x SMs / ceil(Q/8) + 1; grown on demand, so reserve it with
  * links_workspace_reserve before a graph capture).  Asynchronous. */
 LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
                                  const float* db, int k, int32_t* idx, float* dist);
+/* Switches the exact pruning of links_chamfer_topk on (1, default) or off (0).  With
+ * it on, the column term of each database curve's CD is first bounded from below
+ * through a table of the query's distance field (DT(c) >= DT(v) - |c - v| for a grid
+ * node v), and the exact computation stops once its partial column sum passes the
+ * smallest k-th distance found so far for the query (in any database chunk); curves
+ * ruled out either way cannot enter the top-k, so the result is the same bit for
+ * bit, only the work differs.  LINKS_EINVAL
+ * for a NULL ctx or a flag other than 0 or 1. */
+LINKS_API int links_set_chamfer_prune(links_ctx ctx, int on);
 /* Makes the context's workspace at least `bytes` large (allocates; not inside a
  * capture). */
 LINKS_API int links_workspace_reserve(links_ctx ctx, size_t bytes);

@@ -394,7 +394,7 @@ int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* quer
   if (Q > 0 && (!queries || !idx || !dist || (M > 0 && !db)))
     return set_error(LINKS_EINVAL, "links_chamfer_topk: NULL pointer");
   LINKS_CUDA(cudaSetDevice(ctx->device));
-  return chamfer_topk(ctx, Q, M, T, queries, db, k, idx, dist);
+  return chamfer_topk(ctx, Q, M, T, queries, db, k, idx, dist, ctx->chamfer_prune);
 }
 
 int links_profile(links_ctx ctx, int enable) {
@@ -453,6 +453,13 @@ int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes) {
   const TTable* tab = get_table(ctx, T, &st);
   if (!tab) return st;
   return autotune_screen(ctx, plan, tab, lanes);
+}
+
+int links_set_chamfer_prune(links_ctx ctx, int on) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_set_chamfer_prune: NULL ctx");
+  if (on != 0 && on != 1) return set_error(LINKS_EINVAL, "links_set_chamfer_prune: flag must be 0 or 1");
+  ctx->chamfer_prune = on;
+  return LINKS_OK;
 }
 
 int links_set_screen_lanes(links_ctx ctx, int n_max, int lanes) {

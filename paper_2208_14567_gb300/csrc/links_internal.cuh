@@ -121,6 +121,7 @@ struct links_ctx_s {
   size_t ws_bytes = 0;
   links::ServeState* serve = nullptr;
   std::map<int, int> screen_lanes;  // autotuned lanes per mechanism, by n_max
+  int chamfer_prune = 1;             // lower-bound pruning in links_chamfer_topk
 };
 
 struct links_plan_s {
@@ -151,7 +152,7 @@ int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out
 // Same, for the first *M_dev of at most M_cap curves (count read on the device).
 int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, int T, const float* in, float* out);
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,
-                 float* dist);
+                 float* dist, int prune);
 
 // Brackets one kernel launch: counts it and, while profiling, records events around it.
 struct KernelScope {

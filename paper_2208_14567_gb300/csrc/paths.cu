@@ -15,6 +15,8 @@
 //   (an 8-lane min per database point).  No tensor cores: the inner dimension is 2.
 //   Each warp keeps a running top-k in registers; a second kernel merges the partial
 //   lists of the database chunks.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "links_internal.cuh"
@@ -113,9 +115,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const 
 
 // ------------------------------------------------------------------------- chamfer
 
-constexpr int kCWarps = 8;   // queries per CTA
 constexpr int kStage = 32;   // database curves per shared-memory stage
-constexpr int kMaxK = 32;
 constexpr float kFar = 1e18f;
 
 __device__ __forceinline__ bool lex_less(float d, int i, float d2, int i2) {
@@ -169,88 +169,382 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
   return r;
 }
 
-// PL (even) query points per lane, held as PL/2 packed pairs; database points are
-// taken two at a time, so each block of 2 x 2 point pairs costs 8 packed arithmetic
-// instructions and 4 three-input minima.
+// ---- exact pruning
+//
+// Column term.  DT(x) = min over query points p of |x - p| is 1-Lipschitz, so for a
+// database point c and any grid node v, min_p |c - p| = DT(c) >= DT(v) - |c - v|.
+// The column term of CD (mean over c of DT(c)) is therefore bounded below by the
+// mean of max(0, DT(v(c)) - |c - v(c)|), v(c) the node nearest to c: one table
+// look-up per database point.  The table holds DT at kNG x kNG nodes over the query's
+// bounding square with a margin, rounded down to half precision.
+//
+// Row term.  The database curve's points are split into runs of 8 consecutive
+// points with centre z_g; rho bounds |c - z_g| for every point of every run.  A
+// query point p is then at least min_g |p - z_g| - rho from the curve, which costs
+// ceil(T/8) instead of T distance evaluations per query point.
+
+constexpr int kNG = 60;                       // grid nodes per side (7200-byte table)
+constexpr int kMaxG = 32;                     // runs of 8 points per curve (T <= 256)
+constexpr float kLbShrink = 1.0f - 0x1p-20f;  // covers the rounding of computed distances
+constexpr float kLbGrow = 1.0f + 0x1p-20f;    // (relative error below 2^-21.9 each)
+constexpr float kRound = 12582912.0f;         // 1.5 * 2^23: x + kRound rounds x to an integer
+
+// Hardware reciprocal square root (relative error at most 2^-22.9; +inf at 0, so
+// d2 * rsqrt_approx(d2) is NaN there and the caller's fmaxf drops the term, which
+// only lowers the bound).
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// One CTA per query: node spacing and origin, then DT at every node (brute force).
+// Also resets the query's shared pruning distance.
+__global__ void __launch_bounds__(256) dt_grid_kernel(int Q, int T, const float2* __restrict__ qs,
+                                                      __half* __restrict__ grids, float4* __restrict__ gparam,
+                                                      float* __restrict__ gthr) {
+  __shared__ float2 pts[256];
+  __shared__ float red[4][8];
+  const int q = blockIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  float2 v = t < T ? qs[(int64_t)q * T + t] : make_float2(0.f, 0.f);
+  if (t < T) pts[t] = v;
+  float lo_x = t < T ? v.x : INFINITY, hi_x = t < T ? v.x : -INFINITY;
+  float lo_y = t < T ? v.y : INFINITY, hi_y = t < T ? v.y : -INFINITY;
+  for (int o = 16; o > 0; o >>= 1) {
+    lo_x = fminf(lo_x, __shfl_xor_sync(kFull, lo_x, o));
+    hi_x = fmaxf(hi_x, __shfl_xor_sync(kFull, hi_x, o));
+    lo_y = fminf(lo_y, __shfl_xor_sync(kFull, lo_y, o));
+    hi_y = fmaxf(hi_y, __shfl_xor_sync(kFull, hi_y, o));
+  }
+  if (lane == 0) {
+    red[0][warp] = lo_x;
+    red[1][warp] = hi_x;
+    red[2][warp] = lo_y;
+    red[3][warp] = hi_y;
+  }
+  __syncthreads();
+  float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+  for (int w = 0; w < 8; ++w) {
+    x0 = fminf(x0, red[0][w]);
+    x1 = fmaxf(x1, red[1][w]);
+    y0 = fminf(y0, red[2][w]);
+    y1 = fmaxf(y1, red[3][w]);
+  }
+  float side = fmaxf(x1 - x0, y1 - y0);
+  if (!(side > 0.f)) side = 1.0f;  // one distinct point (or non-finite input)
+  const float h = side * 1.3f / (float)(kNG - 1);
+  const float ox = 0.5f * (x0 + x1) - 0.65f * side, oy = 0.5f * (y0 + y1) - 0.65f * side;
+  if (t == 0) {
+    gparam[q] = make_float4(ox, oy, h, 1.0f / h);
+    gthr[q] = INFINITY;
+  }
+  for (int node = t; node < kNG * kNG; node += blockDim.x) {
+    const int ix = node % kNG, iy = node / kNG;
+    const float nx = fmaf((float)ix, h, ox), ny = fmaf((float)iy, h, oy);
+    float m = INFINITY;
+    for (int j = 0; j < T; ++j) {
+      const float dx = pts[j].x - nx, dy = pts[j].y - ny;
+      m = fminf(m, fmaf(dy, dy, dx * dx));
+    }
+    grids[(int64_t)q * kNG * kNG + node] = __float2half_rd(sqrtf(m) * kLbShrink);
+  }
+}
+
+// The exact and the bounding computations run on 16-lane groups (two per warp):
+// lane gl of a group holds query points gl * PL + i (i < PL), packed in pairs;
+// points past T sit far away, so they never give a column minimum, and their row
+// minima are left out of the sums.
 template <int PL>
-__global__ void __launch_bounds__(256) chamfer_kernel(int Q, int64_t M, int T, const float2* __restrict__ qs,
-                                                      const float2* __restrict__ db, int k, int64_t chunk,
-                                                      float* __restrict__ part_d, int32_t* __restrict__ part_i) {
-  static_assert(PL % 2 == 0, "query points are processed in pairs");
-  extern __shared__ float2 stage[];  // [kStage][T]
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int g = lane >> 3, gl = lane & 7;
-  const unsigned gmask = 0xffu << (g * 8);
-  const int q = blockIdx.x * kCWarps + warp;
-  const int64_t c0 = (int64_t)blockIdx.y * chunk;
-  const int64_t c1 = min(M, c0 + chunk);
-  // this lane's query points p = gl * PL + i; padding points sit far away, so they
-  // never give a column minimum, and their row minima are left out of the sum
-  f2 QX[PL / 2], QY[PL / 2];
+__device__ __forceinline__ void load_query(const float2* qp, int T, int gl, f2* QX, f2* QY) {
 #pragma unroll
   for (int i = 0; i < PL / 2; ++i) {
-    int t = gl * PL + 2 * i;
-    float2 a = (q < Q && t < T) ? qs[(int64_t)q * T + t] : make_float2(kFar, kFar);
-    float2 b = (q < Q && t + 1 < T) ? qs[(int64_t)q * T + t + 1] : make_float2(kFar, kFar);
+    const int t = gl * PL + 2 * i;
+    const float2 a = t < T ? qp[t] : make_float2(kFar, kFar);
+    const float2 b = t + 1 < T ? qp[t + 1] : make_float2(kFar, kFar);
     QX[i] = pk2(a.x, b.x);
     QY[i] = pk2(a.y, b.y);
   }
+}
+
+__device__ __forceinline__ float group_sum16(float v, unsigned gmask) {
+  v += __shfl_xor_sync(gmask, v, 1);
+  v += __shfl_xor_sync(gmask, v, 2);
+  v += __shfl_xor_sync(gmask, v, 4);
+  v += __shfl_xor_sync(gmask, v, 8);
+  return v;
+}
+
+// Squared distances of this lane's query points to database point (ax, ay), folded
+// into the row minima (rmin) and returned as the lane's minimum (column minimum).
+template <int PL>
+__device__ __forceinline__ void fold_point4(const f2* QX, const f2* QY, const float2* c, float* rmin, float* m) {
+  f2 CX[4], CY[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    CX[u] = pk2(c[u].x, c[u].x);
+    CY[u] = pk2(c[u].y, c[u].y);
+  }
+#pragma unroll
+  for (int i = 0; i < PL / 2; ++i) {
+    float2 e[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const f2 dx = sub2(QX[i], CX[u]), dy = sub2(QY[i], CY[u]);
+      e[u] = up2(fma2(dy, dy, mul2(dx, dx)));
+      m[u] = min3(m[u], e[u].x, e[u].y);
+    }
+    rmin[2 * i] = min3(min3(rmin[2 * i], e[0].x, e[1].x), e[2].x, e[3].x);
+    rmin[2 * i + 1] = min3(min3(rmin[2 * i + 1], e[0].y, e[1].y), e[2].y, e[3].y);
+  }
+}
+
+// Minimum of four per-lane values over the 16-lane group, transposed: after the
+// exchange the lane holds the minimum of value v = 2 * (gl >> 3) + ((gl >> 2) & 1)
+// (five shuffles for four values instead of sixteen).
+__device__ __forceinline__ float group_min4(const float* m, int gl, unsigned gmask) {
+  const bool hi = gl & 8, b4 = gl & 4;
+  const float k0 = hi ? m[2] : m[0], k1 = hi ? m[3] : m[1];
+  const float s0 = hi ? m[0] : m[2], s1 = hi ? m[1] : m[3];
+  const float a0 = fminf(k0, __shfl_xor_sync(gmask, s0, 8));
+  const float a1 = fminf(k1, __shfl_xor_sync(gmask, s1, 8));
+  float v = fminf(b4 ? a1 : a0, __shfl_xor_sync(gmask, b4 ? a0 : a1, 4));
+  v = fminf(v, __shfl_xor_sync(gmask, v, 2));
+  return fminf(v, __shfl_xor_sync(gmask, v, 1));
+}
+
+// Row-term lower bound: mean over query points of max(0, min_g |p - z_g| - rho),
+// computed by the 16-lane group (all lanes return the same value).
+template <int PL>
+__device__ __forceinline__ float row_bound(const f2* QX, const f2* QY, const float2* cz, int G, float rho, int T,
+                                           int gl, unsigned gmask, float invT) {
+  float rmin[PL];
+#pragma unroll
+  for (int i = 0; i < PL; ++i) rmin[i] = INFINITY;
+  for (int g = 0; g < G; g += 4) {
+    float2 c[4];
+    float m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = cz[g + u < G ? g + u : g];  // repeats change no minimum
+      m[u] = INFINITY;
+    }
+    fold_point4<PL>(QX, QY, c, rmin, m);
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int i = 0; i < PL; ++i)
+    if (gl * PL + i < T) s += fmaxf(fmaf(sqrtf(rmin[i]), kLbShrink, -rho), 0.f);
+  return group_sum16(s, gmask) * invT;
+}
+
+// Exact CD of the query (this lane's PL points, packed) and database curve cp,
+// computed by the lane's 16-lane group (all lanes return the same value).  Returns
+// +inf as soon as the partial column sum alone exceeds thr: the full value can only
+// be larger (the sums only add non-negative terms), so such a curve cannot enter.
+template <int PL>
+__device__ __forceinline__ float chamfer_exact(const f2* QX, const f2* QY, const float2* cp, int T, int gl,
+                                               unsigned gmask, float invT, float thr) {
+  float rmin[PL];
+#pragma unroll
+  for (int i = 0; i < PL; ++i) rmin[i] = INFINITY;
+  const int v = 2 * (gl >> 3) + ((gl >> 2) & 1);  // the database point this lane sums
+  float csum = 0.f;                               // over the points j + v
+  for (int j = 0; j < T; j += 4) {
+    float2 c[4];
+    float m[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      c[u] = cp[j + u < T ? j + u : j];  // repeats change no row minimum
+      m[u] = INFINITY;
+    }
+    fold_point4<PL>(QX, QY, c, rmin, m);
+    const float mv = group_min4(m, gl, gmask);
+    if (j + v < T) csum += sqrtf(mv);
+    if ((j & 15) == 12) {  // every 16 points: stop once the column sum alone passes thr
+      float cs = csum + __shfl_xor_sync(gmask, csum, 4);
+      cs += __shfl_xor_sync(gmask, cs, 8);
+      if (cs * invT > thr) return INFINITY;  // uniform in the group
+    }
+  }
+  float cs = csum + __shfl_xor_sync(gmask, csum, 4);
+  cs += __shfl_xor_sync(gmask, cs, 8);
+  float rsum = 0.f;
+#pragma unroll
+  for (int i = 0; i < PL; ++i)
+    if (gl * PL + i < T) rsum += sqrtf(rmin[i]);
+  rsum = group_sum16(rsum, gmask);
+  return (rsum + cs) * invT;
+}
+
+// W queries per CTA (one warp each, which keeps the query's top-k), one chunk of the
+// database per CTA column, staged kStage curves at a time.  Per stage, with pruning:
+//   A. lane s of warp w bounds the column term of (query w, curve s) with the
+//      query's distance table; pairs whose bound exceeds the pruning distance drop;
+//   B. the CTA's 16-lane groups share out the remaining pairs and add the row-term
+//      bound; pairs over the pruning distance drop again;
+//   C. the groups share out the rest and compute exact CDs (stopping early once the
+//      partial column sum passes the pruning distance), and each warp inserts its
+//      query's results into its top-k.
+// Without pruning every pair goes to C.  The pruning distance of a query is the
+// smaller of its warp's current k-th distance and the query's shared one, the
+// smallest k-th distance any chunk has published: either is the k-th smallest CD of
+// some k database curves, so a curve whose CD is larger cannot be among the k
+// nearest, and the result is the exhaustive one; only the work depends on timing.
+// Both bounds carry a relative rounding error below 2e-5 (sums of at most 256
+// terms), as does the exact CD; the comparison margin covers both.  Sharing the
+// pairs of a stage among all groups keeps the warps' work equal between barriers.
+template <int PL, int W>
+__global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T, const float2* __restrict__ qs,
+                                                         const float2* __restrict__ db, int k, int64_t chunk,
+                                                         float* __restrict__ part_d, int32_t* __restrict__ part_i,
+                                                         const __half* __restrict__ grids,
+                                                         const float4* __restrict__ gparam, float* gthr) {
+  static_assert(PL % 2 == 0, "query points are processed in pairs");
+  constexpr int kGroups = W * 2;
+  extern __shared__ __align__(16) float2 dyn[];
+  float2* stage = dyn;                     // [kStage][T] database curves
+  float2* qpts = stage + kStage * T;       // [W][T] the CTA's queries
+  float2* cen = qpts + W * T;              // [kStage][kMaxG] run centres (pruning)
+  __half* sgrid = reinterpret_cast<__half*>(cen + kStage * kMaxG);  // [W][kNG^2] (pruning)
+  __shared__ unsigned rho_s[kStage];       // run radius per staged curve (float bits)
+  __shared__ float thr_w[W];
+  __shared__ uint16_t listA[W * kStage], listB[W * kStage];
+  __shared__ float lbA[W * kStage];
+  __shared__ int nA, nB, nres[W];
+  __shared__ float res_d[W][kStage];
+  __shared__ uint8_t res_s[W][kStage];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 4, gl = lane & 15, gid = warp * 2 + g;
+  const unsigned gmask = 0xffffu << (g * 16);
+  const int qbase = blockIdx.x * W, q = qbase + warp;
+  const int64_t c0 = (int64_t)blockIdx.y * chunk;
+  const int64_t c1 = min(M, c0 + chunk);
+  const bool prune = grids != nullptr;
+  const int G = (T + 7) / 8;
+  const float invT = 1.0f / (float)T;
+  const float margin = 4e-5f;
+  for (int x = threadIdx.x; x < W * T; x += blockDim.x) {
+    const int w = x / T;
+    qpts[x] = qbase + w < Q ? qs[(int64_t)qbase * T + x] : make_float2(kFar, kFar);
+  }
+  __half* mygrid = sgrid + warp * kNG * kNG;
+  float4 gp = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (prune && q < Q) {
+    const uint4* src = reinterpret_cast<const uint4*>(grids + (int64_t)q * kNG * kNG);
+    uint4* dst = reinterpret_cast<uint4*>(mygrid);
+    for (int x = lane; x < kNG * kNG / 8; x += 32) dst[x] = src[x];
+    gp = gparam[q];
+  }
   float kd = INFINITY;
   int ki = INT32_MAX;
-  const float invT = 1.0f / (float)T;
+  float thr_pub = INFINITY;  // last k-th distance published (lane k-1)
   for (int64_t base = c0; base < c1; base += kStage) {
     const int nst = c1 - base < kStage ? (int)(c1 - base) : kStage;
     __syncthreads();
     for (int x = threadIdx.x; x < nst * T; x += blockDim.x) stage[x] = db[base * T + x];
+    if (threadIdx.x < kStage) rho_s[threadIdx.x] = 0u;
+    if (threadIdx.x < W) nres[threadIdx.x] = 0;
+    if (threadIdx.x == 0) nA = nB = 0;
     __syncthreads();
-    if (q >= Q) continue;
-    for (int s0 = 0; s0 < nst; s0 += 4) {
-      const int s = s0 + g;
-      const bool live = s < nst;
-      const float2* cp = stage + (live ? s : 0) * T;
-      float rmin[PL];
-#pragma unroll
-      for (int i = 0; i < PL; ++i) rmin[i] = INFINITY;
-      float csum = 0.f;
-      for (int j = 0; j < T; j += 2) {
-        const float2 ca = cp[j];
-        const bool two = j + 1 < T;
-        const float2 cb = cp[two ? j + 1 : j];
-        const f2 AX = pk2(ca.x, ca.x), AY = pk2(ca.y, ca.y);
-        const f2 BX = pk2(cb.x, cb.x), BY = pk2(cb.y, cb.y);
-        float ma = INFINITY, mb = INFINITY;
-#pragma unroll
-        for (int i = 0; i < PL / 2; ++i) {
-          f2 dxa = sub2(QX[i], AX), dya = sub2(QY[i], AY);
-          f2 dxb = sub2(QX[i], BX), dyb = sub2(QY[i], BY);
-          float2 ea = up2(fma2(dya, dya, mul2(dxa, dxa)));
-          float2 eb = up2(fma2(dyb, dyb, mul2(dxb, dxb)));
-          rmin[2 * i] = min3(rmin[2 * i], ea.x, eb.x);
-          rmin[2 * i + 1] = min3(rmin[2 * i + 1], ea.y, eb.y);
-          ma = min3(ma, ea.x, ea.y);
-          mb = min3(mb, eb.x, eb.y);
+    if (prune) {  // run centres and radii of the staged curves
+      for (int x = threadIdx.x; x < nst * G; x += blockDim.x) {
+        const int s = x / G, r = x % G;
+        const float2* cp = stage + s * T + r * 8;
+        const int cnt = min(8, T - r * 8);
+        float zx = 0.f, zy = 0.f;
+        for (int i = 0; i < cnt; ++i) {
+          zx += cp[i].x;
+          zy += cp[i].y;
         }
-        ma = fminf(ma, __shfl_xor_sync(gmask, ma, 1));
-        mb = fminf(mb, __shfl_xor_sync(gmask, mb, 1));
-        ma = fminf(ma, __shfl_xor_sync(gmask, ma, 2));
-        mb = fminf(mb, __shfl_xor_sync(gmask, mb, 2));
-        ma = fminf(ma, __shfl_xor_sync(gmask, ma, 4));
-        mb = fminf(mb, __shfl_xor_sync(gmask, mb, 4));
-        csum += sqrtf(ma) + (two ? sqrtf(mb) : 0.f);
+        zx /= (float)cnt;
+        zy /= (float)cnt;
+        float r2 = 0.f;
+        for (int i = 0; i < cnt; ++i) {
+          const float dx = cp[i].x - zx, dy = cp[i].y - zy;
+          r2 = fmaxf(r2, fmaf(dy, dy, dx * dx));
+        }
+        cen[s * kMaxG + r] = make_float2(zx, zy);
+        atomicMax(&rho_s[s], __float_as_uint(fmaf(sqrtf(r2), kLbGrow, 1e-30f)));  // radii are >= 0
       }
-      float rsum = 0.f;
-#pragma unroll
-      for (int i = 0; i < PL; ++i)
-        if (gl * PL + i < T) rsum += sqrtf(rmin[i]);
-      rsum += __shfl_xor_sync(gmask, rsum, 1);
-      rsum += __shfl_xor_sync(gmask, rsum, 2);
-      rsum += __shfl_xor_sync(gmask, rsum, 4);
-      const float cd = live ? (rsum + csum) * invT : INFINITY;
-      // the four groups' results, inserted in database order
-#pragma unroll
-      for (int gg = 0; gg < 4; ++gg) {
-        float d = __shfl_sync(kFull, cd, gg * 8);
-        if (s0 + gg < nst) topk_insert(kd, ki, k, d, (int)(base + s0 + gg));
+    }
+    // A: this warp's query against the staged curves
+    if (q < Q) {
+      float thr = __shfl_sync(kFull, kd, k - 1);
+      if (prune) thr = fminf(thr, __ldcg(gthr + q));
+      if (lane == 0) thr_w[warp] = thr;
+      bool keep = lane < nst;
+      const bool bounded = prune && thr < INFINITY;
+      float lb = 0.f;
+      if (bounded && keep) {
+        // the walk starts at point s mod T so that the lanes' reads spread over banks
+        const float2* cp = stage + lane * T;
+        int t = lane % T;
+        for (int n = 0; n < T; ++n) {
+          const float2 c = cp[t];
+          t = t + 1 == T ? 0 : t + 1;
+          const float rx = fminf(fmaxf((c.x - gp.x) * gp.w, 0.f), (float)(kNG - 1)) + kRound;
+          const float ry = fminf(fmaxf((c.y - gp.y) * gp.w, 0.f), (float)(kNG - 1)) + kRound;
+          const int ix = __float_as_int(rx) - __float_as_int(kRound);
+          const int iy = __float_as_int(ry) - __float_as_int(kRound);
+          const float dx = c.x - fmaf(rx - kRound, gp.z, gp.x), dy = c.y - fmaf(ry - kRound, gp.z, gp.y);
+          const float dt = __half2float(mygrid[iy * kNG + ix]);
+          const float d2 = fmaf(dy, dy, dx * dx);
+          lb += fmaxf(fmaf(-d2 * rsqrt_approx(d2), kLbGrow, dt), 0.f);
+        }
+        lb *= invT;
+        keep = !(lb > thr + (margin * thr + 1e-6f));
+      }
+      const unsigned m = __ballot_sync(kFull, keep);
+      if (m) {
+        int at = 0;
+        if (lane == 0) at = atomicAdd(bounded ? &nA : &nB, __popc(m));
+        at = __shfl_sync(kFull, at, 0) + __popc(m & ((1u << lane) - 1u));
+        if (keep) {
+          if (bounded) {
+            listA[at] = (uint16_t)(warp * kStage + lane);
+            lbA[at] = lb;
+          } else {
+            listB[at] = (uint16_t)(warp * kStage + lane);
+          }
+        }
+      }
+    }
+    __syncthreads();
+    f2 QX[PL / 2], QY[PL / 2];
+    if (prune) {  // B: row-term bound on the survivors of A
+      const int n = nA;
+      for (int e = gid; e < n; e += kGroups) {
+        const int w = listA[e] / kStage, s = listA[e] % kStage;
+        load_query<PL>(qpts + w * T, T, gl, QX, QY);
+        const float lb = lbA[e] + row_bound<PL>(QX, QY, cen + s * kMaxG, G, __uint_as_float(rho_s[s]), T, gl,
+                                                gmask, invT);
+        const float thr = thr_w[w];
+        if (gl == 0 && !(lb > thr + (margin * thr + 1e-6f))) listB[atomicAdd(&nB, 1)] = listA[e];
+      }
+      __syncthreads();
+    }
+    {  // C: exact CDs
+      const int n = nB;
+      for (int e = gid; e < n; e += kGroups) {
+        const int w = listB[e] / kStage, s = listB[e] % kStage;
+        load_query<PL>(qpts + w * T, T, gl, QX, QY);
+        const float thr = thr_w[w];
+        const float d = chamfer_exact<PL>(QX, QY, stage + s * T, T, gl, gmask, invT, prune ? thr : INFINITY);
+        if (gl == 0 && d <= thr) {
+          const int at = atomicAdd(&nres[w], 1);
+          res_d[w][at] = d;
+          res_s[w][at] = (uint8_t)s;
+        }
+      }
+    }
+    __syncthreads();
+    if (q < Q) {
+      const int n = nres[warp];
+      for (int r = 0; r < n; ++r) topk_insert(kd, ki, k, res_d[warp][r], (int)(base + res_s[warp][r]));
+      if (prune && lane == k - 1 && kd < thr_pub) {  // publish this chunk's k-th distance
+        atomicMin(reinterpret_cast<unsigned*>(gthr + q), __float_as_uint(kd));  // CDs are >= 0
+        thr_pub = kd;
       }
     }
   }
@@ -288,34 +582,56 @@ __global__ void topk_merge_kernel(int Q, int nchunk, int k, const float* __restr
   }
 }
 
-template <int PL>
+template <int PL, int W>
 int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, const float2* db, int k,
-                   int32_t* idx, float* dist) {
-  // database chunks: enough CTAs to fill the GPU a few times over
-  const int qtiles = (Q + kCWarps - 1) / kCWarps;
+                   int32_t* idx, float* dist, int prune) {
+  const int qtiles = (Q + W - 1) / W;
   if (M == 0) {  // nothing to rank: idx = -1, dist = +inf
     KernelScope ks(ctx, "topk_merge");
     topk_merge_kernel<<<(Q * 32 + 255) / 256, 256, 0, ctx->stream>>>(Q, 0, k, nullptr, nullptr, idx, dist);
     LINKS_CUDA(cudaGetLastError());
     return LINKS_OK;
   }
-  int64_t want = (int64_t)ctx->num_sms * 8;
-  int64_t nchunk = std::max<int64_t>(1, std::min<int64_t>((want + qtiles - 1) / qtiles, (M + kStage - 1) / kStage));
-  nchunk = std::min<int64_t>(nchunk, 65535);
+  // database chunks: one CTA per SM at a time; at least four waves, the CTA count
+  // a multiple of the SM count where the chunk count allows
+  const int64_t max_chunks = (M + kStage - 1) / kStage;
+  const int64_t sms = ctx->num_sms;
+  int64_t nchunk = std::max<int64_t>(1, (4 * sms + qtiles - 1) / qtiles);
+  for (int64_t c = nchunk; c <= 2 * nchunk; ++c)
+    if ((c * qtiles) % sms == 0) {
+      nchunk = c;
+      break;
+    }
+  nchunk = std::min<int64_t>(std::min<int64_t>(nchunk, max_chunks), 65535);
   int64_t chunk = (M + nchunk - 1) / nchunk;
   chunk = (chunk + kStage - 1) / kStage * kStage;
   nchunk = (M + chunk - 1) / chunk;
-  const size_t need = (size_t)Q * nchunk * k * (sizeof(float) + sizeof(int32_t));
+  const size_t part_bytes = (size_t)Q * nchunk * k * (sizeof(float) + sizeof(int32_t));
+  const size_t grid_off = (part_bytes + 255) / 256 * 256;
+  const size_t grid_bytes = prune ? (size_t)Q * kNG * kNG * sizeof(__half) : 0;
+  const size_t param_off = grid_off + grid_bytes;
+  const size_t thr_off = param_off + (prune ? (size_t)Q * sizeof(float4) : 0);
+  const size_t need = thr_off + (prune ? (size_t)Q * sizeof(float) : 0);
   int st = ensure_workspace(ctx, need);
   if (st) return st;
-  float* part_d = reinterpret_cast<float*>(ctx->ws);
+  char* ws = reinterpret_cast<char*>(ctx->ws);
+  float* part_d = reinterpret_cast<float*>(ws);
   int32_t* part_i = reinterpret_cast<int32_t*>(part_d + (size_t)Q * nchunk * k);
-  const size_t smem = (size_t)kStage * T * sizeof(float2);
-  LINKS_CUDA(cudaFuncSetAttribute(chamfer_kernel<PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  __half* grids = prune ? reinterpret_cast<__half*>(ws + grid_off) : nullptr;
+  float4* gparam = prune ? reinterpret_cast<float4*>(ws + param_off) : nullptr;
+  float* gthr = prune ? reinterpret_cast<float*>(ws + thr_off) : nullptr;
+  if (prune) {
+    KernelScope ks(ctx, "dt_grid");
+    dt_grid_kernel<<<Q, 256, 0, ctx->stream>>>(Q, T, qs, grids, gparam, gthr);
+    LINKS_CUDA(cudaGetLastError());
+  }
+  const size_t smem = (size_t)(kStage + W) * T * sizeof(float2) +
+                      (prune ? (size_t)kStage * kMaxG * sizeof(float2) + (size_t)W * kNG * kNG * sizeof(__half) : 0);
+  LINKS_CUDA(cudaFuncSetAttribute(chamfer_kernel<PL, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
     KernelScope ks(ctx, "chamfer");
-    chamfer_kernel<PL><<<dim3(qtiles, (unsigned)nchunk), 256, smem, ctx->stream>>>(Q, M, T, qs, db, k, chunk,
-                                                                                  part_d, part_i);
+    chamfer_kernel<PL, W><<<dim3(qtiles, (unsigned)nchunk), W * 32, smem, ctx->stream>>>(
+        Q, M, T, qs, db, k, chunk, part_d, part_i, grids, gparam, gthr);
   }
   LINKS_CUDA(cudaGetLastError());
   {
@@ -351,16 +667,16 @@ int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, in
 }
 
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,
-                 float* dist) {
+                 float* dist, int prune) {
   if (Q == 0) return LINKS_OK;
   const float2* q2 = reinterpret_cast<const float2*>(q);
   const float2* d2 = reinterpret_cast<const float2*>(db);
-  const int pl = (T + 7) / 8;
-  if (pl <= 4) return launch_chamfer<4>(ctx, Q, M, T, q2, d2, k, idx, dist);
-  if (pl <= 8) return launch_chamfer<8>(ctx, Q, M, T, q2, d2, k, idx, dist);
-  if (pl <= 16) return launch_chamfer<16>(ctx, Q, M, T, q2, d2, k, idx, dist);
-  if (pl <= 26) return launch_chamfer<26>(ctx, Q, M, T, q2, d2, k, idx, dist);
-  return launch_chamfer<32>(ctx, Q, M, T, q2, d2, k, idx, dist);
+  const int pl = (T + 15) / 16;  // query points per lane of a 16-lane group
+  if (pl <= 2) return launch_chamfer<2, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
+  if (pl <= 4) return launch_chamfer<4, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
+  if (pl <= 8) return launch_chamfer<8, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
+  if (pl <= 14) return launch_chamfer<14, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
+  return launch_chamfer<16, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
 }
 
 }  // namespace links

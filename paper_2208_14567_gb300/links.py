@@ -82,6 +82,7 @@ def lib():
             "links_compact_valid_static": ([P, i64, P, i64, P, P], i32),
             "links_autotune": ([P, P, i32, P], i32),
             "links_set_screen_lanes": ([P, i32, i32], i32),
+            "links_set_chamfer_prune": ([P, i32], i32),
             "links_capture_begin": ([P], i32),
             "links_capture_end": ([P, P], i32),
             "links_graph_launch": ([P, P], i32),
@@ -333,6 +334,10 @@ def links_autotune(ctx, plan, T: int) -> int:
     lanes = ctypes.c_int()
     _check(lib().links_autotune(ctx, plan, int(T), ctypes.byref(lanes)), "links_autotune")
     return lanes.value
+
+
+def links_set_chamfer_prune(ctx, on: bool):
+    _check(lib().links_set_chamfer_prune(ctx, 1 if on else 0), "links_set_chamfer_prune")
 
 
 def links_set_screen_lanes(ctx, n_max: int, lanes: int):

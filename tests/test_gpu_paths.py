@@ -166,3 +166,23 @@ def test_chamfer_rejects_bad_sizes(L, ctx):
     q = torch.zeros((2, 200, 2), dtype=torch.float32, device="cuda")
     with pytest.raises(L.LinksError):
         L.links_chamfer_topk(ctx, q, q, 33, idx, dist)  # k > 32
+
+
+@pytest.mark.parametrize("T,M,Q,k", [(200, 20000, 40, 10), (64, 5000, 33, 32), (13, 3000, 9, 3), (2, 2000, 7, 5)])
+def test_chamfer_pruning_changes_nothing(L, ctx, T, M, Q, k):
+    """The lower-bound pruning only skips curves that cannot enter the top-k, so the
+    pruned and the exhaustive search agree bit for bit, near-duplicates included."""
+    curves = O.normalize(coupler_curves(M // 4 + Q, T, seed=300 + T)).astype(np.float32)
+    base, held = curves[:M // 4], curves[M // 4:]
+    # the database: each curve 4 times, three of them slightly perturbed (near-ties)
+    db = np.concatenate([base] + [I.perturb_curves(base, s, seed=s_i) for s_i, s in enumerate((1e-6, 1e-4, 1e-2))])
+    db = db[np.random.default_rng(T).permutation(len(db))].astype(np.float32)
+    q = np.concatenate([I.perturb_curves(held, 0.02, seed=T), db[:3]]).astype(np.float32)
+    L.links_set_chamfer_prune(ctx, False)
+    idx0, dist0 = gpu_topk(L, ctx, q, db, k)
+    L.links_set_chamfer_prune(ctx, True)
+    idx1, dist1 = gpu_topk(L, ctx, q, db, k)
+    assert np.array_equal(idx0, idx1) and np.array_equal(dist0, dist1)
+    sel = np.random.default_rng(T).choice(len(q), 6, replace=False)
+    check_topk(q[sel], db, idx1[sel], dist1[sel], k, f"pruned T={T} M={len(db)}")
+    assert L.lib().links_set_chamfer_prune(ctx, 2) == L.EINVAL

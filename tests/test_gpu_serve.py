@@ -117,17 +117,27 @@ def test_alone_equals_mix_equals_batch_path(L):
     refp = O.normalize(ref.path[ref.valid == 1])
     same = (valid == ref.valid)[ref.valid == 1]
     x = refp[same]
-    g = paths[(ref.valid == 1)[valid == 1]] if valid.sum() == ref.valid.sum() else None
-    if g is not None:
-        # normalisation amplifies the (<= 1e-5 L) position error by about 1/gap of the
-        # principal axes: compare points where axis and sign are well determined, and
-        # the rotation-invariant radii everywhere
-        sxx, syy = (x[..., 0] ** 2).mean(1), (x[..., 1] ** 2).mean(1)
-        ok = ((sxx - syy) / (sxx + syy) > 0.1) & (np.abs((x[..., 0] ** 3).mean(1)) > 0.05)
-        assert np.abs(g[ok] - x[ok]).max() <= 1e-4
-        assert np.abs(np.linalg.norm(g, axis=-1) - np.linalg.norm(x, axis=-1)).max() <= 1e-4
-        print(f"serve: {len(reqs)} requests, {allb.B} candidates, {int(valid.sum())} valid, "
-              f"max normalised path error {np.abs(g[ok] - x[ok]).max():.2e} ({int(ok.sum())} well-conditioned)")
+    g = paths[(ref.valid == 1)[valid == 1]]
+    # positions carry up to 1e-5 L of error (L = bounding-box diagonal of the
+    # mechanism); normalisation divides by the path's RMS radius r, so the error of a
+    # normalised point is about 1e-5 L / r, and the rotation adds that over the gap of
+    # the principal axes.  Compare points where axis and sign are well determined, and
+    # the rotation-invariant radii everywhere.
+    Lb = bbox_diag(allb.pos, allb.n_joints)[ref.valid == 1][same]
+    raw = ref.path[ref.valid == 1][same]
+    rms = np.sqrt(((raw - raw.mean(1, keepdims=True)) ** 2).sum(-1).mean(1))
+    amp = 1e-5 * Lb / rms
+    sxx, syy = (x[..., 0] ** 2).mean(1), (x[..., 1] ** 2).mean(1)
+    gap = (sxx - syy) / (sxx + syy)
+    s3 = np.abs((x[..., 0] ** 3).mean(1))
+    ok = (gap > 100 * amp) & (s3 > 100 * amp)
+    err = np.abs(g - x).max(axis=(1, 2))
+    assert (err[ok] <= amp[ok] * (4 + 4 / gap[ok])).all()
+    rerr = np.abs(np.linalg.norm(g, axis=-1) - np.linalg.norm(x, axis=-1)).max(1)
+    assert (rerr <= 4 * amp).all()
+    print(f"serve: {len(reqs)} requests, {allb.B} candidates, {int(valid.sum())} valid, "
+          f"max normalised path error {err[ok].max():.2e} ({int(ok.sum())} well-conditioned), "
+          f"max error / (1e-5 L / r) {(err[ok] / (amp[ok] * (1 + 1 / gap[ok]))).max():.2f}")
 
 
 def test_admission_timeout_and_refusals(L):
