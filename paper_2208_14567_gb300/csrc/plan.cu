@@ -57,6 +57,61 @@ LINKS_HD dw2 rel(const double* pos, int a, int b) {
 LINKS_HD dw abs_dw(const float* pos, int c) { return dw_make(pos[c]); }
 LINKS_HD dw abs_dw(const double* pos, int c) { return dw_from_double(pos[c]); }
 LINKS_HD dw norm2(dw2 v) { return dw_add(dw_sqr(v.x), dw_sqr(v.y)); }
+
+// Per-mechanism scratch of the builder: neighbour masks, the joint of each slot's
+// dyad record (joint k, parents i, j), the slot of each joint and the position bound
+// of each slot.  For n_max <= 8 it is packed into bit fields and a float array read
+// by unrolled selects, so that the device thread keeps it in registers; larger
+// mechanisms use plain arrays.  Only the storage differs, not the arithmetic.
+template <int NJ>
+struct Scratch {
+  uint32_t nbv[NJ];
+  int slotv[NJ], dkv[NJ], div_[NJ], djv[NJ];
+  float bnd[NJ];
+  LINKS_HD uint32_t nb(int a) const { return nbv[a]; }
+  LINKS_HD void set_nb(int a, uint32_t m) { nbv[a] = m; }
+  LINKS_HD int slot(int a) const { return slotv[a]; }
+  LINKS_HD void set_slot(int a, int s) { slotv[a] = s; }
+  LINKS_HD void set_dyad(int d, int k, int i, int j) {
+    dkv[d] = k;
+    div_[d] = i;
+    djv[d] = j;
+  }
+  LINKS_HD int dk(int d) const { return dkv[d]; }
+  LINKS_HD int di(int d) const { return div_[d]; }
+  LINKS_HD int dj(int d) const { return djv[d]; }
+  LINKS_HD float bound(int s) const { return bnd[s]; }
+  LINKS_HD void set_bound(int s, float v) { bnd[s] = v; }
+};
+
+template <>
+struct Scratch<8> {
+  uint64_t nbw = 0;    // 8 bits per joint
+  uint32_t slotw = 0;  // 4 bits per joint
+  uint64_t dyw = 0;    // 9 bits per dyad (k, i, j: 3 bits each; at most 6 dyads)
+  float bnd[8];
+  LINKS_HD uint32_t nb(int a) const { return (uint32_t)(nbw >> (8 * a)) & 0xffu; }
+  LINKS_HD void set_nb(int a, uint32_t m) { nbw |= (uint64_t)(m & 0xffu) << (8 * a); }
+  LINKS_HD int slot(int a) const { return (int)((slotw >> (4 * a)) & 0xfu); }
+  LINKS_HD void set_slot(int a, int s) { slotw |= (uint32_t)s << (4 * a); }  // set once per joint
+  LINKS_HD void set_dyad(int d, int k, int i, int j) {
+    dyw |= (uint64_t)(k | (i << 3) | (j << 6)) << (9 * d);
+  }
+  LINKS_HD int dk(int d) const { return (int)(dyw >> (9 * d)) & 7; }
+  LINKS_HD int di(int d) const { return (int)(dyw >> (9 * d + 3)) & 7; }
+  LINKS_HD int dj(int d) const { return (int)(dyw >> (9 * d + 6)) & 7; }
+  LINKS_HD float bound(int s) const {
+    float r = 0.0f;
+#pragma unroll
+    for (int t = 0; t < 8; ++t) r = t == s ? bnd[t] : r;
+    return r;
+  }
+  LINKS_HD void set_bound(int s, float v) {
+#pragma unroll
+    for (int t = 0; t < 8; ++t)
+      if (t == s) bnd[t] = v;
+  }
+};
 LINKS_HD float u2f(uint32_t u) {
   union { uint32_t u; float f; } cv;
   cv.u = u;
@@ -67,18 +122,17 @@ LINKS_HD float hyp_up(float x, float y) {
   return fmul(fsqrt_rn(fadd(fmul(x, x), fmul(y, y))), 1.0f + 4.0f * kU);
 }
 
-template <typename PT>
+template <typename PT, int NJ>
 LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type, const PT* pos,
                        BuildOut o) {
   MechHdr h{};
   h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
   int status = LINKS_MECH_OK;
-  uint32_t nb[kMaxJ];
+  Scratch<NJ> S;
   uint32_t fixm = 0, simm = 0, motm = 0;
   int motor = -1, pivot = -1, nd = 0;
-  int dk[kMaxJ], di[kMaxJ], dj[kMaxJ];
 
-  if (n < 2 || n > n_max || n_max > kMaxJ) {
+  if (n < 2 || n > n_max || n_max > NJ) {
     status = LINKS_MECH_BAD_SIZE;
   } else {
     for (int a = 0; a < n && status == LINKS_MECH_OK; ++a) {
@@ -94,18 +148,18 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
       uint32_t m = 0;
       const uint8_t* row = adj + (size_t)a * n_max;
       for (int c = 0; c < n; ++c) m |= (row[c] != 0 ? 1u : 0u) << c;
-      nb[a] = m;
+      S.set_nb(a, m);
     }
     for (int a = 0; a < n && status == LINKS_MECH_OK; ++a) {
-      if (nb[a] & (1u << a)) status = LINKS_MECH_BAD_ADJ;
-      for (uint32_t m = nb[a]; m && status == LINKS_MECH_OK; m &= m - 1)
-        if (!((nb[ffs32(m)] >> a) & 1u)) status = LINKS_MECH_BAD_ADJ;
+      if (S.nb(a) & (1u << a)) status = LINKS_MECH_BAD_ADJ;
+      for (uint32_t m = S.nb(a); m && status == LINKS_MECH_OK; m &= m - 1)
+        if (!((S.nb(ffs32(m)) >> a) & 1u)) status = LINKS_MECH_BAD_ADJ;
     }
   }
   if (status == LINKS_MECH_OK && popc32(motm) != 1) status = LINKS_MECH_NO_MOTOR;
   if (status == LINKS_MECH_OK) {
     motor = ffs32(motm);
-    uint32_t pm = nb[motor] & fixm;
+    uint32_t pm = S.nb(motor) & fixm;
     if (!pm) status = LINKS_MECH_NO_PIVOT;
     else pivot = ffs32(pm);
   }
@@ -115,15 +169,13 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
       int pick = -1, cnt = 0;
       for (uint32_t u = unknown; u; u &= u - 1) {
         int a = ffs32(u);
-        int c = popc32(nb[a] & known);
+        int c = popc32(S.nb(a) & known);
         if (c >= 2) { pick = a; cnt = c; break; }
       }
       if (pick < 0) { status = LINKS_MECH_NOT_DYAD_SOLVABLE; break; }
       if (cnt > 2) { status = LINKS_MECH_OVERCONSTRAINED; break; }
-      uint32_t par = nb[pick] & known;
-      dk[nd] = pick;
-      di[nd] = ffs32(par);
-      dj[nd] = ffs32(par & (par - 1));
+      uint32_t par = S.nb(pick) & known;
+      S.set_dyad(nd, pick, ffs32(par), ffs32(par & (par - 1)));
       ++nd;
       known |= 1u << pick;
       unknown &= ~(1u << pick);
@@ -132,8 +184,8 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   if (status == LINKS_MECH_OK) {
     int e2 = 0, ff2 = 0;
     for (int a = 0; a < n; ++a) {
-      e2 += popc32(nb[a]);
-      if ((fixm >> a) & 1u) ff2 += popc32(nb[a] & fixm);
+      e2 += popc32(S.nb(a));
+      if ((fixm >> a) & 1u) ff2 += popc32(S.nb(a) & fixm);
     }
     int links_ = (e2 - ff2) / 2 - 1;  // minus the crank
     if (links_ != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
@@ -146,41 +198,43 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   }
 
   // Slots: fixed joints by index, then the actuated joint, then dyads in solve order.
-  int slot_of[kMaxJ];
   int nf = 0;
   for (uint32_t m = fixm; m; m &= m - 1) {
     int a = ffs32(m);
-    slot_of[a] = nf;
+    S.set_slot(a, nf);
     o.slot_joint[nf] = (uint8_t)a;
     ++nf;
   }
-  slot_of[motor] = nf;
+  S.set_slot(motor, nf);
   o.slot_joint[nf] = (uint8_t)motor;
   for (int d = 0; d < nd; ++d) {
-    slot_of[dk[d]] = nf + 1 + d;
-    o.slot_joint[nf + 1 + d] = (uint8_t)dk[d];
+    S.set_slot(S.dk(d), nf + 1 + d);
+    o.slot_joint[nf + 1 + d] = (uint8_t)S.dk(d);
   }
   for (int s = 0; s < n; ++s) {
     int a = o.slot_joint[s];
     o.pos64[s] = make_double2((double)pos[2 * a], (double)pos[2 * a + 1]);
   }
 
-  float bound[kMaxJ];
   float bmax = 0.0f;
-  for (int s = 0; s < nf; ++s) {
-    int a = o.slot_joint[s];
-    dw2 r = rel(pos, a, pivot);
-    o.fixpos[s] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
-    bound[s] = hyp_up(r.x.h, r.y.h);
-    bmax = fmaxf(bmax, bound[s]);
+  {
+    int s = 0;
+    for (uint32_t m = fixm; m; m &= m - 1, ++s) {
+      int a = ffs32(m);
+      dw2 r = rel(pos, a, pivot);
+      o.fixpos[s] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
+      const float bs = hyp_up(r.x.h, r.y.h);
+      S.set_bound(s, bs);
+      bmax = fmaxf(bmax, bs);
+    }
   }
   dw2 u = rel(pos, motor, pivot);
   float crank = hyp_up(u.x.h, u.y.h);
-  bound[nf] = crank;
+  S.set_bound(nf, crank);
   bmax = fmaxf(bmax, crank);
 
   for (int d = 0; d < nd; ++d) {
-    int k = dk[d], i = di[d], j = dj[d];
+    int k = S.dk(d), i = S.di(d), j = S.dj(d);
     dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
     dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
     if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
@@ -193,10 +247,11 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
     dw Rm = dw_sub(r1, r2);
     if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
     dw c = dw_sub(r1sq, r2sq);
-    int si = slot_of[i], sj = slot_of[j], sk = nf + 1 + d;
-    float bi = bound[si], bj = bound[sj];
-    bound[sk] = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
-    bmax = fmaxf(bmax, bound[sk]);
+    int si = S.slot(i), sj = S.slot(j), sk = nf + 1 + d;
+    float bi = S.bound(si), bj = S.bound(sj);
+    const float bk = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
+    S.set_bound(sk, bk);
+    bmax = fmaxf(bmax, bk);
     float locc = fmul(kAmpErr * kU, R12.h);
     const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
     // byte offsets into a lane's slot arrays: positions 256 B per slot, bounds 128 B
@@ -214,7 +269,7 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   h.nf = (uint8_t)nf;
   h.motor_joint = (uint8_t)motor;
   h.pivot_joint = (uint8_t)pivot;
-  h.pad0 = (uint8_t)slot_of[pivot];  // pivot slot
+  h.pad0 = (uint8_t)S.slot(pivot);  // pivot slot
   h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
   h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
   dw px = abs_dw(pos, 2 * pivot), py = abs_dw(pos, 2 * pivot + 1);
@@ -247,7 +302,7 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
   return o;
 }
 
-template <typename PT>
+template <typename PT, int NJ>
 __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __restrict__ n_joints,
                                                     const uint8_t* __restrict__ adj,
                                                     const int8_t* __restrict__ type,
@@ -260,7 +315,7 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
   if (b < B) {
     int n = n_joints[b];
     int nm = p.n_max;
-    int st = build_one<PT>(n, nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2, out_of(p, b));
+    int st = build_one<PT, NJ>(n, nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2, out_of(p, b));
     if (status_out) status_out[b] = st;
     if (st == LINKS_MECH_OK) atomicAdd(&hist[p.hdr[b].nd], 1);
   }
@@ -307,10 +362,16 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
   unsigned grid = (unsigned)((B + 255) / 256);
   {
   KernelScope ks(ctx, "plan_build");
-  if (pos_dtype == LINKS_F32)
-    build_kernel<float><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, (const float*)pos0, p, status_out);
-  else
-    build_kernel<double><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, (const double*)pos0, p, status_out);
+  const bool small = p.n_max <= 8;
+  if (pos_dtype == LINKS_F32) {
+    const float* ps = (const float*)pos0;
+    if (small) build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+    else build_kernel<float, kMaxJ><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+  } else {
+    const double* ps = (const double*)pos0;
+    if (small) build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+    else build_kernel<double, kMaxJ><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+  }
   }
   LINKS_CUDA(cudaGetLastError());
   {
@@ -336,11 +397,17 @@ int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_
   auto work = [&](int64_t lo, int64_t hi) {
     for (int64_t b = lo; b < hi; ++b) {
       BuildOut o{&hdr[b], &sj[b * kMaxJ], &fix[b * nm], &p64[b * nm], &dy[b * p.max_dyads]};
-      int st = pos_dtype == LINKS_F32
-                   ? build_one<float>(n_joints[b], nm, adj + b * nm * nm, type + b * nm,
-                                      (const float*)pos0 + b * nm * 2, o)
-                   : build_one<double>(n_joints[b], nm, adj + b * nm * nm, type + b * nm,
-                                       (const double*)pos0 + b * nm * 2, o);
+      const int n = n_joints[b];
+      const uint8_t* a = adj + b * nm * nm;
+      const int8_t* t = type + b * nm;
+      int st;
+      if (pos_dtype == LINKS_F32) {
+        const float* ps = (const float*)pos0 + b * nm * 2;
+        st = nm <= 8 ? build_one<float, 8>(n, nm, a, t, ps, o) : build_one<float, kMaxJ>(n, nm, a, t, ps, o);
+      } else {
+        const double* ps = (const double*)pos0 + b * nm * 2;
+        st = nm <= 8 ? build_one<double, 8>(n, nm, a, t, ps, o) : build_one<double, kMaxJ>(n, nm, a, t, ps, o);
+      }
       if (status_out) status_out[b] = st;
     }
   };
