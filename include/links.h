@@ -128,6 +128,7 @@ LINKS_API int links_plan_build_host(links_ctx ctx, links_plan plan, int64_t B, c
 /* Mechanisms in the last build, the plan's n_max and its capacity. */
 LINKS_API int links_plan_info(links_plan plan, int64_t* B, int* n_max, int64_t* capacity);
 
+
 /* Copies the plans of mechanisms [b0, b0 + count) to HOST memory, for inspection:
  *   topo [count, 6 + 3 (n_max - 2)] int32: status, n, motor joint, pivot joint,
  *       coupler joint, dyad count nd, then per dyad (k, i, j) as joint indices with
@@ -159,6 +160,19 @@ LINKS_API int links_plan_export(links_plan plan, int64_t b0, int64_t count, int3
 LINKS_API int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out_mode,
                    void* traj, void* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+
+/* Census of the LINKS_MIXED emit (the work its precision design does; no
+ * counterpart in the paper): runs the emit's FP32 chain and forward error bound
+ * (Sec. "Graphical Simulator" steps) over the rows links_simulate wrote for this plan
+ * at T -- every OK mechanism's steps before its lock (LINKS_OUT_FULL, from lock_step
+ * [B] device) or the first min(n_out, out_capacity) rows of out_index (device;
+ * LINKS_OUT_VALID_ONLY, all T steps) -- writing nothing, and copies to out[3] (host):
+ * [0] steps computed, [1] steps whose bound exceeds the tolerance, which the emit
+ * recomputes in double-word, [2] the same in dyad-steps.  The decisions are the
+ * emit's own (same arithmetic on the same inputs).  Synchronises the context's stream.
+ * LINKS_EINVAL for bad arguments. */
+LINKS_API int links_emit_census(links_ctx ctx, links_plan plan, int T, int out_mode, const int16_t* lock_step,
+                                const int32_t* out_index, int64_t out_capacity, int64_t* out);
 
 /* Path normalisation (Sec. "Dataset Curation & Processing"; the configured variant):
  * for each of M curves of T points (device float32 [M,T,2] in, [M,T,2] out, may

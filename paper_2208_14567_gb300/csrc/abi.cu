@@ -371,6 +371,26 @@ int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out
                         out_index, out_capacity, n_out);
 }
 
+int links_emit_census(links_ctx ctx, links_plan plan, int T, int out_mode, const int16_t* lock_step,
+                      const int32_t* out_index, int64_t out_capacity, int64_t* out) {
+  if (!ctx || !plan || !out) return set_error(LINKS_EINVAL, "links_emit_census: NULL ctx, plan or out");
+  if (plan->ctx != ctx) return set_error(LINKS_EINVAL, "links_emit_census: plan belongs to another context");
+  if (T < 1 || T > LINKS_MAX_T) return set_error(LINKS_EINVAL, "links_emit_census: T out of [1, 32767]");
+  if (out_mode != LINKS_OUT_FULL && out_mode != LINKS_OUT_VALID_ONLY)
+    return set_error(LINKS_EINVAL, "links_emit_census: unknown out_mode");
+  if (plan->B > 0 && out_mode == LINKS_OUT_FULL && !lock_step)
+    return set_error(LINKS_EINVAL, "links_emit_census: FULL rows need lock_step");
+  if (out_mode == LINKS_OUT_VALID_ONLY && (out_capacity < 0 || (out_capacity > 0 && !out_index)))
+    return set_error(LINKS_EINVAL, "links_emit_census: VALID_ONLY rows need out_index and out_capacity >= 0");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  int st = LINKS_OK;
+  const TTable* tab = get_table(ctx, T, &st);
+  if (!tab) return st;
+  out[0] = out[1] = out[2] = 0;
+  if (plan->B == 0) return LINKS_OK;
+  return emit_census(ctx, plan, tab, out_mode, lock_step, out_index, out_capacity, out);
+}
+
 int links_normalize(links_ctx ctx, int64_t M, int T, const float* curves, float* out) {
   if (!ctx) return set_error(LINKS_EINVAL, "links_normalize: NULL ctx");
   if (M < 0 || T < 1 || T > 1024) return set_error(LINKS_EINVAL, "links_normalize: need M >= 0 and 1 <= T <= 1024");

@@ -87,6 +87,10 @@ constexpr int kCursor = 32;       // [32] scatter cursors
 constexpr int kWork = 64;         // work counter of the screen / FP64 kernels
 constexpr int kWork2 = 65;        // work counter of the emit kernel
 constexpr int kNValid = 66;       // number of valid mechanisms (VALID_ONLY rows)
+// census counts of the emit (links_emit_census), 64-bit each (two slots)
+constexpr int kStatEmitSteps = 68;     // steps the emit computes
+constexpr int kStatEmitDW = 70;        // ... that its FP32 bound sends to double-word
+constexpr int kStatEmitDWDyads = 72;   // ... in dyad-steps
 constexpr int kCtrs = 80;
 
 struct TTable {
@@ -176,6 +180,8 @@ int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_
 int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, double* traj,
                  double* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                  int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+int emit_census(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, const int16_t* lock_step,
+                const int32_t* out_index, int64_t out_capacity, int64_t* out);
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);

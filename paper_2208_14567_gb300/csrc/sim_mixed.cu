@@ -29,6 +29,14 @@ constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kBatch = 16;  // work items taken per atomic by a warp
 
+// Adds a per-lane count to a 64-bit counter (one atomic per warp).
+__device__ __forceinline__ void add_stat(int32_t* ctrs, int slot, unsigned v) {
+#pragma unroll
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v)
+    atomicAdd(reinterpret_cast<unsigned long long*>(ctrs + slot), (unsigned long long)v);
+}
+
 struct dwp {
   dw x, y;
 };
@@ -242,6 +250,10 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
 // forward error bound is within kEmitTol of the bounding-box diagonal the FP32
 // positions are written, otherwise that lane recomputes the step in double-word
 // arithmetic (absolute coordinates) and writes those.
+// With CENSUS the kernel writes nothing and only counts what the emit does: steps
+// computed, and steps (and dyad-steps) whose FP32 bound sends them to double-word
+// (the same FP32 chain on the same inputs, so the same decisions).
+template <bool CENSUS>
 __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int T, const float4* __restrict__ cs,
                                                       int full, const int16_t* __restrict__ lock_step,
                                                       const int32_t* __restrict__ out_index,
@@ -257,6 +269,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
   const float nanf_ = __int_as_float(0x7fc00000);
+  unsigned n_steps = 0, n_dw = 0, n_dw_dyads = 0;  // census counts of this lane
   for (int64_t r = gw; r < rows; r += nw) {
     const int64_t b = full ? r : (int64_t)out_index[r];
     if (b < 0 || b >= B) {
@@ -298,6 +311,14 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
         *reinterpret_cast<float*>(Eb + nf * 128) = h.e_motor;
         float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f, emax = 0.0f;
         for (int d = 0; d < nd; ++d) fp32_dyad<true>(rec + d, Pb, Eb, lockw, zmin, isgmax, &emax);
+        if (CENSUS) {
+          ++n_steps;
+          if (!(emax <= tol && zmin >= 0.0f)) {
+            ++n_dw;
+            n_dw_dyads += nd;
+          }
+          continue;
+        }
         if (emax <= tol && zmin >= 0.0f) {
           for (int s = 0; s < nslot; ++s) {
             const float2 q = *reinterpret_cast<const float2*>(Pb + s * 256);
@@ -316,14 +337,20 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
         }
-      } else {
+      } else if (!CENSUS) {
         for (int s = 0; s < n; ++s)
           if (trow) trow[(int64_t)sj[s] * T + t] = make_float2(nanf_, nanf_);
         if (prow) prow[t] = make_float2(nanf_, nanf_);
       }
-      for (int j = n; j < ns; ++j)
-        if (trow) trow[(int64_t)j * T + t] = make_float2(nanf_, nanf_);
+      if (!CENSUS)
+        for (int j = n; j < ns; ++j)
+          if (trow) trow[(int64_t)j * T + t] = make_float2(nanf_, nanf_);
     }
+  }
+  if (CENSUS) {
+    add_stat(p.ctrs, kStatEmitSteps, n_steps);
+    add_stat(p.ctrs, kStatEmitDW, n_dw);
+    add_stat(p.ctrs, kStatEmitDWDyads, n_dw_dyads);
   }
 }
 
@@ -406,6 +433,24 @@ int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lane
   return st;
 }
 
+template <bool CENSUS>
+int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, const int16_t* lock_step,
+                const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name) {
+  auto kern = emit_kernel<CENSUS>;
+  const size_t smem = (size_t)kWarps * plan->d.n_max * 384;
+  if (smem > 48 * 1024)
+    LINKS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem));
+  if (per_sm < 1) per_sm = 1;
+  KernelScope ks(ctx, name);
+  kern<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, plan->B, tab->T, tab->cs, full ? 1 : 0,
+                                                            lock_step, out_index, out_capacity, traj, path,
+                                                            ctx->d_err);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
@@ -420,19 +465,22 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
     st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
     if (st) return st;
   }
-  if (traj || path) {
-    const size_t smem = (size_t)kWarps * plan->d.n_max * 384;
-    if (smem > 48 * 1024)
-      LINKS_CUDA(cudaFuncSetAttribute(emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int per_sm = 0;
-    LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, emit_kernel, kBlock, smem));
-    if (per_sm < 1) per_sm = 1;
-    KernelScope ks(ctx, "mixed_emit");
-    emit_kernel<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, B, T, tab->cs, full ? 1 : 0,
-                                                                   lock_step, out_index, out_capacity,
-                                                                   traj, path, ctx->d_err);
-    LINKS_CUDA(cudaGetLastError());
-  }
+  if (traj || path)
+    return launch_emit<false>(ctx, plan, tab, full, lock_step, out_index, out_capacity, traj, path, "mixed_emit");
+  return LINKS_OK;
+}
+
+int emit_census(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, const int16_t* lock_step,
+                const int32_t* out_index, int64_t out_capacity, int64_t* out) {
+  PlanDev& p = plan->d;
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kStatEmitSteps, 0, 6 * sizeof(int32_t), ctx->stream));
+  int st = launch_emit<true>(ctx, plan, tab, out_mode == LINKS_OUT_FULL, lock_step, out_index, out_capacity,
+                             nullptr, nullptr, "emit_census");
+  if (st) return st;
+  unsigned long long v[3];
+  LINKS_CUDA(cudaMemcpyAsync(v, p.ctrs + kStatEmitSteps, sizeof(v), cudaMemcpyDeviceToHost, ctx->stream));
+  LINKS_CUDA(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < 3; ++i) out[i] = (int64_t)v[i];
   return LINKS_OK;
 }
 

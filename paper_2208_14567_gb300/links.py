@@ -68,6 +68,7 @@ def lib():
             "links_plan_info": ([P, P, P, P], i32),
             "links_plan_export": ([P, i64, i64, P, P], i32),
             "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
+            "links_emit_census": ([P, P, i32, i32, P, P, i64, P], i32),
             "links_normalize": ([P, i64, i32, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
@@ -231,6 +232,17 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
                                 _dev(out_index, torch.int32, "out_index"), int(out_capacity),
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_emit_census(ctx, plan, T: int, out_mode: int, lock_step=None, out_index=None, out_capacity: int = 0):
+    """-> dict(steps, double_word_steps, double_word_dyads): what the mixed emit does for
+    the rows links_simulate wrote (FULL: from lock_step; VALID_ONLY: out_index rows)."""
+    import torch
+    out = (ctypes.c_int64 * 3)()
+    _check(lib().links_emit_census(ctx, plan, int(T), int(out_mode), _dev(lock_step, torch.int16, "lock_step"),
+                                   _dev(out_index, torch.int32, "out_index"), int(out_capacity), out),
+           "links_emit_census")
+    return dict(zip(("steps", "double_word_steps", "double_word_dyads"), (int(v) for v in out)))
 
 
 def links_normalize(ctx, curves, out):

@@ -212,6 +212,45 @@ def test_valid_only_rows(L, precision):
     assert np.array_equal(part["traj"][:cap], full["traj"][idx[:cap]], equal_nan=True)
 
 
+def test_emit_census(L):
+    """links_emit_census: the emit computes every step before the lock of each row it
+    writes; the double-word recomputations are a subset, in steps and dyad-steps; the
+    census is deterministic and writes no output."""
+    import torch
+    from paper_2208_14567_gb300.api import to_device
+    batch = I.dyad_batch(3000, 6, 10, seed=9)
+    T = 64
+    s = sim_for(batch, L)
+    try:
+        st = s.build(to_device(batch)).cpu().numpy()
+        nd = batch.n_joints - (batch.jtype[:, :batch.nmax] == 0).sum(1) - 1
+        ok = st == 0
+        for mode in (L.OUT_FULL, L.OUT_VALID_ONLY):
+            o = s.simulate(T, L.MIXED, mode)
+            s.sync()
+            traj0 = o.traj.clone()
+            cap = o.traj.shape[0]
+            args = (o.lock_step, o.out_index, cap)
+            w = L.links_emit_census(s.ctx, s.plan, T, mode, *args)
+            assert w == L.links_emit_census(s.ctx, s.plan, T, mode, *args)
+            assert torch.allclose(o.traj, traj0, rtol=0, atol=0, equal_nan=True)  # nothing written
+            lock = o.lock_step.cpu().numpy().astype(np.int64)
+            if mode == L.OUT_FULL:
+                steps = np.where(lock < 0, T, lock)[ok]
+                dyads = (np.where(lock < 0, T, lock) * nd)[ok]
+            else:
+                v = o.valid.cpu().numpy().astype(bool)
+                steps = np.full(v.sum(), T)
+                dyads = T * nd[v]
+            assert w["steps"] == steps.sum()
+            assert 0 <= w["double_word_steps"] <= w["steps"] and 0 <= w["double_word_dyads"] <= dyads.sum()
+            print(f"mode {mode}: {w}")
+        with pytest.raises(L.LinksError):
+            L.links_emit_census(s.ctx, s.plan, 0, L.OUT_FULL, o.lock_step)
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("T", [1, 7, 33, 64])
 def test_ragged_steps_and_statuses(L, T):
     batch = planted_bad(I.dyad_batch(700, 6, 12, seed=6, permute=True))
