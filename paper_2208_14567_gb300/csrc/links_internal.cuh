@@ -28,7 +28,10 @@ constexpr float kAddErr = 2.0f;
 // Emitted FP32 positions are used where their forward error bound is below this
 // fraction of the bounding-box diagonal (so the true error stays below ~5.2e-6 of it),
 // else the step is recomputed in double-word arithmetic.
-constexpr float kEmitTol = 6e-6f;
+// Position budget of the emit's certified FP32 path, relative to the bounding-box
+// diagonal L: the error bound E of every joint plus the rounding of the absolute
+// float32 output (u |p| per coordinate, |p| <= |pivot| + bmax) must stay below it.
+constexpr float kEmitBudget = 9.5e-6f;
 
 // ---------------------------------------------------------------------------------------
 // Plan layout (device, one record per mechanism, padded to n_max joints).

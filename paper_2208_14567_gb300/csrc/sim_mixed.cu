@@ -28,6 +28,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kBatch = 16;  // work items taken per atomic by a warp
+// Two steps per lane save record loads but double the slot arrays in shared memory;
+// they pay for small mechanisms only (4 CTAs per SM still fit).
+constexpr int kScreenTwoStepMaxSlots = 9;
 
 // Adds a per-lane count to a 64-bit counter (one atomic per warp).
 __device__ __forceinline__ void add_stat(int32_t* ctrs, int slot, unsigned v) {
@@ -105,9 +108,8 @@ __device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-p
 // slack - bound (>= 0 everywhere: certainly free; NaN propagates), isgmax = max
 // 1/sin(gamma).
 template <bool EMAX = false>
-__device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
-                                          float& zmin, float& isgmax, float* emax = nullptr) {
-  const float4 r0 = __ldg(&rec->r0), r1 = __ldg(&rec->r1);
+__device__ __forceinline__ void fp32_dyad_rec(const float4& r0, const float4& r1, char* Pb, char* Eb, float& lockw,
+                                              float& zmin, float& isgmax, float* emax = nullptr) {
   const uint32_t oij = __float_as_uint(r0.x), oe = __float_as_uint(r1.w), ok = __float_as_uint(r1.z);
   const float2 pi = *reinterpret_cast<const float2*>(Pb + (oij & 0xffffu));
   const float2 pj = *reinterpret_cast<const float2*>(Pb + (oij >> 16));
@@ -134,19 +136,31 @@ __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char*
   if (EMAX) *emax = fmaxf(*emax, ek);
 }
 
-template <int G>
-__global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
+template <bool EMAX = false>
+__device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
+                                          float& zmin, float& isgmax, float* emax = nullptr) {
+  const float4 r0 = __ldg(&rec->r0), r1 = __ldg(&rec->r1);
+  fp32_dyad_rec<EMAX>(r0, r1, Pb, Eb, lockw, zmin, isgmax, emax);
+}
+
+// Groups of G lanes screen one mechanism; each lane takes S steps of a chunk of G * S
+// consecutive steps (step chunk * G * S + u * G + lane-in-group, u < S), so that one
+// load of a dyad record serves S steps.  The slot arrays hold S columns per lane.
+template <int G, int S>
+__global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
                                                         uint8_t* __restrict__ valid,
                                                         int16_t* __restrict__ lock_step,
                                                         float* __restrict__ min_disc) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
-  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384;
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384 * S;
+  // column u of this lane: positions at region + u * ns * 256, bounds after all positions
   char* const Pb = region + lane * 8;
-  char* const Eb = region + ns * 256 + lane * 4;
+  char* const Eb = region + S * ns * 256 + lane * 4;
   const int g = lane / G, gl = lane % G;
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
+  constexpr int CH = G * S;  // steps per chunk
 
   int n_ok = p.ctrs[kHist + lane];
 #pragma unroll
@@ -198,44 +212,70 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
       const float4* fix = p.fixpos + b * ns;
       for (int s = 0; s < nf; ++s) {
         float4 f = __ldg(fix + s);
-        *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
-        *reinterpret_cast<float*>(Eb + s * 128) = e_fixed;
+#pragma unroll
+        for (int u = 0; u < S; ++u) {
+          *reinterpret_cast<float2*>(Pb + u * ns * 256 + s * 256) = make_float2(f.x, f.z);
+          *reinterpret_cast<float*>(Eb + u * ns * 128 + s * 128) = e_fixed;
+        }
       }
     }
     const bool has = item >= 0;
-    const int t = chunk * G + gl;
-    const bool act = has && t < T;
-    float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f;
-    if (has) {
-      float4 csv = __ldg(cs + min(t, T - 1));
-      *reinterpret_cast<float2*>(Pb + nf * 256) = make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
-      *reinterpret_cast<float*>(Eb + nf * 128) = e_motor;
+    float lockw[S], zmin[S], isgmax[S];
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      lockw[u] = INFINITY;
+      zmin[u] = INFINITY;
+      isgmax[u] = 0.0f;
+      if (has) {
+        const int t = chunk * CH + u * G + gl;
+        float4 csv = __ldg(cs + min(t, T - 1));
+        *reinterpret_cast<float2*>(Pb + u * ns * 256 + nf * 256) =
+            make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
+        *reinterpret_cast<float*>(Eb + u * ns * 128 + nf * 128) = e_motor;
+      }
     }
     const int ndl = has ? nd : 0;
     const int ndw = __reduce_max_sync(kFull, (unsigned)ndl);
     for (int d = 0; d < ndw; ++d)
-      if (d < ndl) fp32_dyad(rec + d, Pb, Eb, lockw, zmin, isgmax);
-    const bool certain_lock = lockw < 0.0f;
-    const bool amb = act && !certain_lock && !(zmin >= 0.0f);
-    float qstep = __fdividef(1.0f, isgmax * isgmax);
-    bool locked = act && certain_lock;
-    if (amb) {
-      dwp loc[kMaxJ];
-      float qd;
-      locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), loc, &qd);
-      qstep = qd;
+      if (d < ndl) {
+        const float4 r0 = __ldg(&rec[d].r0), r1 = __ldg(&rec[d].r1);
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+          fp32_dyad_rec(r0, r1, Pb + u * ns * 256, Eb + u * ns * 128, lockw[u], zmin[u], isgmax[u]);
+      }
+    // per step: certain lock, certain freedom, or a double-word rescue that decides
+    int first = CH;  // first locking step of the chunk (group-uniform)
+    float qstep[S];
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      const int t = chunk * CH + u * G + gl;
+      const bool act = has && t < T;
+      const bool certain_lock = lockw[u] < 0.0f;
+      const bool amb = act && !certain_lock && !(zmin[u] >= 0.0f);
+      qstep[u] = __fdividef(1.0f, isgmax[u] * isgmax[u]);
+      bool locked = act && certain_lock;
+      if (amb) {
+        dwp loc[kMaxJ];
+        float qd;
+        locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), loc, &qd);
+        qstep[u] = qd;
+      }
+      const unsigned lb = __ballot_sync(kFull, locked) & gmask;
+      if (lb && first == CH) first = u * G + (__ffs(lb) - 1 - g * G);
     }
-    const unsigned lb = __ballot_sync(kFull, locked) & gmask;
-    const int first = lb ? (__ffs(lb) - 1 - g * G) : G;
-    if (act && gl < first) qacc = fminf(qacc, qstep);
-    const bool done = has && (lb != 0 || (chunk + 1) * G >= T);
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      const int t = chunk * CH + u * G + gl;
+      if (has && t < T && u * G + gl < first) qacc = fminf(qacc, qstep[u]);
+    }
+    const bool done = has && (first < CH || (chunk + 1) * CH >= T);
     if (done) {
       float qr = qacc;
 #pragma unroll
       for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(gmask, qr, o));
       if (gl == 0) {
-        valid[b] = lb == 0;
-        lock_step[b] = (int16_t)(lb ? chunk * G + first : -1);
+        valid[b] = first == CH;
+        lock_step[b] = (int16_t)(first < CH ? chunk * CH + first : -1);
         min_disc[b] = qr;
       }
       item = -1;
@@ -247,9 +287,10 @@ __global__ void __launch_bounds__(kBlock) screen_kernel(PlanDev p, int T, const 
 
 // One warp per output row; 32 consecutive steps per pass.  Each step first runs the
 // certified FP32 chain of the screen (shared-memory slot arrays); if every joint's
-// forward error bound is within kEmitTol of the bounding-box diagonal the FP32
-// positions are written, otherwise that lane recomputes the step in double-word
-// arithmetic (absolute coordinates) and writes those.
+// forward error bound is within the tolerance (kEmitBudget of the bounding-box
+// diagonal, less the output rounding) the FP32 positions are written, otherwise that
+// lane recomputes the step in double-word arithmetic (absolute coordinates) and
+// writes those.
 // With CENSUS the kernel writes nothing and only counts what the emit does: steps
 // computed, and steps (and dyad-steps) whose FP32 bound sends them to double-word
 // (the same FP32 chain on the same inputs, so the same decisions).
@@ -286,7 +327,8 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     const DyadRec* rec = p.dyad + b * p.max_dyads;
     float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
     float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
-    const float tol = kEmitTol * h.lbox;
+    // FP32 tolerance: the budget minus the rounding of the absolute output coordinates
+    const float tol = fmaf(-2.0f * kU, fabsf(h.px_h) + fabsf(h.py_h) + h.bmax, kEmitBudget * h.lbox);
     const int nslot = nf + 1 + nd;
     // fixed joints: FP32 relative (shared) and double-word absolute (registers)
     float4 fabs[kMaxJ];
@@ -354,23 +396,24 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   }
 }
 
-template <int G>
+template <int G, int S>
 int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
                   int16_t* lock_step, float* min_disc) {
   PlanDev& p = plan->d;
-  size_t smem = (size_t)kWarps * p.n_max * 384;
+  size_t smem = (size_t)kWarps * p.n_max * 384 * S;
   static bool attr_set = false;
   if (!attr_set) {
-    LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+    LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
     attr_set = true;
   }
   int per_sm = 0;
-  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G>, kBlock, smem));
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G, S>, kBlock, smem));
   if (per_sm < 1) per_sm = 1;
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
   {
     KernelScope ks(ctx, "mixed_screen");
-    screen_kernel<G><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(p, T, tab->cs, valid, lock_step, min_disc);
+    screen_kernel<G, S><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(p, T, tab->cs, valid, lock_step,
+                                                                            min_disc);
   }
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
@@ -378,9 +421,14 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
 
 int launch_screen_lanes(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
                         int16_t* lock_step, float* min_disc, int lanes) {
-  if (lanes == 32) return launch_screen<32>(ctx, plan, T, tab, valid, lock_step, min_disc);
-  if (lanes == 16) return launch_screen<16>(ctx, plan, T, tab, valid, lock_step, min_disc);
-  return launch_screen<8>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  if (plan->d.n_max <= kScreenTwoStepMaxSlots) {
+    if (lanes == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
+    if (lanes == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
+    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  }
+  if (lanes == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  if (lanes == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
 }
 
 int screen_lanes(links_ctx ctx, links_plan plan) {
