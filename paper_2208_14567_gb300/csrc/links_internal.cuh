@@ -284,6 +284,49 @@ LINKS_HD dw dw_sqr(dw x) {
   return fast_two_sum(p, e);
 }
 LINKS_HD dw dw_scale2(dw x, float pow2) { return {fmul(x.h, pow2), fmul(x.l, pow2)}; }  // exact
+
+// Fused double-word expressions: the exact high products are combined with one
+// error-free sum and the low-order terms are accumulated in single precision before
+// the final renormalisation (the compensated dot product of Ogita, Rump and Oishi,
+// 2005, for two or three terms).  Relative error O(u^2) of the sum of the terms'
+// magnitudes, as for the chained operations, in fewer operations.
+// x^2 + y^2
+LINKS_HD dw dw_sum_sq(dw x, dw y) {
+  const float p1 = fmul(x.h, x.h), e1 = ffma(x.h, x.h, -p1);
+  const float p2 = fmul(y.h, y.h), e2 = ffma(y.h, y.h, -p2);
+  const dw s = two_sum(p1, p2);
+  float t = fadd(fadd(e1, e2), s.l);
+  t = ffma(fadd(x.h, x.h), x.l, t);
+  t = ffma(fadd(y.h, y.h), y.l, t);
+  return fast_two_sum(s.h, t);
+}
+// 4ab - c^2
+LINKS_HD dw dw_4ab_minus_sq(dw a, dw b, dw c) {
+  const float p = fmul(a.h, b.h);
+  float ep = ffma(a.h, b.h, -p);
+  ep = ffma(a.h, b.l, ep);
+  ep = ffma(a.l, b.h, ep);
+  const float q = fmul(c.h, c.h);
+  float eq = ffma(c.h, c.h, -q);
+  eq = ffma(fadd(c.h, c.h), c.l, eq);
+  const dw s = two_sum(fmul(4.0f, p), -q);
+  const float t = fsub(ffma(4.0f, ep, s.l), eq);
+  return fast_two_sum(s.h, t);
+}
+// z + a x + sg b y, sg = +1 or -1
+LINKS_HD dw dw_axpby(dw z, dw a, dw x, dw b, dw y, float sg) {
+  const float p1 = fmul(a.h, x.h), e1 = ffma(a.h, x.h, -p1);
+  const float bs = fmul(sg, b.h), bl = fmul(sg, b.l);
+  const float p2 = fmul(bs, y.h), e2 = ffma(bs, y.h, -p2);
+  const dw s1 = two_sum(p1, p2);
+  const dw s2 = two_sum(z.h, s1.h);
+  float t = fadd(fadd(fadd(z.l, s1.l), s2.l), fadd(e1, e2));
+  t = ffma(a.h, x.l, t);
+  t = ffma(a.l, x.h, t);
+  t = ffma(bs, y.l, t);
+  t = ffma(bl, y.h, t);
+  return fast_two_sum(s2.h, t);
+}
 // sqrt(x) for x > 0: FP32 seed from rsqrt, one Newton correction with an exact residual.
 LINKS_HD dw dw_sqrt(dw x) {
   if (!(x.h > 0.0f)) return {0.0f, 0.0f};

@@ -71,9 +71,9 @@ __device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const
     uint32_t sl = __float_as_uint(r2.w);
     const dwp pi = loc[sl & 0xff], pj = loc[(sl >> 8) & 0xff];
     dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
-    dw d2 = dw_add(dw_sqr(dx), dw_sqr(dy_));
+    dw d2 = dw_sum_sq(dx, dy_);
     dw e = dw_add(d2, dw{c_h, r2.z});
-    dw D = dw_sub(dw_scale2(dw_mul(d2, dw{r2.x, r2.y}), 4.0f), dw_sqr(e));
+    dw D = dw_4ab_minus_sq(d2, dw{r2.x, r2.y}, e);
     if (!(dw_sign(D) > 0.0f)) {
       *qmin = q;
       return true;
@@ -83,8 +83,8 @@ __device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const
     dw hinv = dw_scale2(dw_rcp(d2), 0.5f);
     dw a = dw_mul(e, hinv), bq = dw_mul(sq, hinv);
     dwp pk;
-    pk.x = dw_add(pi.x, dw_sub(dw_mul(a, dx), dw_mul(bq, dy_)));
-    pk.y = dw_add(pi.y, dw_add(dw_mul(a, dy_), dw_mul(bq, dx)));
+    pk.x = dw_axpby(pi.x, a, dx, bq, dy_, -1.0f);
+    pk.y = dw_axpby(pi.y, a, dy_, bq, dx, 1.0f);
     loc[sl >> 24] = pk;
   }
   *qmin = q;
