@@ -48,9 +48,11 @@ struct dwp {
 // (x_h, x_l, y_h, y_l); with ABS the positions are absolute (fix absolute, the
 // actuated joint offset by the pivot), otherwise relative to the pivot.
 // Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
+// Inlined: as a call it cost the emit 12% (argument passing and saved registers
+// around it).
 template <bool ABS>
-__device__ __noinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
-                                      float4 csv, dwp* loc, float* qmin) {
+__device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
+                                         float4 csv, dwp* loc, float* qmin) {
   const int nf = h.nf, nd = h.nd;
   for (int s = 0; s < nf; ++s) {
     float4 f = fix[s];
@@ -301,11 +303,13 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
                                                       int64_t out_capacity, float* __restrict__ traj,
                                                       float* __restrict__ path, int32_t* err) {
   extern __shared__ float4 smem4[];
+  __shared__ int s_jofs[kWarps][kMaxJ];  // per warp: offset of each slot's joint row in the output row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
   char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384;
   char* const Pb = region + lane * 8;
   char* const Eb = region + ns * 256 + lane * 4;
+  int* const jofs = s_jofs[warp];
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
@@ -330,6 +334,9 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     // FP32 tolerance: the budget minus the rounding of the absolute output coordinates
     const float tol = fmaf(-2.0f * kU, fabsf(h.px_h) + fabsf(h.py_h) + h.bmax, kEmitBudget * h.lbox);
     const int nslot = nf + 1 + nd;
+    __syncwarp();
+    if (lane < nslot) jofs[lane] = (int)sj[lane] * T;
+    __syncwarp();
     // fixed joints: FP32 relative (shared) and double-word absolute (registers)
     float4 fabs[kMaxJ];
     if (ok) {
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
           for (int s = 0; s < nslot; ++s) {
             const float2 q = *reinterpret_cast<const float2*>(Pb + s * 256);
             const float2 v = make_float2(q.x + h.px_h, q.y + h.py_h);
-            if (trow) trow[(int64_t)sj[s] * T + t] = v;
+            if (trow) trow[jofs[s] + t] = v;
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
         } else {
@@ -375,7 +382,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
           if (lk) atomicOr(err, kErrEmitLock);
           for (int s = 0; s < nslot; ++s) {
             float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(loc[s].x.h, loc[s].y.h);
-            if (trow) trow[(int64_t)sj[s] * T + t] = v;
+            if (trow) trow[jofs[s] + t] = v;
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
         }
