@@ -476,9 +476,11 @@ def main():
         views["plan_build"] = {"hbm": {"bound": "hbm", "achieved": nbytes / (ms_b * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
                                        "unit": "GB/s", "frac": nbytes / (ms_b * 1e-3) / 1e9 / pk["hbm_gbs"],
                                        "algorithmic_bytes": nbytes}}
-    # the binding roofline of the dominant kernel: the one its counters show binding
-    bind = {"mixed_emit": "alu", "mixed_screen": "alu", "plan_build": "hbm"}.get(top, "hbm")
-    roof = dict(views.get(top, {}).get(bind, {}))
+    # the binding roofline of the dominant kernel: of its views (ALU issue, HBM bytes),
+    # the one it runs closest to
+    tv = views.get(top, {})
+    bind = max(tv, key=lambda k: tv[k]["frac"]) if tv else None
+    roof = dict(tv.get(bind, {}))
     roof.update({"traffic": None, "kernel": top, "peak_source": pk["src"]})
 
     # ---- plain FP64 kernel on the same inputs (the comparator named by the metric)

@@ -28,6 +28,9 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kBatch = 16;  // work items taken per atomic by a warp
+constexpr int kEmitSlotBytes = 400;
+constexpr int kEmitSlotBytesDW = 656;
+constexpr int kEmitSharedDWMaxSlots = 12;
 // Two steps per lane save record loads but double the slot arrays in shared memory;
 // they pay for small mechanisms only (4 CTAs per SM still fit).
 constexpr int kScreenTwoStepMaxSlots = 9;
@@ -50,14 +53,44 @@ struct dwp {
 // Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
 // Inlined: as a call it cost the emit 12% (argument passing and saved registers
 // around it).
-template <bool ABS>
-__device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
-                                         float4 csv, dwp* loc, float* qmin) {
-  const int nf = h.nf, nd = h.nd;
-  for (int s = 0; s < nf; ++s) {
-    float4 f = fix[s];
-    loc[s] = {{f.x, f.y}, {f.z, f.w}};
+struct LocLocal {  // thread-local array; the fixed slots are copied in
+  static constexpr bool kFixInLoc = true;
+  dwp* v;
+  __device__ dwp get(int s) const { return v[s]; }
+  __device__ void set(int s, const dwp& x) const { v[s] = x; }
+};
+struct LocShared {  // the lane's columns of shared slot arrays (x, y: 256 B per slot)
+  static constexpr bool kFixInLoc = false;  // fixed slots stay in fix
+  char* xb;
+  char* yb;
+  __device__ dwp get(int s) const {
+    const float2 x = *reinterpret_cast<const float2*>(xb + s * 256);
+    const float2 y = *reinterpret_cast<const float2*>(yb + s * 256);
+    return {{x.x, x.y}, {y.x, y.y}};
   }
+  __device__ void set(int s, const dwp& v) const {
+    *reinterpret_cast<float2*>(xb + s * 256) = make_float2(v.x.h, v.x.l);
+    *reinterpret_cast<float2*>(yb + s * 256) = make_float2(v.y.h, v.y.l);
+  }
+};
+template <class Loc>
+__device__ __forceinline__ dwp slot_pos(const Loc& loc, const float4* fix, int nf, int s) {
+  if (!Loc::kFixInLoc && s < nf) {
+    const float4 f = fix[s];
+    return {{f.x, f.y}, {f.z, f.w}};
+  }
+  return loc.get(s);
+}
+
+template <bool ABS, class Loc>
+__device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
+                                         float4 csv, Loc loc, float* qmin) {
+  const int nf = h.nf, nd = h.nd;
+  if (Loc::kFixInLoc)
+    for (int s = 0; s < nf; ++s) {
+      float4 f = fix[s];
+      loc.set(s, {{f.x, f.y}, {f.z, f.w}});
+    }
   dw c = {csv.x, csv.y}, s = {csv.z, csv.w};
   dw ux = {h.ux_h, h.ux_l}, uy = {h.uy_h, h.uy_l};
   dwp m = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
@@ -65,13 +98,13 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
     m.x = dw_add(m.x, dw{h.px_h, h.px_l});
     m.y = dw_add(m.y, dw{h.py_h, h.py_l});
   }
-  loc[nf] = m;
+  loc.set(nf, m);
   float q = INFINITY;
   for (int d = 0; d < nd; ++d) {
     const float c_h = __ldg(&dy[d].r0.w), w2 = __ldg(&dy[d].r1.x);
     const float4 r2 = __ldg(&dy[d].r2);
     uint32_t sl = __float_as_uint(r2.w);
-    const dwp pi = loc[sl & 0xff], pj = loc[(sl >> 8) & 0xff];
+    const dwp pi = slot_pos(loc, fix, nf, sl & 0xff), pj = slot_pos(loc, fix, nf, (sl >> 8) & 0xff);
     dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
     dw d2 = dw_sum_sq(dx, dy_);
     dw e = dw_add(d2, dw{c_h, r2.z});
@@ -87,7 +120,7 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
     dwp pk;
     pk.x = dw_axpby(pi.x, a, dx, bq, dy_, -1.0f);
     pk.y = dw_axpby(pi.y, a, dy_, bq, dx, 1.0f);
-    loc[sl >> 24] = pk;
+    loc.set(sl >> 24, pk);
   }
   *qmin = q;
   return false;
@@ -259,7 +292,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       if (amb) {
         dwp loc[kMaxJ];
         float qd;
-        locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), loc, &qd);
+        locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), LocLocal{loc}, &qd);
         qstep[u] = qd;
       }
       const unsigned lb = __ballot_sync(kFull, locked) & gmask;
@@ -293,10 +326,15 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
 // diagonal, less the output rounding) the FP32 positions are written, otherwise that
 // lane recomputes the step in double-word arithmetic (absolute coordinates) and
 // writes those.
+// Shared memory per warp and slot: FP32 positions (256 B), error bounds (128 B),
+// absolute fixed joints (16 B, one per warp) and, with DWS, the double-word y of the
+// lane's slot positions (256 B; x reuses the FP32 positions, the fixed slots stay in
+// the warp's copy).  Larger mechanisms keep the double-word slots thread-local, which
+// costs less occupancy.
 // With CENSUS the kernel writes nothing and only counts what the emit does: steps
 // computed, and steps (and dyad-steps) whose FP32 bound sends them to double-word
 // (the same FP32 chain on the same inputs, so the same decisions).
-template <bool CENSUS>
+template <bool CENSUS, bool DWS>
 __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int T, const float4* __restrict__ cs,
                                                       int full, const int16_t* __restrict__ lock_step,
                                                       const int32_t* __restrict__ out_index,
@@ -306,9 +344,11 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   __shared__ int s_jofs[kWarps][kMaxJ];  // per warp: offset of each slot's joint row in the output row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
-  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384;
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * (DWS ? kEmitSlotBytesDW : kEmitSlotBytes);
   char* const Pb = region + lane * 8;
   char* const Eb = region + ns * 256 + lane * 4;
+  float4* const Fb = reinterpret_cast<float4*>(region + ns * 384);  // absolute fixed joints (warp)
+  char* const Yb = region + ns * 400 + lane * 8;                    // DWS: double-word y
   int* const jofs = s_jofs[warp];
   const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -337,8 +377,8 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     __syncwarp();
     if (lane < nslot) jofs[lane] = (int)sj[lane] * T;
     __syncwarp();
-    // fixed joints: FP32 relative (shared) and double-word absolute (registers)
-    float4 fabs[kMaxJ];
+    // fixed joints: FP32 relative (the lane's column) and double-word absolute (one
+    // copy per warp)
     if (ok) {
       const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
       const float4* fr = p.fixpos + b * ns;
@@ -346,10 +386,13 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
         float4 f = __ldg(fr + s);
         *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
         *reinterpret_cast<float*>(Eb + s * 128) = h.e_fixed;
-        dw x = dw_add(px, dw{f.x, f.y}), y = dw_add(py, dw{f.z, f.w});
-        fabs[s] = make_float4(x.h, x.l, y.h, y.l);
+        if (lane == s) {
+          dw x = dw_add(px, dw{f.x, f.y}), y = dw_add(py, dw{f.z, f.w});
+          Fb[s] = make_float4(x.h, x.l, y.h, y.l);
+        }
       }
     }
+    __syncwarp();
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;
       if (t >= T) continue;
@@ -376,12 +419,17 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
         } else {
-          dwp loc[kMaxJ];
+          dwp lbuf[DWS ? 1 : kMaxJ];
+          const auto loc = [&] {
+            if constexpr (DWS) return LocShared{Pb, Yb};
+            else return LocLocal{lbuf};
+          }();
           float qd;
-          bool lk = dw_chain<true>(h, fabs, rec, csv, loc, &qd);
+          bool lk = dw_chain<true>(h, Fb, rec, csv, loc, &qd);
           if (lk) atomicOr(err, kErrEmitLock);
           for (int s = 0; s < nslot; ++s) {
-            float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(loc[s].x.h, loc[s].y.h);
+            const dwp ls = slot_pos(loc, Fb, nf, s);
+            float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(ls.x.h, ls.y.h);
             if (trow) trow[jofs[s] + t] = v;
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
@@ -491,8 +539,9 @@ int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lane
 template <bool CENSUS>
 int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, const int16_t* lock_step,
                 const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name) {
-  auto kern = emit_kernel<CENSUS>;
-  const size_t smem = (size_t)kWarps * plan->d.n_max * 384;
+  const bool dws = plan->d.n_max <= kEmitSharedDWMaxSlots;
+  auto kern = dws ? emit_kernel<CENSUS, true> : emit_kernel<CENSUS, false>;
+  const size_t smem = (size_t)kWarps * plan->d.n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes);
   if (smem > 48 * 1024)
     LINKS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
