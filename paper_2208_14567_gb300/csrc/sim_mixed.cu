@@ -101,8 +101,8 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
   loc.set(nf, m);
   float q = INFINITY;
   for (int d = 0; d < nd; ++d) {
-    const float c_h = __ldg(&dy[d].r0.w), w2 = __ldg(&dy[d].r1.x);
-    const float4 r2 = __ldg(&dy[d].r2);
+    const float c_h = dy[d].r0.w, w2 = dy[d].r1.x;  // records in global or shared memory
+    const float4 r2 = dy[d].r2;
     uint32_t sl = __float_as_uint(r2.w);
     const dwp pi = slot_pos(loc, fix, nf, sl & 0xff), pj = slot_pos(loc, fix, nf, (sl >> 8) & 0xff);
     dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
@@ -174,7 +174,7 @@ __device__ __forceinline__ void fp32_dyad_rec(const float4& r0, const float4& r1
 template <bool EMAX = false>
 __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
                                           float& zmin, float& isgmax, float* emax = nullptr) {
-  const float4 r0 = __ldg(&rec->r0), r1 = __ldg(&rec->r1);
+  const float4 r0 = rec->r0, r1 = rec->r1;  // records in global or shared memory
   fp32_dyad_rec<EMAX>(r0, r1, Pb, Eb, lockw, zmin, isgmax, emax);
 }
 
@@ -189,11 +189,14 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
-  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * 384 * S;
+  const int g = lane / G, gl = lane % G;
+  const int rstride = 2 * p.max_dyads + 1;  // float4 per group: (r0, r1) per dyad, padded
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * (ns * 384 * S + (32 / G) * rstride * 16);
   // column u of this lane: positions at region + u * ns * 256, bounds after all positions
   char* const Pb = region + lane * 8;
   char* const Eb = region + S * ns * 256 + lane * 4;
-  const int g = lane / G, gl = lane % G;
+  // the group's mechanism: the FP32 parts of its dyad records
+  float4* const Rg = reinterpret_cast<float4*>(region + S * ns * 384) + g * rstride;
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
   constexpr int CH = G * S;  // steps per chunk
 
@@ -230,6 +233,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       ++qhead;
     }
     if (__ballot_sync(kFull, item >= 0) == 0) break;
+    __syncwarp();  // the previous mechanism's records are no longer read
 
     if (fresh) {
       b = p.order[item];
@@ -244,6 +248,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       rec = p.dyad + b * p.max_dyads;
       chunk = 0;
       qacc = INFINITY;
+      for (int x = gl; x < 2 * nd; x += G) Rg[x] = __ldg(x & 1 ? &rec[x >> 1].r1 : &rec[x >> 1].r0);
       const float4* fix = p.fixpos + b * ns;
       for (int s = 0; s < nf; ++s) {
         float4 f = __ldg(fix + s);
@@ -254,6 +259,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
         }
       }
     }
+    __syncwarp();  // a fresh group's records are in place
     const bool has = item >= 0;
     float lockw[S], zmin[S], isgmax[S];
 #pragma unroll
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
     const int ndw = __reduce_max_sync(kFull, (unsigned)ndl);
     for (int d = 0; d < ndw; ++d)
       if (d < ndl) {
-        const float4 r0 = __ldg(&rec[d].r0), r1 = __ldg(&rec[d].r1);
+        const float4 r0 = Rg[2 * d], r1 = Rg[2 * d + 1];
 #pragma unroll
         for (int u = 0; u < S; ++u)
           fp32_dyad_rec(r0, r1, Pb + u * ns * 256, Eb + u * ns * 128, lockw[u], zmin[u], isgmax[u]);
@@ -344,7 +350,9 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   __shared__ int s_jofs[kWarps][kMaxJ];  // per warp: offset of each slot's joint row in the output row
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
-  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * ns * (DWS ? kEmitSlotBytesDW : kEmitSlotBytes);
+  const int slot_bytes = DWS ? kEmitSlotBytesDW : kEmitSlotBytes;
+  char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * (ns * slot_bytes + p.max_dyads * 48);
+  float4* const Rw = reinterpret_cast<float4*>(region + ns * slot_bytes);  // the row's dyad records
   char* const Pb = region + lane * 8;
   char* const Eb = region + ns * 256 + lane * 4;
   float4* const Fb = reinterpret_cast<float4*>(region + ns * 384);  // absolute fixed joints (warp)
@@ -368,7 +376,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     int lock = T;
     if (full) lock = ok ? (lock_step[b] < 0 ? T : lock_step[b]) : 0;
     const uint8_t* sj = p.slot_joint + b * kMaxJ;
-    const DyadRec* rec = p.dyad + b * p.max_dyads;
+    const DyadRec* const rec = reinterpret_cast<const DyadRec*>(Rw);
     float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
     float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
     // FP32 tolerance: the budget minus the rounding of the absolute output coordinates
@@ -376,6 +384,8 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
     const int nslot = nf + 1 + nd;
     __syncwarp();
     if (lane < nslot) jofs[lane] = (int)sj[lane] * T;
+    for (int x = lane; x < 3 * nd; x += 32)
+      Rw[x] = __ldg(reinterpret_cast<const float4*>(p.dyad + b * p.max_dyads) + x);
     __syncwarp();
     // fixed joints: FP32 relative (the lane's column) and double-word absolute (one
     // copy per warp)
@@ -455,7 +465,7 @@ template <int G, int S>
 int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
                   int16_t* lock_step, float* min_disc) {
   PlanDev& p = plan->d;
-  size_t smem = (size_t)kWarps * p.n_max * 384 * S;
+  size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
   static bool attr_set = false;
   if (!attr_set) {
     LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
@@ -541,7 +551,8 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
                 const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name) {
   const bool dws = plan->d.n_max <= kEmitSharedDWMaxSlots;
   auto kern = dws ? emit_kernel<CENSUS, true> : emit_kernel<CENSUS, false>;
-  const size_t smem = (size_t)kWarps * plan->d.n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes);
+  const size_t smem = (size_t)kWarps * (plan->d.n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes) +
+                                        plan->d.max_dyads * 48);
   if (smem > 48 * 1024)
     LINKS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
