@@ -178,13 +178,15 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
 // look-up per database point.  The table holds DT at kNG x kNG nodes over the query's
 // bounding square with a margin, rounded down to half precision.
 //
-// Row term.  The database curve's points are split into runs of 8 consecutive
+// Row term.  The database curve's points are split into runs of kRun consecutive
 // points with centre z_g; rho bounds |c - z_g| for every point of every run.  A
 // query point p is then at least min_g |p - z_g| - rho from the curve, which costs
-// ceil(T/8) instead of T distance evaluations per query point.
+// ceil(T/kRun) instead of T distance evaluations per query point.  (Runs of 4 prune
+// about twice as many pairs as runs of 8 for twice the cost of this bound, which pays.)
 
 constexpr int kNG = 60;                       // grid nodes per side (7200-byte table)
-constexpr int kMaxG = 32;                     // runs of 8 points per curve (T <= 256)
+constexpr int kRun = 4;                       // points per run
+constexpr int kMaxG = 64;                     // runs per curve (T <= 256)
 constexpr float kLbShrink = 1.0f - 0x1p-20f;  // covers the rounding of computed distances
 constexpr float kLbGrow = 1.0f + 0x1p-20f;    // (relative error below 2^-21.9 each)
 constexpr float kRound = 12582912.0f;         // 1.5 * 2^23: x + kRound rounds x to an integer
@@ -252,7 +254,8 @@ __global__ void __launch_bounds__(256) dt_grid_kernel(int Q, int T, const float2
 }
 
 // The exact and the bounding computations run on 16-lane groups (two per warp):
-// lane gl of a group holds query points gl * PL + i (i < PL), packed in pairs;
+// lane gl of a group holds query points gl * PL + i (i < PL), packed in pairs, read
+// from global memory (L1) for each pair it takes;
 // points past T sit far away, so they never give a column minimum, and their row
 // minima are left out of the sums.
 template <int PL>
@@ -404,8 +407,7 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
   constexpr int kGroups = W * 2;
   extern __shared__ __align__(16) float2 dyn[];
   float2* stage = dyn;                     // [kStage][T] database curves
-  float2* qpts = stage + kStage * T;       // [W][T] the CTA's queries
-  float2* cen = qpts + W * T;              // [kStage][kMaxG] run centres (pruning)
+  float2* cen = stage + kStage * T;        // [kStage][kMaxG] run centres (pruning)
   __half* sgrid = reinterpret_cast<__half*>(cen + kStage * kMaxG);  // [W][kNG^2] (pruning)
   __shared__ unsigned rho_s[kStage];       // run radius per staged curve (float bits)
   __shared__ float thr_w[W];
@@ -421,13 +423,9 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
   const int64_t c0 = (int64_t)blockIdx.y * chunk;
   const int64_t c1 = min(M, c0 + chunk);
   const bool prune = grids != nullptr;
-  const int G = (T + 7) / 8;
+  const int G = (T + kRun - 1) / kRun;
   const float invT = 1.0f / (float)T;
   const float margin = 4e-5f;
-  for (int x = threadIdx.x; x < W * T; x += blockDim.x) {
-    const int w = x / T;
-    qpts[x] = qbase + w < Q ? qs[(int64_t)qbase * T + x] : make_float2(kFar, kFar);
-  }
   __half* mygrid = sgrid + warp * kNG * kNG;
   float4 gp = make_float4(0.f, 0.f, 0.f, 0.f);
   if (prune && q < Q) {
@@ -450,8 +448,8 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
     if (prune) {  // run centres and radii of the staged curves
       for (int x = threadIdx.x; x < nst * G; x += blockDim.x) {
         const int s = x / G, r = x % G;
-        const float2* cp = stage + s * T + r * 8;
-        const int cnt = min(8, T - r * 8);
+        const float2* cp = stage + s * T + r * kRun;
+        const int cnt = min(kRun, T - r * kRun);
         float zx = 0.f, zy = 0.f;
         for (int i = 0; i < cnt; ++i) {
           zx += cp[i].x;
@@ -516,7 +514,7 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
       const int n = nA;
       for (int e = gid; e < n; e += kGroups) {
         const int w = listA[e] / kStage, s = listA[e] % kStage;
-        load_query<PL>(qpts + w * T, T, gl, QX, QY);
+        load_query<PL>(qs + (int64_t)(qbase + w) * T, T, gl, QX, QY);
         const float lb = lbA[e] + row_bound<PL>(QX, QY, cen + s * kMaxG, G, __uint_as_float(rho_s[s]), T, gl,
                                                 gmask, invT);
         const float thr = thr_w[w];
@@ -528,7 +526,7 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
       const int n = nB;
       for (int e = gid; e < n; e += kGroups) {
         const int w = listB[e] / kStage, s = listB[e] % kStage;
-        load_query<PL>(qpts + w * T, T, gl, QX, QY);
+        load_query<PL>(qs + (int64_t)(qbase + w) * T, T, gl, QX, QY);
         const float thr = thr_w[w];
         const float d = chamfer_exact<PL>(QX, QY, stage + s * T, T, gl, gmask, invT, prune ? thr : INFINITY);
         if (gl == 0 && d <= thr) {
@@ -625,7 +623,7 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
     dt_grid_kernel<<<Q, 256, 0, ctx->stream>>>(Q, T, qs, grids, gparam, gthr);
     LINKS_CUDA(cudaGetLastError());
   }
-  const size_t smem = (size_t)(kStage + W) * T * sizeof(float2) +
+  const size_t smem = (size_t)kStage * T * sizeof(float2) +
                       (prune ? (size_t)kStage * kMaxG * sizeof(float2) + (size_t)W * kNG * kNG * sizeof(__half) : 0);
   LINKS_CUDA(cudaFuncSetAttribute(chamfer_kernel<PL, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   {
