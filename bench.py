@@ -481,7 +481,13 @@ def main():
     tv = views.get(top, {})
     bind = max(tv, key=lambda k: tv[k]["frac"]) if tv else None
     roof = dict(tv.get(bind, {}))
-    roof.update({"traffic": None, "kernel": top, "peak_source": pk["src"]})
+    # DRAM bytes per launch from the committed ncu capture of the same kernels
+    # (300,000 candidates; 74,163 valid rows), scaled by the units this launch processed
+    per_unit = {"mixed_emit": (1053.9e6 / 74163, rows), "mixed_screen": (142.2e6 / 300000, B),
+                "plan_build": (158.7e6 / 300000, B)}
+    traffic = per_unit[top][0] * per_unit[top][1] if top in per_unit else None
+    roof.update({"traffic": traffic, "traffic_source": "ncu dram bytes of a 300k-candidate capture, scaled",
+                 "kernel": top, "peak_source": pk["src"]})
 
     # ---- plain FP64 kernel on the same inputs (the comparator named by the metric)
     f64_out = sim.alloc(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out_capacity=max(n_valid, 1))
