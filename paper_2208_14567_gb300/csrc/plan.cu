@@ -124,7 +124,7 @@ LINKS_HD float hyp_up(float x, float y) {
 
 template <typename PT, int NJ>
 LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type, const PT* pos,
-                       BuildOut o) {
+                       BuildOut o, int* nd_out = nullptr) {
   MechHdr h{};
   h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
   int status = LINKS_MECH_OK;
@@ -266,6 +266,7 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   }
 
   h.nd = (uint8_t)nd;
+  if (nd_out) *nd_out = nd;
   h.nf = (uint8_t)nf;
   h.motor_joint = (uint8_t)motor;
   h.pivot_joint = (uint8_t)pivot;
@@ -302,22 +303,62 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
   return o;
 }
 
+// Inputs of the block's 256 mechanisms (n_max <= 8) staged in shared memory with
+// coalesced loads: each mechanism's adjacency, type and position rows padded to an odd
+// number of words, so that the threads' reads of their own rows fall in distinct banks.
+constexpr int kStageRow = 17;  // words per staged adjacency / position row (<= 16 used)
+constexpr int kTypeRow = 3;    // words per staged type row (<= 2 used)
+
 template <typename PT, int NJ>
 __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __restrict__ n_joints,
                                                     const uint8_t* __restrict__ adj,
                                                     const int8_t* __restrict__ type,
                                                     const PT* __restrict__ pos, PlanDev p,
                                                     int32_t* __restrict__ status_out) {
+  constexpr bool kStaged = NJ <= 8;
+  constexpr bool kStagedPos = kStaged && sizeof(PT) == 4;  // FP64 rows would pass 48 KB
   __shared__ int hist[32];
+  __shared__ uint32_t s_adj[kStaged ? 256 * kStageRow : 1];
+  __shared__ PT s_pos[kStagedPos ? 256 * kStageRow : 1];
+  __shared__ uint32_t s_type[kStaged ? 256 * kTypeRow : 1];
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+  const int nm = p.n_max;
+  const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
+  const int t = threadIdx.x;
+  const int64_t b = b0 + t;
+  const uint8_t* my_adj = adj + b * nm * nm;
+  const int8_t* my_type = type + b * nm;
+  const PT* my_pos = pos + b * nm * 2;
+  if (kStaged) {
+    const int nb = B - b0 < 256 ? (int)(B - b0) : 256;
+    const int nn = nm * nm;
+    if ((nn & 3) == 0) {  // whole words per row, rows word-aligned
+      const int wpm = nn >> 2;
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(adj + b0 * nn);
+      for (int x = t; x < nb * wpm; x += 256) s_adj[(x / wpm) * kStageRow + x % wpm] = __ldg(src + x);
+    } else {
+      const uint8_t* src = adj + b0 * nn;
+      uint8_t* dst = reinterpret_cast<uint8_t*>(s_adj);
+      for (int x = t; x < nb * nn; x += 256) dst[(x / nn) * (4 * kStageRow) + x % nn] = __ldg(src + x);
+    }
+    if (kStagedPos) {
+      const PT* psrc = pos + b0 * 2 * nm;
+      for (int x = t; x < nb * 2 * nm; x += 256) s_pos[(x / (2 * nm)) * kStageRow + x % (2 * nm)] = __ldg(psrc + x);
+      my_pos = s_pos + t * kStageRow;
+    }
+    const int8_t* tsrc = type + b0 * nm;
+    int8_t* tdst = reinterpret_cast<int8_t*>(s_type);
+    for (int x = t; x < nb * nm; x += 256) tdst[(x / nm) * (4 * kTypeRow) + x % nm] = __ldg(tsrc + x);
+    my_adj = reinterpret_cast<const uint8_t*>(s_adj + t * kStageRow);
+    my_type = reinterpret_cast<const int8_t*>(s_type + t * kTypeRow);
+  }
   __syncthreads();
-  int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (b < B) {
     int n = n_joints[b];
-    int nm = p.n_max;
-    int st = build_one<PT, NJ>(n, nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2, out_of(p, b));
+    int nd = 0;
+    int st = build_one<PT, NJ>(n, nm, my_adj, my_type, my_pos, out_of(p, b), &nd);
     if (status_out) status_out[b] = st;
-    if (st == LINKS_MECH_OK) atomicAdd(&hist[p.hdr[b].nd], 1);
+    if (st == LINKS_MECH_OK) atomicAdd(&hist[nd], 1);
   }
   __syncthreads();
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
