@@ -20,6 +20,7 @@
 //   emit    every requested trajectory step in double-word arithmetic, written as
 //           float32 (one warp per output row, 32 consecutive steps per store).
 #include "links_internal.cuh"
+#include "packed.cuh"
 
 namespace links {
 namespace {
@@ -171,6 +172,48 @@ __device__ __forceinline__ void fp32_dyad_rec(const float4& r0, const float4& r1
   if (EMAX) *emax = fmaxf(*emax, ek);
 }
 
+// The same dyad for two steps of one lane at once, in packed f32x2 arithmetic (each
+// result rounded as the scalar code rounds it, so both steps get the scalar values).
+// Slot layout: per slot and lane a float4 (x of both steps, y of both steps) at
+// P2 + 2 * (position offset), the two bounds at E2 + 2 * (bound offset).
+__device__ __forceinline__ void fp32_dyad2(const float4& r0, const float4& r1, char* P2, char* E2, float* lockw,
+                                           float* zmin, float* isgmax) {
+  const uint32_t oij = __float_as_uint(r0.x), oe = __float_as_uint(r1.w), ok = __float_as_uint(r1.z);
+  const float4 pi = *reinterpret_cast<const float4*>(P2 + 2 * (oij & 0xffffu));
+  const float4 pj = *reinterpret_cast<const float4*>(P2 + 2 * (oij >> 16));
+  const float2 ei = *reinterpret_cast<const float2*>(E2 + 2 * (oe & 0xffffu));
+  const float2 ej = *reinterpret_cast<const float2*>(E2 + 2 * (oe >> 16));
+  const f2 PIX = pk2(pi.x, pi.y), PIY = pk2(pi.z, pi.w);
+  const f2 DX = sub2(pk2(pj.x, pj.y), PIX), DY = sub2(pk2(pj.z, pj.w), PIY);
+  const f2 D2 = fma2(DX, DX, mul2(DY, DY));
+  const float2 d2 = up2(D2);
+  const f2 RD = pk2(rsqrtf(d2.x), rsqrtf(d2.y));
+  const f2 DD = mul2(D2, RD);
+  const f2 R12 = pk2(r0.y, r0.y), RM = pk2(r0.z, r0.z);
+  const f2 S2 = sub2(R12, DD), S3 = sub2(DD, RM);
+  const f2 D = mul2(mul2(add2(DD, R12), S2), mul2(S3, add2(DD, RM)));
+  const float2 dv = up2(D);
+  const f2 RDD = pk2(rsqrtf(dv.x), rsqrtf(dv.y));
+  const f2 ISG = mul2(pk2(r1.x, r1.x), RDD);
+  const f2 DEL = add2(add2(pk2(ei.x, ei.y), pk2(ej.x, ej.y)), pk2(r1.y, r1.y));
+  const float2 lo = up2(add2(S2, DEL)), hi = up2(add2(S3, DEL));
+  lockw[0] = min3(lockw[0], lo.x, hi.x);
+  lockw[1] = min3(lockw[1], lo.y, hi.y);
+  const float2 zl = up2(sub2(S2, DEL)), zh = up2(sub2(S3, DEL));
+  zmin[0] = min3_nan(zmin[0], zl.x, zh.x);
+  zmin[1] = min3_nan(zmin[1], zl.y, zh.y);
+  const float2 isg = up2(ISG);
+  isgmax[0] = fmaxf(isgmax[0], isg.x);
+  isgmax[1] = fmaxf(isgmax[1], isg.y);
+  const f2 HINV = mul2(pk2(0.5f, 0.5f), mul2(RD, RD));
+  const f2 A = mul2(add2(D2, pk2(r0.w, r0.w)), HINV), BQ = mul2(mul2(D, RDD), HINV);
+  const f2 KX = fma2(A, DX, fma2(neg2(BQ), DY, PIX)), KY = fma2(A, DY, fma2(BQ, DX, PIY));
+  const float2 kx = up2(KX), ky = up2(KY);
+  *reinterpret_cast<float4*>(P2 + 2 * (ok & 0xffffu)) = make_float4(kx.x, kx.y, ky.x, ky.y);
+  const f2 EK = fma2(DEL, ISG, mul2(pk2(kAddErr * kU, kAddErr * kU), add2(R12, add2(abs2(KX), abs2(KY)))));
+  *reinterpret_cast<float2*>(E2 + 2 * (ok >> 16)) = up2(EK);
+}
+
 template <bool EMAX = false>
 __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char* Pb, char* Eb, float& lockw,
                                           float& zmin, float& isgmax, float* emax = nullptr) {
@@ -192,9 +235,13 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
   const int g = lane / G, gl = lane % G;
   const int rstride = 2 * p.max_dyads + 1;  // float4 per group: (r0, r1) per dyad, padded
   char* const region = reinterpret_cast<char*>(smem4) + (size_t)warp * (ns * 384 * S + (32 / G) * rstride * 16);
-  // column u of this lane: positions at region + u * ns * 256, bounds after all positions
+  // one step per lane: positions (float2) at Pb + 256 * slot, bounds (float) at
+  // Eb + 128 * slot; two steps per lane: both steps' positions (float4) at P2 + 512 *
+  // slot, their bounds (float2) at E2 + 256 * slot
   char* const Pb = region + lane * 8;
-  char* const Eb = region + S * ns * 256 + lane * 4;
+  char* const Eb = region + ns * 256 + lane * 4;
+  char* const P2 = region + lane * 16;
+  char* const E2 = region + ns * 512 + lane * 8;
   // the group's mechanism: the FP32 parts of its dyad records
   float4* const Rg = reinterpret_cast<float4*>(region + S * ns * 384) + g * rstride;
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
@@ -252,27 +299,35 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       const float4* fix = p.fixpos + b * ns;
       for (int s = 0; s < nf; ++s) {
         float4 f = __ldg(fix + s);
-#pragma unroll
-        for (int u = 0; u < S; ++u) {
-          *reinterpret_cast<float2*>(Pb + u * ns * 256 + s * 256) = make_float2(f.x, f.z);
-          *reinterpret_cast<float*>(Eb + u * ns * 128 + s * 128) = e_fixed;
+        if (S == 2) {
+          *reinterpret_cast<float4*>(P2 + s * 512) = make_float4(f.x, f.x, f.z, f.z);
+          *reinterpret_cast<float2*>(E2 + s * 256) = make_float2(e_fixed, e_fixed);
+        } else {
+          *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
+          *reinterpret_cast<float*>(Eb + s * 128) = e_fixed;
         }
       }
     }
     __syncwarp();  // a fresh group's records are in place
     const bool has = item >= 0;
     float lockw[S], zmin[S], isgmax[S];
+    float2 mpos[S];
 #pragma unroll
     for (int u = 0; u < S; ++u) {
       lockw[u] = INFINITY;
       zmin[u] = INFINITY;
       isgmax[u] = 0.0f;
-      if (has) {
-        const int t = chunk * CH + u * G + gl;
-        float4 csv = __ldg(cs + min(t, T - 1));
-        *reinterpret_cast<float2*>(Pb + u * ns * 256 + nf * 256) =
-            make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
-        *reinterpret_cast<float*>(Eb + u * ns * 128 + nf * 128) = e_motor;
+      const int t = chunk * CH + u * G + gl;
+      const float4 csv = __ldg(cs + min(t, T - 1));
+      mpos[u] = make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
+    }
+    if (has) {
+      if (S == 2) {
+        *reinterpret_cast<float4*>(P2 + nf * 512) = make_float4(mpos[0].x, mpos[S - 1].x, mpos[0].y, mpos[S - 1].y);
+        *reinterpret_cast<float2*>(E2 + nf * 256) = make_float2(e_motor, e_motor);
+      } else {
+        *reinterpret_cast<float2*>(Pb + nf * 256) = mpos[0];
+        *reinterpret_cast<float*>(Eb + nf * 128) = e_motor;
       }
     }
     const int ndl = has ? nd : 0;
@@ -280,9 +335,8 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
     for (int d = 0; d < ndw; ++d)
       if (d < ndl) {
         const float4 r0 = Rg[2 * d], r1 = Rg[2 * d + 1];
-#pragma unroll
-        for (int u = 0; u < S; ++u)
-          fp32_dyad_rec(r0, r1, Pb + u * ns * 256, Eb + u * ns * 128, lockw[u], zmin[u], isgmax[u]);
+        if (S == 2) fp32_dyad2(r0, r1, P2, E2, lockw, zmin, isgmax);
+        else fp32_dyad_rec(r0, r1, Pb, Eb, lockw[0], zmin[0], isgmax[0]);
       }
     // per step: certain lock, certain freedom, or a double-word rescue that decides
     int first = CH;  // first locking step of the chunk (group-uniform)
