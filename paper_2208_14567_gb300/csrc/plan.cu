@@ -211,10 +211,8 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
     S.set_slot(S.dk(d), nf + 1 + d);
     o.slot_joint[nf + 1 + d] = (uint8_t)S.dk(d);
   }
-  for (int s = 0; s < n; ++s) {
-    int a = o.slot_joint[s];
-    o.pos64[s] = make_double2((double)pos[2 * a], (double)pos[2 * a + 1]);
-  }
+  for (int a = 0; a < n; ++a)  // every joint has a slot (fixed, actuated or dyad)
+    o.pos64[S.slot(a)] = make_double2((double)pos[2 * a], (double)pos[2 * a + 1]);
 
   float bmax = 0.0f;
   {
