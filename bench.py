@@ -489,6 +489,30 @@ def main():
     roof.update({"traffic": traffic, "traffic_source": "ncu dram bytes of a 300k-candidate capture, scaled",
                  "kernel": top, "peak_source": pk["src"]})
 
+    # ---- the paper's two-stage screen on the same inputs: T/4 positions, then T for the
+    # mechanisms valid on the coarse grid (same valid flags and rows)
+    two = None
+    if T % 4 == 0:
+        n_low = torch.zeros(1, dtype=torch.int32, device=dev)
+        out2 = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=out.traj.shape[0])
+        sim.build(db, status)
+        sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
+        sim.sync()
+        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0e.record(stream)
+        for _ in range(args.steps):
+            sim.build(db, status)
+            sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
+        t1e.record(stream)
+        torch.cuda.synchronize(dev)
+        ms2 = t0e.elapsed_time(t1e) / args.steps
+        nl, n2 = int(n_low.item()), int(out2.n_out[0])
+        two = {"T_low": T // 4, "ms_per_step": ms2, "mechanism_steps_per_s": B * T / (ms2 * 1e-3),
+               "valid_on_coarse_grid": nl, "valid": n2, "false_valid_rate": (nl - n2) / max(nl, 1),
+               "same_valid_flags": bool(torch.equal(out2.valid, out.valid))}
+        del out2
+        torch.cuda.empty_cache()
+
     # ---- plain FP64 kernel on the same inputs (the comparator named by the metric)
     f64_out = sim.alloc(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out_capacity=max(n_valid, 1))
     sim.build(db, status)
@@ -604,6 +628,7 @@ def main():
         "config": {"workload": WORKLOAD, "batch": B, "T": T, "joints": "6-8", "precision": "mixed",
                    "out_mode": "valid_only", "valid_rows": n_valid,
                    "l2": "inputs 140 MB per step exceed the 126 MB L2; no flush", "parallelism": f"replicas x{world}"},
+        "two_stage_screen": two,
         "plain_f64": {"value": world * B * T / (f64_ms * 1e-3), "ms_per_step": f64_ms,
                       "speedup_of_mixed": f64_ms / ms, "same_valid_flags": same_flags},
         "algorithmic_dyad_steps_per_step": dyad_steps,

@@ -161,6 +161,23 @@ LINKS_API int links_simulate(links_ctx ctx, links_plan plan, int T, int precisio
                    void* traj, void* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
 
+/* Two-stage screen (Sec. "Finding Valid Initial Positions", paragraph on low fidelity
+ * evaluations): LINKS_MIXED simulation of every OK mechanism on the coarse grid of
+ * T_low actuator positions, then on the full grid of T positions only for the
+ * mechanisms valid on the coarse one, then the valid rows as in links_simulate with
+ * LINKS_OUT_VALID_ONLY (traj [out_capacity, n_max, T, 2], path [out_capacity, T, 2],
+ * out_index, *n_out; all device).  T_low must divide T, so the coarse angles
+ * 2 pi t / T_low are fine-grid angles: a coarse lock is a fine lock, and valid[] is
+ * exactly the full-grid verdict.  For the mechanisms the coarse pass rejects,
+ * lock_step is that locking step scaled to the fine grid (a locking step, not
+ * necessarily the first) and min_disc covers the coarse steps before it; for the
+ * others all outputs are those of links_simulate.  *n_low_valid (device int32, may be
+ * NULL) receives the number valid on the coarse grid, so n_low_valid - *n_out counts
+ * the coarse grid's false valids.  Asynchronous.  LINKS_EINVAL for bad arguments. */
+LINKS_API int links_simulate_two_stage(links_ctx ctx, links_plan plan, int T, int T_low, float* traj, float* path,
+                                       uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                                       int64_t out_capacity, int32_t* n_out, int32_t* n_low_valid);
+
 /* Census of the LINKS_MIXED emit (the work its precision design does; no
  * counterpart in the paper): runs the emit's FP32 chain and forward error bound
  * (Sec. "Graphical Simulator" steps) over the rows links_simulate wrote for this plan

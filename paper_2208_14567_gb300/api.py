@@ -116,5 +116,17 @@ class Simulator:
                          out.min_disc, out.out_index, cap, out.n_out)
         return out
 
+    def simulate_two_stage(self, T: int, T_low: int, out: SimOut | None = None, traj=True, path=True,
+                           out_capacity=None, n_low_valid=None) -> SimOut:
+        """Low-fidelity screen on T_low positions, confirmation on T of the survivors,
+        valid rows out (links_simulate_two_stage)."""
+        if out is None:
+            out = self.alloc(T, L.MIXED, L.OUT_VALID_ONLY, traj, path, out_capacity)
+        cap = out.traj.shape[0] if out.traj is not None else (out.path.shape[0] if out.path is not None else
+                                                              out.out_index.shape[0])
+        L.links_simulate_two_stage(self.ctx, self.plan, T, T_low, out.traj, out.path, out.valid, out.lock_step,
+                                   out.min_disc, out.out_index, cap, out.n_out, n_low_valid)
+        return out
+
     def sync(self):
         L.links_sync(self.ctx)

@@ -230,6 +230,7 @@ int links_plan_create(links_ctx ctx, int64_t capacity, int n_max, links_plan* ou
   alloc((void**)&d.pos64, sizeof(double2) * n_max * c);
   alloc((void**)&d.dyad, sizeof(DyadRec) * d.max_dyads * c);
   alloc((void**)&d.order, sizeof(int32_t) * c);
+  alloc((void**)&d.order2, sizeof(int32_t) * c);
   alloc((void**)&d.ctrs, sizeof(int32_t) * kCtrs);
   alloc((void**)&d.scan, sizeof(int32_t) * (c / 1024 + 2));
   if (e == cudaSuccess) e = cudaMemset(d.ctrs, 0, sizeof(int32_t) * kCtrs);
@@ -250,6 +251,7 @@ int links_plan_free(links_plan plan) {
   cudaFree(d.pos64);
   cudaFree(d.dyad);
   cudaFree(d.order);
+  cudaFree(d.order2);
   cudaFree(d.ctrs);
   cudaFree(d.scan);
   delete plan;
@@ -369,6 +371,27 @@ int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out
                         out_index, out_capacity, n_out);
   return simulate_mixed(ctx, plan, tab, out_mode, (float*)traj, (float*)path, valid, lock_step, min_disc,
                         out_index, out_capacity, n_out);
+}
+
+int links_simulate_two_stage(links_ctx ctx, links_plan plan, int T, int T_low, float* traj, float* path,
+                             uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                             int64_t out_capacity, int32_t* n_out, int32_t* n_low_valid) {
+  if (!ctx || !plan) return set_error(LINKS_EINVAL, "links_simulate_two_stage: NULL ctx or plan");
+  if (plan->ctx != ctx) return set_error(LINKS_EINVAL, "links_simulate_two_stage: plan belongs to another context");
+  if (T < 1 || T > LINKS_MAX_T || T_low < 1 || T_low > T || T % T_low != 0)
+    return set_error(LINKS_EINVAL, "links_simulate_two_stage: need 1 <= T_low <= T <= 32767 and T_low dividing T");
+  if (plan->B > 0 && (!valid || !lock_step || !min_disc))
+    return set_error(LINKS_EINVAL, "links_simulate_two_stage: valid, lock_step and min_disc are required");
+  if (out_capacity < 0 || ((traj || path) && out_capacity > 0 && !out_index))
+    return set_error(LINKS_EINVAL, "links_simulate_two_stage: rows need out_index and out_capacity >= 0");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  int st = LINKS_OK;
+  const TTable* tab_lo = get_table(ctx, T_low, &st);
+  if (!tab_lo) return st;
+  const TTable* tab = get_table(ctx, T, &st);
+  if (!tab) return st;
+  return simulate_two_stage(ctx, plan, tab_lo, tab, traj, path, valid, lock_step, min_disc, out_index, out_capacity,
+                            n_out, n_low_valid);
 }
 
 int links_emit_census(links_ctx ctx, links_plan plan, int T, int out_mode, const int16_t* lock_step,

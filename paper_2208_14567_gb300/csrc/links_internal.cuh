@@ -76,6 +76,7 @@ struct PlanDev {
   double2* pos64;        // [cap][n_max]   absolute initial positions by slot (FP64 path)
   DyadRec* dyad;         // [cap][n_max - 2]
   int32_t* order;        // [cap]          OK mechanisms sorted by dyad count
+  int32_t* order2;       // [cap]          confirmation work list of the two-stage screen
   int32_t* ctrs;         // [kCtrs]        histogram / cursors / work counters
   int32_t* scan;         // [cap/1024 + 2] block sums of the valid-row scan
   int32_t* row_of;       // [cap]          output row of each mechanism (VALID_ONLY), or -1
@@ -90,6 +91,7 @@ constexpr int kCursor = 32;       // [32] scatter cursors
 constexpr int kWork = 64;         // work counter of the screen / FP64 kernels
 constexpr int kWork2 = 65;        // work counter of the emit kernel
 constexpr int kNValid = 66;       // number of valid mechanisms (VALID_ONLY rows)
+constexpr int kNConfirm = 67;     // length of the two-stage screen's confirmation list
 // census counts of the emit (links_emit_census), 64-bit each (two slots)
 constexpr int kStatEmitSteps = 68;     // steps the emit computes
 constexpr int kStatEmitDW = 70;        // ... that its FP32 bound sends to double-word
@@ -183,6 +185,9 @@ int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_
 int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, double* traj,
                  double* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                  int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, const TTable* tab, float* traj,
+                       float* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                       int64_t out_capacity, int32_t* n_out, int32_t* n_low_valid);
 int emit_census(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, const int16_t* lock_step,
                 const int32_t* out_index, int64_t out_capacity, int64_t* out);
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,

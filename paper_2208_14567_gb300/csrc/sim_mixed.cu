@@ -224,11 +224,15 @@ __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char*
 // Groups of G lanes screen one mechanism; each lane takes S steps of a chunk of G * S
 // consecutive steps (step chunk * G * S + u * G + lane-in-group, u < S), so that one
 // load of a dyad record serves S steps.  The slot arrays hold S columns per lane.
+// The work list is order[0, n) with n = *n_list, or p.order and the number of OK
+// mechanisms when n_list is null.
 template <int G, int S>
 __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
                                                         uint8_t* __restrict__ valid,
                                                         int16_t* __restrict__ lock_step,
-                                                        float* __restrict__ min_disc) {
+                                                        float* __restrict__ min_disc,
+                                                        const int32_t* __restrict__ order,
+                                                        const int32_t* __restrict__ n_list) {
   extern __shared__ float4 smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ns = p.n_max;
@@ -247,9 +251,14 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
   constexpr int CH = G * S;  // steps per chunk
 
-  int n_ok = p.ctrs[kHist + lane];
+  int n_ok = 0;
+  if (n_list) {
+    n_ok = *n_list;
+  } else {
+    n_ok = p.ctrs[kHist + lane];
 #pragma unroll
-  for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(kFull, n_ok, o);
+    for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(kFull, n_ok, o);
+  }
 
   int qhead = 0, qend = 0;
   bool exhausted = false;
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
     __syncwarp();  // the previous mechanism's records are no longer read
 
     if (fresh) {
-      b = p.order[item];
+      b = order[item];
       const MechHdr* hp = p.hdr + b;
       const int4 w0 = __ldg(reinterpret_cast<const int4*>(hp));
       nd = (w0.y >> 8) & 0xff;
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
 
 template <int G, int S>
 int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
-                  int16_t* lock_step, float* min_disc) {
+                  int16_t* lock_step, float* min_disc, const int32_t* order, const int32_t* n_list) {
   PlanDev& p = plan->d;
   size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
   static bool attr_set = false;
@@ -531,23 +540,60 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
   {
     KernelScope ks(ctx, "mixed_screen");
-    screen_kernel<G, S><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(p, T, tab->cs, valid, lock_step,
-                                                                            min_disc);
+    screen_kernel<G, S><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
+        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list);
   }
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
 }
 
 int launch_screen_lanes(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
-                        int16_t* lock_step, float* min_disc, int lanes) {
+                        int16_t* lock_step, float* min_disc, int lanes, const int32_t* order = nullptr,
+                        const int32_t* n_list = nullptr) {
   if (plan->d.n_max <= kScreenTwoStepMaxSlots) {
-    if (lanes == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
-    if (lanes == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
-    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc);
+    if (lanes == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+    if (lanes == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
   }
-  if (lanes == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
-  if (lanes == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
-  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc);
+  if (lanes == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+  if (lanes == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+}
+
+// After the low-fidelity pass: the mechanisms it found valid go, in work-list order
+// within each block, to the confirmation list; the others keep their verdict, their
+// lock step scaled to the fine grid (a locking step there: the coarse angles are fine
+// grid angles).
+__global__ void __launch_bounds__(256) confirm_list_kernel(PlanDev p, const uint8_t* __restrict__ valid,
+                                                           int16_t* __restrict__ lock_step, int ratio) {
+  __shared__ int base;
+  int n_ok = 0;
+  for (int i = 0; i < 32; ++i) n_ok += p.ctrs[kHist + i];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = -1;
+  bool keep = false;
+  if (i < n_ok) {
+    b = p.order[i];
+    keep = valid[b] != 0;
+    if (!keep && lock_step[b] >= 0) lock_step[b] = (int16_t)(lock_step[b] * ratio);
+  }
+  // block-aggregated append: one atomic per block, positions in work-list order
+  const unsigned m = __ballot_sync(0xffffffffu, keep);
+  __shared__ int wcount[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) wcount[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w = 0; w < 8; ++w) {
+      const int c = wcount[w];
+      wcount[w] = tot;
+      tot += c;
+    }
+    base = tot ? atomicAdd(&p.ctrs[kNConfirm], tot) : 0;
+  }
+  __syncthreads();
+  if (keep) p.order2[base + wcount[warp] + __popc(m & ((1u << lane) - 1u))] = b;
 }
 
 int screen_lanes(links_ctx ctx, links_plan plan) {
@@ -636,6 +682,36 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
   }
   if (traj || path)
     return launch_emit<false>(ctx, plan, tab, full, lock_step, out_index, out_capacity, traj, path, "mixed_emit");
+  return LINKS_OK;
+}
+
+// Low-fidelity screen on the coarse grid (tab_lo), confirmation on the fine grid (tab)
+// of the mechanisms valid on the coarse one, then valid-row compaction and emit.
+int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, const TTable* tab, float* traj,
+                       float* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                       int64_t out_capacity, int32_t* n_out, int32_t* n_low_valid) {
+  PlanDev& p = plan->d;
+  int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
+  if (st) return st;
+  const int lanes = screen_lanes(ctx, plan);
+  st = launch_screen_lanes(ctx, plan, tab_lo->T, tab_lo, valid, lock_step, min_disc, lanes);
+  if (st) return st;
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kNConfirm, 0, sizeof(int32_t), ctx->stream));
+  if (plan->B > 0) {
+    KernelScope ks(ctx, "confirm_list");
+    confirm_list_kernel<<<(unsigned)((plan->B + 255) / 256), 256, 0, ctx->stream>>>(p, valid, lock_step,
+                                                                                   tab->T / tab_lo->T);
+    LINKS_CUDA(cudaGetLastError());
+  }
+  if (n_low_valid)
+    LINKS_CUDA(cudaMemcpyAsync(n_low_valid, p.ctrs + kNConfirm, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+  st = launch_screen_lanes(ctx, plan, tab->T, tab, valid, lock_step, min_disc, lanes, p.order2, p.ctrs + kNConfirm);
+  if (st) return st;
+  st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
+  if (st) return st;
+  if (traj || path)
+    return launch_emit<false>(ctx, plan, tab, false, lock_step, out_index, out_capacity, traj, path, "mixed_emit");
   return LINKS_OK;
 }
 

@@ -69,6 +69,7 @@ def lib():
             "links_plan_export": ([P, i64, i64, P, P], i32),
             "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
             "links_emit_census": ([P, P, i32, i32, P, P, i64, P], i32),
+            "links_simulate_two_stage": ([P, P, i32, i32, P, P, P, P, P, P, i64, P, P], i32),
             "links_normalize": ([P, i64, i32, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
@@ -232,6 +233,18 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
                                 _dev(out_index, torch.int32, "out_index"), int(out_capacity),
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_simulate_two_stage(ctx, plan, T: int, T_low: int, traj, path, valid, lock_step, min_disc,
+                             out_index=None, out_capacity: int = 0, n_out=None, n_low_valid=None):
+    import torch
+    _check(lib().links_simulate_two_stage(ctx, plan, int(T), int(T_low), _dev(traj, torch.float32, "traj"),
+                                          _dev(path, torch.float32, "path"), _dev(valid, torch.uint8, "valid"),
+                                          _dev(lock_step, torch.int16, "lock_step"),
+                                          _dev(min_disc, torch.float32, "min_disc"),
+                                          _dev(out_index, torch.int32, "out_index"), int(out_capacity),
+                                          _dev(n_out, torch.int32, "n_out"), _dev(n_low_valid, torch.int32, "n_low_valid")),
+           "links_simulate_two_stage")
 
 
 def links_emit_census(ctx, plan, T: int, out_mode: int, lock_step=None, out_index=None, out_capacity: int = 0):

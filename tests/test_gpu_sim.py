@@ -251,6 +251,46 @@ def test_emit_census(L):
         s.close()
 
 
+@pytest.mark.parametrize("case", ["dyad6-8", "dyad6-20"])
+def test_two_stage_screen(L, case):
+    """links_simulate_two_stage: the coarse grid's angles are fine-grid angles, so the
+    valid flags, the valid rows and their outputs equal the single-stage run; rejected
+    mechanisms carry a fine-grid locking step no earlier than the first one."""
+    import torch
+    from paper_2208_14567_gb300.api import to_device
+    batch = I.dyad_batch(5000, 6, 8, seed=21) if case == "dyad6-8" else I.dyad_batch(4000, 6, 20, seed=22, nmax=20)
+    T, T_low = 200, 50
+    s = sim_for(batch, L)
+    try:
+        st = s.build(to_device(batch)).cpu().numpy()
+        one = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY)
+        s.sync()
+        ref = {k: (None if v is None else v.cpu().numpy().copy()) for k, v in one.__dict__.items()}
+        n_low = torch.zeros(1, dtype=torch.int32, device="cuda")
+        two = s.simulate_two_stage(T, T_low, n_low_valid=n_low)
+        s.sync()
+        got = {k: (None if v is None else v.cpu().numpy()) for k, v in two.__dict__.items()}
+        n = int(ref["n_out"][0])
+        assert int(got["n_out"][0]) == n and np.array_equal(got["valid"], ref["valid"])
+        assert np.array_equal(got["out_index"][:n], ref["out_index"][:n])
+        assert np.array_equal(got["traj"][:n], ref["traj"][:n], equal_nan=True)
+        assert np.array_equal(got["path"][:n], ref["path"][:n], equal_nan=True)
+        v = ref["valid"] == 1
+        assert np.array_equal(got["lock_step"][v], ref["lock_step"][v])
+        assert np.array_equal(got["min_disc"][v], ref["min_disc"][v])
+        rej = (st == 0) & ~v
+        assert (got["lock_step"][rej] >= ref["lock_step"][rej]).all()
+        coarse = got["lock_step"][rej] != ref["lock_step"][rej]
+        assert (got["lock_step"][rej][coarse] % (T // T_low) == 0).all()
+        nl = int(n_low.item())
+        assert nl >= n
+        print(f"[{case}] valid {n}, valid on {T_low} positions {nl}: false-valid rate {(nl - n) / max(nl, 1):.4f}")
+        with pytest.raises(L.LinksError):
+            s.simulate_two_stage(T, 60)
+    finally:
+        s.close()
+
+
 @pytest.mark.parametrize("T", [1, 7, 33, 64])
 def test_ragged_steps_and_statuses(L, T):
     batch = planted_bad(I.dyad_batch(700, 6, 12, seed=6, permute=True))
