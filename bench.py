@@ -235,6 +235,48 @@ def path_stage(args, local, stream):
         L.links_destroy(ctx)
 
 
+def paper_generator_stage(args, local, stream):
+    """The paper's own candidates (standardised positions, topology rules) for a sweep of
+    joint counts: the valid rate (and random samples per valid candidate, the paper's
+    infeasibility curve) and the screen time, single-stage and two-stage (T/4 first)."""
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T, K, S = args.T, 256, 1024
+    dev = torch.device("cuda", local)
+    rows = []
+    for n in (6, 8, 10, 12, 15, 20):
+        batch = I.paper_batch(K, S, n, seed=n)
+        with Simulator(batch.B, n, device=local, stream=stream) as s:
+            db = to_device(batch, dev)
+            st = s.build(db)
+            one = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+            two = s.alloc(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+            n_low = torch.zeros(1, dtype=torch.int32, device=dev)
+            s.simulate_two_stage(T, T // 4, out=two, n_low_valid=n_low)
+            s.sync()
+            times = {}
+            for name, fn in (("single", lambda: s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=one)),
+                             ("two_stage", lambda: s.simulate_two_stage(T, T // 4, out=two, n_low_valid=n_low))):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    s.build(db, st)
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                times[name] = e0.elapsed_time(e1) / 3
+            nv = int(one.n_out[0])
+            rows.append({"joints": n, "candidates": batch.B, "valid": nv, "valid_rate": nv / batch.B,
+                         "samples_per_valid": batch.B / max(nv, 1), "valid_on_coarse_grid": int(n_low.item()),
+                         "same_flags": bool(torch.equal(one.valid, two.valid)),
+                         "ms_single": times["single"], "ms_two_stage": times["two_stage"]})
+        torch.cuda.empty_cache()
+    return {"topologies_per_n": K, "positions_per_topology": S, "T": T, "sweep": rows}
+
+
 def serve_stage(args, local, stream):
     """Poisson arrivals of requests of log-uniform size on [1, 65536] candidates of
     6-20 joints, served by the continuous-batching loop; p50/p99 latency (submit to
@@ -363,6 +405,7 @@ def main():
     ap.add_argument("--path-queries", type=int, default=1024)
     ap.add_argument("--no-path-stage", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-paper-generator", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=600_000)
@@ -620,6 +663,7 @@ def main():
         return
     ps = None if args.no_path_stage or world > 1 else path_stage(args, local, stream)
     sv = None if args.no_serve or world > 1 else serve_stage(args, local, stream)
+    pg = None if args.no_paper_generator or world > 1 else paper_generator_stage(args, local, stream)
     cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -638,6 +682,7 @@ def main():
         "cpu_baseline": cb,
         "path_stage": ps,
         "serve": sv,
+        "paper_generator": pg,
         "e2e": e2e,
         "e2e_full": e2e_full,
         "gpu_launches": int(launches * args.steps),

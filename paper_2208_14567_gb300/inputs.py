@@ -197,6 +197,97 @@ def dyad_batch(B: int, n_lo: int, n_hi: int, seed: int = 0, *, ground_max: int =
     return batch
 
 
+def topology_rules(batch: MechBatch) -> tuple[np.ndarray, np.ndarray]:
+    """The paper's topology rules (Sec. "Dataset Features", rules of topology creation)
+    for candidates built by ``dyad_batch`` without permutation, where joint k's parents
+    are its neighbours of lower index and the last joint is the last one solved:
+
+    * irreducible: the last joint depends, through its parents, on every joint;
+    * the last joint is not linked to a fixed joint.
+
+    Returns the two boolean masks [B]."""
+    B, nmax = batch.B, batch.nmax
+    n = batch.n_joints
+    rows = np.arange(B)
+    anc = np.zeros((B, nmax), dtype=np.uint64)
+    anc[:, 0] = 1
+    anc[:, 1] = 3  # the actuated joint turns about joint 0
+    lower = np.tril(np.ones((nmax, nmax), dtype=bool), -1)
+    for k in range(2, nmax):
+        live = k < n
+        fixed = batch.jtype[:, k] == FIXED
+        par = (batch.adj[:, k, :] != 0) & lower[k][None, :]  # neighbours of lower index
+        dep = np.bitwise_or.reduce(np.where(par, anc, np.uint64(0)), axis=1)
+        anc[:, k] = np.where(live, np.uint64(1) << np.uint64(k), 0) | np.where(live & ~fixed, dep, 0)
+    last = n - 1
+    full = (np.uint64(1) << n.astype(np.uint64)) - np.uint64(1)
+    irreducible = anc[rows, last] == full
+    isfix = batch.jtype == FIXED
+    linked = (batch.adj[rows, last, :] != 0) & isfix
+    return irreducible, ~linked.any(axis=1)
+
+
+def paper_topologies(K: int, n: int, seed: int = 0, *, ground_max: int = 3, p_ground: float = 0.25) -> MechBatch:
+    """K topologies of n joints from the J operator that meet the paper's topology rules
+    (``topology_rules``).  The operator's pairs are drawn with the heuristic the rules
+    suggest: the first parent of a new joint is a joint that no joint depends on yet
+    (fixed ones first), so that at the end only the last joint is left without
+    dependants; candidates that still break a rule are drawn again."""
+    if n < 5:
+        raise ValueError("need n >= 5 for a topology with a free final joint")
+    st = Stream(seed, 700 + _T_PAIR)
+    adj = np.zeros((K, n, n), dtype=np.uint8)
+    jt = np.full((K, n), PAD, dtype=np.int8)
+    for t in range(K):
+        for attempt in range(1000):
+            u = st.uniform(np.uint64(t) * np.uint64(1 << 20) + np.uint64(attempt) * np.uint64(1 << 10)
+                           + np.arange(4 * n, dtype=np.uint64))
+            a = np.zeros((n, n), dtype=np.uint8)
+            typ = np.full(n, SIMPLE, dtype=np.int8)
+            typ[0], typ[1], typ[2] = FIXED, MOTOR, FIXED
+            a[0, 1] = a[1, 0] = 1
+            sinks = [2, 1]  # joints nothing depends on yet, fixed ones first
+            nfix = 2
+            for k in range(3, n):
+                r = u[4 * k: 4 * k + 4]
+                if k < n - 2 and nfix < ground_max and r[0] < p_ground:
+                    typ[k] = FIXED
+                    nfix += 1
+                    sinks.insert(0, k)
+                    continue
+                i = sinks[0]
+                cand = [c for c in range(k) if c != i and not (typ[c] == FIXED and typ[i] == FIXED)]
+                if k == n - 1:  # the last joint: no fixed parent
+                    cand = [c for c in cand if typ[c] != FIXED]
+                j = cand[min(int(r[1] * len(cand)), len(cand) - 1)] if cand else i
+                a[k, i] = a[i, k] = a[k, j] = a[j, k] = 1
+                sinks = [c for c in sinks if c not in (i, j)] + [k]
+            trial = MechBatch(np.array([n], dtype=np.int32), a[None], typ[None], np.zeros((1, n, 2)))
+            irr, free = topology_rules(trial)
+            if irr[0] and free[0]:
+                adj[t], jt[t] = a, typ
+                break
+        else:
+            raise RuntimeError("no topology met the rules in 1000 draws")
+    return MechBatch(np.full(K, n, dtype=np.int32), adj, jt, np.zeros((K, n, 2)))
+
+
+def paper_batch(n_topologies: int, samples: int, n: int, seed: int = 0) -> MechBatch:
+    """The paper's own candidates (Sec. "Dataset Features"): ``n_topologies`` topologies of
+    n joints meeting the topology rules (``paper_topologies``), each with ``samples``
+    random initial positions standardised as the paper does: the actuator's ground
+    joint at (0.5, 0.5), the actuator arm of length 0.05 and horizontal (actuated joint
+    at (0.55, 0.5)), every other joint uniform in the unit square.  Candidates are
+    topology-major."""
+    t = paper_topologies(n_topologies, n, seed)
+    rep = np.repeat(np.arange(n_topologies), samples)
+    pos = _positions(Stream(seed, 900 + _T_POS), rep.size, n, t.n_joints[rep], np.float64)
+    pos[:, 0] = (0.5, 0.5)
+    pos[:, 1] = (0.55, 0.5)
+    return MechBatch(t.n_joints[rep].copy(), np.ascontiguousarray(t.adj[rep]), np.ascontiguousarray(t.jtype[rep]),
+                     pos.astype(np.float32))
+
+
 def _permute(batch: MechBatch, st: Stream) -> MechBatch:
     B, nmax = batch.B, batch.nmax
     key = st.uniform(np.arange(B, dtype=np.uint64)[:, None] * np.uint64(64)

@@ -1,5 +1,6 @@
 """The seeded input generator: determinism and the structure the recipes promise."""
 import numpy as np
+import pytest
 
 from paper_2208_14567_gb300 import inputs as I
 
@@ -81,3 +82,59 @@ def test_perturb_and_requests():
     assert n.min() >= 1 and n.max() <= 65536
     # log-uniform: the median is near sqrt(65537)
     assert 150 < np.median(n) < 350
+
+
+@pytest.mark.parametrize("n", [6, 9, 14, 20])
+def test_paper_topologies_meet_the_rules(n):
+    """The paper's topology rules, checked from the oracle's solve path: every joint is an
+    ancestor of the last-solved joint, which has no fixed neighbour; 1-DOF and
+    dyad-solvable (oracle status OK)."""
+    from oracle import oracle as O
+    t = I.paper_topologies(24, n, seed=n)
+    for b in range(t.B):
+        P = O.plan(n, t.adj[b], t.jtype[b], np.zeros((n, 2)))
+        assert P.status == 0
+        assert P.coupler == n - 1
+        parents = {P.k[d]: (P.i[d], P.j[d]) for d in range(P.n_dyads)}
+        parents[P.motor] = (P.pivot,)
+        seen, stack = set(), [P.coupler]
+        while stack:
+            a = stack.pop()
+            if a not in seen:
+                seen.add(a)
+                stack.extend(parents.get(a, ()))
+        assert seen == set(range(n))
+        fixed = set(np.nonzero(t.jtype[b, :n] == I.FIXED)[0].tolist())
+        assert not (set(np.nonzero(t.adj[b, n - 1, :n])[0].tolist()) & fixed)
+
+
+def test_topology_rules_flags_breaking_topologies():
+    """topology_rules against a direct check on random J-operator candidates: most of them
+    break a rule, and the masks agree with the solve-path check."""
+    from oracle import oracle as O
+    d = I.dyad_batch(400, 7, 7, seed=3)
+    irr, free = I.topology_rules(d)
+    assert 0 < irr.mean() < 1 and 0 < free.mean() < 1
+    for b in range(60):
+        n = int(d.n_joints[b])
+        P = O.plan(n, d.adj[b], d.jtype[b], d.pos[b].astype(np.float64))
+        parents = {P.k[q]: (P.i[q], P.j[q]) for q in range(P.n_dyads)}
+        parents[P.motor] = (P.pivot,)
+        seen, stack = set(), [P.coupler]
+        while stack:
+            a = stack.pop()
+            if a not in seen:
+                seen.add(a)
+                stack.extend(parents.get(a, ()))
+        assert irr[b] == (seen == set(range(n)))
+        assert free[b] == (not (d.adj[b, P.coupler, :n] & (d.jtype[b, :n] == I.FIXED)).any())
+
+
+def test_paper_batch_standardised_positions():
+    b = I.paper_batch(8, 16, 10, seed=5)
+    assert b.B == 128 and b.nmax == 10
+    assert np.all(b.pos[:, 0] == np.float32(0.5)) and np.all(b.pos[:, 1, 0] == np.float32(0.55))
+    assert np.all(b.pos[:, 1, 1] == np.float32(0.5))
+    assert (b.pos >= 0).all() and (b.pos <= 1).all()
+    assert np.array_equal(b.adj[0], b.adj[15])  # topology-major: 16 samples per topology
+    assert np.array_equal(b.pos, I.paper_batch(8, 16, 10, seed=5).pos)
