@@ -301,6 +301,63 @@ void lo_normalize(int64_t m0, int64_t m1, int T, const double* in, double* out) 
     }
 }
 
+/* The paper's path normalisation (Sec. "Dataset Curation & Processing"): find the line of
+ * maximum distance between two points of the path, rotate the path so that this line is
+ * horizontal, scale it so that the line has length 1, and centre the path in the unit
+ * box.  Readings: the line joins the pair (a, b), a < b, of largest distance, the first
+ * such pair in (a, b) order on ties; the rotation takes p_b - p_a onto +x; "centre" puts
+ * the centre of the bounding box at (0.5, 0.5); a path of equal points becomes (0.5, 0.5)
+ * everywhere.  If pair_in is not NULL it gives the pair to use instead of the search
+ * (to compare with a computation whose float rounding picked a near-tied pair).
+ * pair_out [2] and circ_var (the population variance of the distances of the normalised
+ * points from (0.5, 0.5), the paper's circle statistic) may be NULL. */
+void lo_normalize_maxline(int T, const double* p, double* o, const int32_t* pair_in, int32_t* pair_out,
+                          double* circ_var) {
+    int a = 0, b = T > 1 ? 1 : 0;
+    if (pair_in) {
+        a = pair_in[0];
+        b = pair_in[1];
+    } else {
+        double best = -1.0;
+        for (int u = 0; u < T; ++u)
+            for (int v = u + 1; v < T; ++v) {
+                double d = sq_dist(p + 2 * u, p + 2 * v);
+                if (d > best) { best = d; a = u; b = v; }
+            }
+    }
+    if (pair_out) { pair_out[0] = a; pair_out[1] = b; }
+    double dx = p[2 * b] - p[2 * a], dy = p[2 * b + 1] - p[2 * a + 1];
+    double d = sqrt(dx * dx + dy * dy);
+    if (!(d > 0.0)) {
+        for (int t = 0; t < T; ++t) { o[2 * t] = 0.5; o[2 * t + 1] = 0.5; }
+        if (circ_var) *circ_var = 0.0;
+        return;
+    }
+    double c = dx / d, s = dy / d;  /* rotation by minus the line's angle, and 1/d scale */
+    double x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+    for (int t = 0; t < T; ++t) {
+        double x = p[2 * t] - p[2 * a], y = p[2 * t + 1] - p[2 * a + 1];
+        double xr = (c * x + s * y) / d, yr = (-s * x + c * y) / d;
+        o[2 * t] = xr;
+        o[2 * t + 1] = yr;
+        if (xr < x0) x0 = xr;
+        if (xr > x1) x1 = xr;
+        if (yr < y0) y0 = yr;
+        if (yr > y1) y1 = yr;
+    }
+    double sx = 0.5 - 0.5 * (x0 + x1), sy = 0.5 - 0.5 * (y0 + y1);
+    double m = 0.0, m2 = 0.0;
+    for (int t = 0; t < T; ++t) {
+        o[2 * t] += sx;
+        o[2 * t + 1] += sy;
+        double r = sqrt((o[2 * t] - 0.5) * (o[2 * t] - 0.5) + (o[2 * t + 1] - 0.5) * (o[2 * t + 1] - 0.5));
+        m += r;
+        m2 += r * r;
+    }
+    m /= T;
+    if (circ_var) *circ_var = m2 / T - m * m;
+}
+
 /* Bidirectional chamfer distance: mean over P of the Euclidean distance to the
  * nearest point of Q, plus the same from Q to P. */
 double lo_chamfer(int tp, const double* P, int tq, const double* Q) {

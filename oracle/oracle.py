@@ -59,6 +59,8 @@ def _bind(L):
     L.lo_simulate.restype = None
     L.lo_normalize.argtypes = [i64, i64, i32, P, P]
     L.lo_normalize.restype = None
+    L.lo_normalize_maxline.argtypes = [i32, P, P, P, P, P]
+    L.lo_normalize_maxline.restype = None
     L.lo_chamfer.argtypes = [i32, P, i32, P]
     L.lo_chamfer.restype = ctypes.c_double
     L.lo_chamfer_many.argtypes = [i32, P, i64, i64, i32, P, P]
@@ -176,6 +178,23 @@ def normalize(curves: np.ndarray, threads: int | None = None) -> np.ndarray:
     L = lib()
     _run_parallel(lambda a, b: L.lo_normalize(a, b, T, _ptr(c), _ptr(out)), M, threads)
     return out
+
+
+def normalize_maxline(curves: np.ndarray, pairs: np.ndarray | None = None):
+    """The paper's normalisation (lo_normalize_maxline) of [M, T, 2] curves.
+    -> (normalised [M, T, 2], pair [M, 2] int32, circle variance [M]).  ``pairs`` [M, 2]
+    imposes the pair of each curve instead of the maximum-distance search."""
+    c = np.ascontiguousarray(curves, dtype=np.float64)
+    M, T = c.shape[0], c.shape[1]
+    out = np.empty_like(c)
+    pair = np.zeros((M, 2), dtype=np.int32)
+    var = np.zeros(M, dtype=np.float64)
+    pin = None if pairs is None else np.ascontiguousarray(pairs, dtype=np.int32)
+    L = lib()
+    for m in range(M):
+        L.lo_normalize_maxline(T, _ptr(c[m]), _ptr(out[m]), None if pin is None else _ptr(pin[m]),
+                               _ptr(pair[m]), _ptr(var[m:]))
+    return out, pair, var
 
 
 def chamfer(p: np.ndarray, q: np.ndarray) -> float:

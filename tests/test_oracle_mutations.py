@@ -24,6 +24,15 @@ MUTANTS = {
     "normalise sign rule flipped": ("if (s3 < 0.0)", "if (s3 > 0.0)"),
     "squared chamfer": ("double d = sqrt(sq_dist(P + 2 * a, Q + 2 * b));", "double d = sq_dist(P + 2 * a, Q + 2 * b);"),
     "one-directional chamfer": ("return sp / tp + sq / tq;", "return sp / tp;"),
+    "max line rotated the wrong way": ("double xr = (c * x + s * y) / d, yr = (-s * x + c * y) / d;",
+                                       "double xr = (c * x - s * y) / d, yr = (s * x + c * y) / d;"),
+    "max line not scaled": ("double xr = (c * x + s * y) / d, yr = (-s * x + c * y) / d;",
+                            "double xr = (c * x + s * y), yr = (-s * x + c * y);"),
+    "max line centred at the first point": ("double sx = 0.5 - 0.5 * (x0 + x1), sy = 0.5 - 0.5 * (y0 + y1);",
+                                            "double sx = 0.0, sy = 0.5;"),
+    "max line pair not the farthest": ("if (d > best) { best = d; a = u; b = v; }",
+                                       "if (d > best && v == u + 1) { best = d; a = u; b = v; }"),
+    "circle variance of squared radii": ("m2 += r * r;", "m2 += r * r * r * r;"),
 }
 
 
@@ -52,6 +61,10 @@ def run_pins(lib):
             lambda: pins.test_normalize_properties_and_invariance(O, fourbars),
             lambda: pins.test_normalize_ellipse_and_degenerate(O),
             lambda: pins.test_chamfer_against_cdist(O),
+            lambda: pins.test_maxline_circle_ellipse_segment(O),
+            lambda: pins.test_maxline_pair_is_the_farthest_pair(O),
+            lambda: pins.test_maxline_similarity_invariance_and_mirror(O),
+            lambda: pins.test_maxline_degenerate_and_imposed_pair(O),
         ]
         for i, c in enumerate(checks):
             try:

@@ -426,3 +426,78 @@ def test_topk_ties_go_to_lower_index(oracle_lib):
     d = np.array([3.0, 1.0, 2.0, 1.0, 1.0, 0.5])
     idx, dist = oracle_lib.topk(d, 4)
     assert list(idx) == [5, 1, 3, 4]
+
+
+# ---- the paper's max-distance-line normalisation (Sec. "Dataset Curation & Processing")
+
+def _similar(c, seed):
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0, 2 * np.pi)
+    R = np.array([[np.cos(a), -np.sin(a)], [np.sin(a), np.cos(a)]])
+    return rng.uniform(0.2, 5) * c @ R.T + rng.normal(size=2) * 3
+
+
+def test_maxline_circle_ellipse_segment(oracle_lib):
+    O = oracle_lib
+    s = np.linspace(0, 2 * np.pi, 200, endpoint=False)
+    circle = np.stack([3 + 2 * np.cos(s), -1 + 2 * np.sin(s)], -1)
+    ellipse = _similar(np.stack([3 * np.cos(s), np.sin(s)], -1), 1)
+    u = np.linspace(0, 1, 50)
+    segment = np.stack([0.3 + 2 * u, -0.2 + 1.5 * u], -1)
+    out, pair, var = O.normalize_maxline(np.stack([circle, ellipse, segment[np.arange(200) % 50]]))
+    # circle: diameter 1 centred in the box, every point 0.5 from the centre
+    assert abs(out[0, :, 0].min()) < 1e-12 and abs(out[0, :, 0].max() - 1) < 1e-12
+    assert np.abs(np.hypot(out[0, :, 0] - 0.5, out[0, :, 1] - 0.5) - 0.5).max() < 1e-3
+    assert var[0] < 1e-12
+    # ellipse 3:1: major axis horizontal with length 1, minor axis 1/3, centred
+    assert abs(np.ptp(out[1, :, 0]) - 1) < 1e-12 and abs(np.ptp(out[1, :, 1]) - 1 / 3) < 1e-3
+    assert abs(out[1, :, 1].min() + out[1, :, 1].max() - 1) < 1e-12
+    assert var[1] > 5e-4  # not a circle by the paper's threshold
+    # segment: horizontal, length 1, at mid-height; its ends are the pair, in index order
+    assert np.abs(out[2, :, 1] - 0.5).max() < 1e-12 and abs(out[2, :, 0].min()) < 1e-12
+    assert tuple(pair[2]) == (0, 49) and out[2, 0, 0] < out[2, 49, 0]
+
+
+def test_maxline_pair_is_the_farthest_pair(oracle_lib):
+    O = oracle_lib
+    from scipy.spatial.distance import pdist, squareform
+    rng = np.random.default_rng(4)
+    curves = rng.normal(size=(20, 60, 2))
+    out, pair, _ = O.normalize_maxline(curves)
+    for m in range(20):
+        D = squareform(pdist(curves[m]))
+        a, b = pair[m]
+        assert a < b and abs(D[a, b] - D.max()) <= 1e-12 * D.max()
+        # the pair becomes a horizontal line of length 1 from a to b; the box is centred
+        assert abs(out[m, b, 0] - out[m, a, 0] - 1) < 1e-12 and abs(out[m, b, 1] - out[m, a, 1]) < 1e-12
+        lo, hi = out[m].min(0), out[m].max(0)
+        assert np.abs((lo + hi) / 2 - 0.5).max() < 1e-12
+        assert np.abs(squareform(pdist(out[m])) - D / D.max()).max() < 1e-12  # a similarity
+
+
+def test_maxline_similarity_invariance_and_mirror(oracle_lib):
+    O = oracle_lib
+    rng = np.random.default_rng(5)
+    c = rng.normal(size=(80, 2))
+    ref, pr, vr = O.normalize_maxline(c[None])
+    for seed in range(5):
+        out, pair, var = O.normalize_maxline(_similar(c, seed)[None])
+        assert np.array_equal(pair, pr)
+        assert np.abs(out - ref).max() < 1e-9 and abs(var[0] - vr[0]) < 1e-12
+    mir = c * np.array([-1.0, 1.0])
+    out, pair, _ = O.normalize_maxline(mir[None])
+    assert np.array_equal(pair, pr)
+    assert np.abs(out[0, :, 0] - ref[0, :, 0]).max() < 1e-9
+    assert np.abs(out[0, :, 1] - (1 - ref[0, :, 1])).max() < 1e-9
+
+
+def test_maxline_degenerate_and_imposed_pair(oracle_lib):
+    O = oracle_lib
+    same = np.full((1, 30, 2), 0.7)
+    out, _, var = O.normalize_maxline(same)
+    assert np.all(out == 0.5) and var[0] == 0
+    rng = np.random.default_rng(6)
+    c = rng.normal(size=(3, 40, 2))
+    out, pair, var = O.normalize_maxline(c)
+    out2, pair2, var2 = O.normalize_maxline(c, pairs=pair)
+    assert np.array_equal(out, out2) and np.array_equal(pair, pair2) and np.array_equal(var, var2)
