@@ -199,6 +199,18 @@ LINKS_API int links_emit_census(links_ctx ctx, links_plan plan, int T, int out_m
  * 1 <= T <= 1024.  Asynchronous. */
 LINKS_API int links_normalize(links_ctx ctx, int64_t M, int T, const float* curves, float* out);
 
+/* The paper's own path normalisation (Sec. "Dataset Curation & Processing"): the two
+ * points of a curve farthest apart, (a, b) with a < b (the first such pair in (a, b)
+ * order on ties, in float32), become a horizontal line of length 1 from a to b, and the
+ * curve's bounding box is centred at (0.5, 0.5); a curve of equal points becomes
+ * (0.5, 0.5).  M curves of T points (device float32 [M,T,2] in, [M,T,2] out, not
+ * aliased; 1 <= T <= 256).  pair [M,2] int32 (device, may be NULL) receives (a, b);
+ * circ_var [M] float32 (device, may be NULL) the variance of the normalised points'
+ * distances from (0.5, 0.5), which the paper's curation compares with 5e-4 to find
+ * circles.  Asynchronous.  LINKS_EINVAL for bad arguments. */
+LINKS_API int links_normalize_maxline(links_ctx ctx, int64_t M, int T, const float* curves, float* out,
+                                      int32_t* pair, float* circ_var);
+
 /* Bidirectional chamfer retrieval (Sec. "A Case Study of Mechanism Retrieval"):
  * CD(P, C) = mean over p in P of min_c |p - c| + mean over c in C of min_p |c - p|
  * (Euclidean), for Q query curves against M database curves of T points each

@@ -422,6 +422,16 @@ int links_normalize(links_ctx ctx, int64_t M, int T, const float* curves, float*
   return normalize_paths(ctx, M, T, curves, out);
 }
 
+int links_normalize_maxline(links_ctx ctx, int64_t M, int T, const float* curves, float* out, int32_t* pair,
+                            float* circ_var) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_normalize_maxline: NULL ctx");
+  if (M < 0 || T < 1 || T > 256) return set_error(LINKS_EINVAL, "links_normalize_maxline: need M >= 0 and 1 <= T <= 256");
+  if (M > 0 && (!curves || !out)) return set_error(LINKS_EINVAL, "links_normalize_maxline: NULL pointer");
+  if (M > 0 && curves == out) return set_error(LINKS_EINVAL, "links_normalize_maxline: out must not alias curves");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  return normalize_maxline(ctx, M, T, curves, out, pair, circ_var);
+}
+
 int links_workspace_reserve(links_ctx ctx, size_t bytes) {
   if (!ctx) return set_error(LINKS_EINVAL, "links_workspace_reserve: NULL ctx");
   LINKS_CUDA(cudaSetDevice(ctx->device));

@@ -158,6 +158,8 @@ int cuda_status(cudaError_t e, const char* what);
 const TTable* get_table(links_ctx ctx, int T, int* status);
 int ensure_workspace(links_ctx ctx, size_t bytes);
 int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out);
+int normalize_maxline(links_ctx ctx, int64_t M, int T, const float* in, float* out, int32_t* pair,
+                      float* circ_var);
 // Same, for the first *M_dev of at most M_cap curves (count read on the device).
 int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, int T, const float* in, float* out);
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,

@@ -114,6 +114,127 @@ __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const 
   }
 }
 
+// The paper's path normalisation (Sec. "Dataset Curation & Processing"): the farthest
+// pair of points (a, b), a < b, becomes a horizontal line of length 1 from a to b and
+// the bounding box is centred at (0.5, 0.5); circ_var is the variance of the points'
+// distances from (0.5, 0.5) (the paper's circle test).  One warp per curve: lane l holds
+// points l + 32 i; every lane compares its points with every later point broadcast in
+// turn (T^2 / 64 distances per lane), and the warp reduces the largest squared
+// distance, ties to the first pair in (a, b) order.
+template <int PL>
+__global__ void __launch_bounds__(256) maxline_kernel(int64_t M, int T, const float2* __restrict__ in,
+                                                      float2* __restrict__ out, int32_t* __restrict__ pair,
+                                                      float* __restrict__ circ_var) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float invT = 1.0f / (float)T;
+  for (int64_t m = w0; m < M; m += nw) {
+    const float2* src = in + m * T;
+    float2 p[PL];
+#pragma unroll
+    for (int i = 0; i < PL; ++i) {
+      const int t = lane + 32 * i;
+      p[i] = t < T ? src[t] : make_float2(0.f, 0.f);
+    }
+    // farthest pair: (d2, a, b) largest d2, then smallest a, then smallest b
+    float best = -1.0f;
+    int ba = 0, bb = T > 1 ? 1 : 0;
+#pragma unroll
+    for (int j = 0; j < PL; ++j) {
+      for (int vl = 0; vl < 32; ++vl) {
+        const int v = 32 * j + vl;
+        const float vx = __shfl_sync(kFull, p[j].x, vl), vy = __shfl_sync(kFull, p[j].y, vl);
+        if (v >= T) continue;  // uniform in the warp
+#pragma unroll
+        for (int i = 0; i < PL; ++i) {
+          const int u = lane + 32 * i;
+          const float dx = vx - p[i].x, dy = vy - p[i].y;
+          const float d2 = fmaf(dx, dx, dy * dy);
+          if (u < v && (d2 > best || (d2 == best && (u < ba || (u == ba && v < bb))))) {
+            best = d2;
+            ba = u;
+            bb = v;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      const float ob = __shfl_xor_sync(kFull, best, o);
+      const int oa = __shfl_xor_sync(kFull, ba, o), obb = __shfl_xor_sync(kFull, bb, o);
+      if (ob > best || (ob == best && (oa < ba || (oa == ba && obb < bb)))) {
+        best = ob;
+        ba = oa;
+        bb = obb;
+      }
+    }
+    float2 pa = p[0], pb = p[0];  // the pair's points, selected without indexing the array
+#pragma unroll
+    for (int i = 1; i < PL; ++i) {
+      if (i == (ba >> 5)) pa = p[i];
+      if (i == (bb >> 5)) pb = p[i];
+    }
+    const float ax = __shfl_sync(kFull, pa.x, ba & 31), ay = __shfl_sync(kFull, pa.y, ba & 31);
+    const float bx = __shfl_sync(kFull, pb.x, bb & 31), by = __shfl_sync(kFull, pb.y, bb & 31);
+    const float dx = bx - ax, dy = by - ay;
+    const float d = sqrtf(fmaf(dx, dx, dy * dy));
+    float2* dst = out + m * T;
+    if (!(d > 0.0f)) {  // equal points: the centre of the box
+#pragma unroll
+      for (int i = 0; i < PL; ++i)
+        if (lane + 32 * i < T) dst[lane + 32 * i] = make_float2(0.5f, 0.5f);
+      if (lane == 0) {
+        if (pair) pair[2 * m] = ba, pair[2 * m + 1] = bb;
+        if (circ_var) circ_var[m] = 0.0f;
+      }
+      continue;
+    }
+    const float c = dx / d, s = dy / d, inv = 1.0f / d;
+    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+#pragma unroll
+    for (int i = 0; i < PL; ++i) {
+      const float x = p[i].x - ax, y = p[i].y - ay;
+      p[i] = make_float2(fmaf(c, x, s * y) * inv, fmaf(c, y, -s * x) * inv);
+      if (lane + 32 * i < T) {
+        x0 = fminf(x0, p[i].x);
+        x1 = fmaxf(x1, p[i].x);
+        y0 = fminf(y0, p[i].y);
+        y1 = fmaxf(y1, p[i].y);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
+      x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
+      y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
+      y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
+    }
+    const float sx = 0.5f - 0.5f * (x0 + x1), sy = 0.5f - 0.5f * (y0 + y1);
+    float r[PL], rs = 0.f;
+#pragma unroll
+    for (int i = 0; i < PL; ++i) {
+      p[i].x += sx;
+      p[i].y += sy;
+      r[i] = hypotf(p[i].x - 0.5f, p[i].y - 0.5f);
+      if (lane + 32 * i < T) {
+        dst[lane + 32 * i] = p[i];
+        rs += r[i];
+      }
+    }
+    const float mean = warp_sum(rs) * invT;
+    float v = 0.f;
+#pragma unroll
+    for (int i = 0; i < PL; ++i)
+      if (lane + 32 * i < T) v = fmaf(r[i] - mean, r[i] - mean, v);
+    v = warp_sum(v) * invT;
+    if (lane == 0) {
+      if (pair) pair[2 * m] = ba, pair[2 * m + 1] = bb;
+      if (circ_var) circ_var[m] = v;
+    }
+  }
+}
+
 // ------------------------------------------------------------------------- chamfer
 
 constexpr int kStage = 32;   // database curves per shared-memory stage
@@ -626,6 +747,19 @@ static int normalize_launch(links_ctx ctx, int64_t M, const int32_t* M_dev, int 
   if (T <= 64) normalize_kernel<2><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
   else if (T <= 256) normalize_kernel<8><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
   else normalize_kernel<32><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, M_dev);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
+int normalize_maxline(links_ctx ctx, int64_t M, int T, const float* in, float* out, int32_t* pair,
+                      float* circ_var) {
+  if (M == 0) return LINKS_OK;
+  const unsigned grid = (unsigned)std::min<int64_t>((M + 7) / 8, (int64_t)ctx->num_sms * 8);
+  KernelScope ks(ctx, "normalize_maxline");
+  const float2* i2 = reinterpret_cast<const float2*>(in);
+  float2* o2 = reinterpret_cast<float2*>(out);
+  if (T <= 64) maxline_kernel<2><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, pair, circ_var);
+  else maxline_kernel<8><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, pair, circ_var);
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
 }

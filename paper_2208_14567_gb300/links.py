@@ -71,6 +71,7 @@ def lib():
             "links_emit_census": ([P, P, i32, i32, P, P, i64, P], i32),
             "links_simulate_two_stage": ([P, P, i32, i32, P, P, P, P, P, P, i64, P, P], i32),
             "links_normalize": ([P, i64, i32, P, P], i32),
+            "links_normalize_maxline": ([P, i64, i32, P, P, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
             "links_serve_start": ([P, ctypes.c_size_t, i32, i32, i32, i32], i32),
@@ -264,6 +265,15 @@ def links_normalize(ctx, curves, out):
     M, T = curves.shape[0], curves.shape[1]
     _check(lib().links_normalize(ctx, int(M), int(T), _dev(curves, torch.float32, "curves"),
                                  _dev(out, torch.float32, "out")), "links_normalize")
+
+
+def links_normalize_maxline(ctx, curves, out, pair=None, circ_var=None):
+    """curves, out: float32 CUDA tensors [M, T, 2]; pair int32 [M, 2] and circ_var float32 [M] optional."""
+    import torch
+    M, T = curves.shape[0], curves.shape[1]
+    _check(lib().links_normalize_maxline(ctx, int(M), int(T), _dev(curves, torch.float32, "curves"),
+                                         _dev(out, torch.float32, "out"), _dev(pair, torch.int32, "pair"),
+                                         _dev(circ_var, torch.float32, "circ_var")), "links_normalize_maxline")
 
 
 def links_chamfer_topk(ctx, queries, db, k: int, idx, dist):

@@ -186,3 +186,41 @@ def test_chamfer_pruning_changes_nothing(L, ctx, T, M, Q, k):
     sel = np.random.default_rng(T).choice(len(q), 6, replace=False)
     check_topk(q[sel], db, idx1[sel], dist1[sel], k, f"pruned T={T} M={len(db)}")
     assert L.lib().links_set_chamfer_prune(ctx, 2) == L.EINVAL
+
+
+@pytest.mark.parametrize("T", [200, 7, 33, 256])
+def test_normalize_maxline_matches_oracle(L, ctx, T):
+    """The paper's normalisation: the pair the kernel finds (float32) is a farthest pair up
+    to float rounding, and with that pair imposed the oracle's normalised curve and
+    circle statistic match."""
+    base = coupler_curves(300, T, seed=50 + T)
+    curves = transformed(base, seed=T).astype(np.float32)
+    s = np.linspace(0, 2 * np.pi, T, endpoint=False)
+    special = np.stack([
+        np.stack([np.cos(s), np.sin(s)], -1) * 2 + 1,                        # circle
+        np.stack([0.3 + 2 * np.linspace(0, 1, T), -0.2 + np.linspace(0, 1, T)], -1),  # segment
+        np.full((T, 2), 0.25),                                               # one point
+    ]).astype(np.float32)
+    curves = np.concatenate([curves, special])
+    x = torch.from_numpy(curves).cuda()
+    y = torch.empty_like(x)
+    pair = torch.empty((len(curves), 2), dtype=torch.int32, device="cuda")
+    var = torch.empty(len(curves), dtype=torch.float32, device="cuda")
+    L.links_normalize_maxline(ctx, x, y, pair, var)
+    torch.cuda.synchronize()
+    out, pr, vr = y.cpu().numpy(), pair.cpu().numpy(), var.cpu().numpy()
+    c64 = curves.astype(np.float64)
+    _, opair, _ = O.normalize_maxline(c64)
+    ref, _, rvar = O.normalize_maxline(c64, pairs=pr)
+    dist = lambda c, pq: np.hypot(*(c[pq[1]] - c[pq[0]]))
+    for m in range(len(curves) - 1):
+        assert pr[m, 0] < pr[m, 1] and dist(c64[m], pr[m]) >= dist(c64[m], opair[m]) * (1 - 1e-5)
+    err = np.abs(out - ref).max()
+    print(f"[T={T}] curves {len(curves)} same pair as the oracle {np.mean((pr == opair).all(1)):.3f} "
+          f"max |gpu - oracle| {err:.2e} max |var - oracle| {np.abs(vr - rvar).max():.2e}")
+    assert err <= 2e-5 and np.abs(vr - rvar).max() <= 2e-6
+    assert (out[-1] == 0.5).all()
+    if T % 2 == 0:  # antipodal points: a circle of diameter 1 about the box centre
+        assert vr[-3] < 1e-6
+    with pytest.raises(L.LinksError):
+        L.links_normalize_maxline(ctx, x, x)
