@@ -228,3 +228,24 @@ def chamfer_topk(queries: np.ndarray, db: np.ndarray, k: int, threads: int | Non
         d = chamfer_many(queries[qi], db, threads)
         idx[qi], dist[qi] = topk(d, k)
     return idx, dist
+
+
+def first_under(dist: np.ndarray, rank: np.ndarray, threshold: float, k: int):
+    """The paper's retrieval (Sec. "A Case Study of Mechanism Retrieval"): going through
+    the database in the order given by ``rank`` (rank[i] = position of curve i in the
+    scan), the first k curves whose distance is below the threshold.
+    -> (indices [<= k] in scan order, their distances)."""
+    hits = np.nonzero(dist < threshold)[0]
+    hits = hits[np.argsort(rank[hits], kind="stable")][:k]
+    return hits.astype(np.int64), dist[hits]
+
+
+def chamfer_first_under(queries: np.ndarray, db: np.ndarray, rank: np.ndarray, threshold: float, k: int,
+                        threads: int | None = None):
+    """first_under of each query's chamfer distances; -1 / inf past the hits found."""
+    idx = np.full((queries.shape[0], k), -1, np.int64)
+    dist = np.full((queries.shape[0], k), np.inf)
+    for qi in range(queries.shape[0]):
+        i, d = first_under(chamfer_many(queries[qi], db, threads), rank, threshold, k)
+        idx[qi, :len(i)], dist[qi, :len(i)] = i, d
+    return idx, dist

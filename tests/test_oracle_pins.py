@@ -501,3 +501,25 @@ def test_maxline_degenerate_and_imposed_pair(oracle_lib):
     out, pair, var = O.normalize_maxline(c)
     out2, pair2, var2 = O.normalize_maxline(c, pairs=pair)
     assert np.array_equal(out, out2) and np.array_equal(pair, pair2) and np.array_equal(var, var2)
+
+
+def test_first_under_scan_order(oracle_lib):
+    """The paper's retrieval: the first k curves below the threshold in scan order. A copy
+    of the query placed first in the scan is returned first at distance 0; a threshold
+    above every distance returns the first k curves of the scan whatever their
+    distances; one below every distance returns none."""
+    O = oracle_lib
+    rng = np.random.default_rng(8)
+    s = np.linspace(0, 2 * np.pi, 40, endpoint=False)
+    db = np.stack([np.stack([np.cos(s) * a, np.sin(s)], -1) for a in rng.uniform(0.5, 2, 30)])
+    q = db[17].copy()
+    rank = rng.permutation(30)
+    rank[[17, int(np.argmin(rank))]] = rank[[int(np.argmin(rank)), 17]]  # curve 17 is scanned first
+    idx, dist = O.chamfer_first_under(q[None], db, rank, 0.3, 3)
+    assert idx[0, 0] == 17 and dist[0, 0] == 0.0
+    d = O.chamfer_many(q, db)
+    assert np.all(d[idx[0][idx[0] >= 0]] < 0.3)
+    idx, _ = O.chamfer_first_under(q[None], db, rank, 1e9, 5)
+    assert np.array_equal(idx[0], np.argsort(rank)[:5])
+    idx, dist = O.chamfer_first_under(q[None], db, rank, 0.0, 3)
+    assert np.all(idx == -1) and np.all(np.isinf(dist))
