@@ -222,7 +222,50 @@ def path_stage(args, local, stream):
         pairs = Q * M * T * T
         hbm = peaks()["hbm_gbs"]
         nbytes = 2 * M * T * 8
+        # the paper's retrieval: max-distance-line normalisation, the database read in a
+        # shuffled order until 3 curves lie under the cut-off 0.03 (queries: paths of other
+        # mechanisms, not in the database)
+        ml = torch.empty_like(db)
+        cv = torch.empty(M, dtype=torch.float32, device=dev)
+        L.links_normalize_maxline(ctx, db, ml, None, cv)  # warm-up
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for _ in range(reps):
+            L.links_normalize_maxline(ctx, db, ml, None, cv)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        mlms = e0.elapsed_time(e1) / reps
+        qraw = torch.from_numpy(held).to(dev)
+        qm = torch.empty_like(qraw)
+        L.links_normalize_maxline(ctx, qraw, qm)
+        order = torch.randperm(M, generator=torch.Generator().manual_seed(779)).to(torch.int32).to(dev)
+        fidx = torch.empty((Q, 3), dtype=torch.int32, device=dev)
+        fdist = torch.empty((Q, 3), dtype=torch.float32, device=dev)
+        L.links_chamfer_first_under(ctx, qm[:8], ml, order, 0.03, 3, fidx[:8], fdist[:8])  # warm-up
+        L.links_sync(ctx)
+        e0.record(stream)
+        L.links_chamfer_first_under(ctx, qm, ml, order, 0.03, 3, fidx, fdist)
+        e1.record(stream)
+        L.links_sync(ctx)
+        fms = e0.elapsed_time(e1)
+        found = (fidx >= 0).sum(1).cpu()
+        # the same scan without the chamfer lower bounds (the position cut-off stays)
+        L.links_set_chamfer_prune(ctx, False)
+        e0.record(stream)
+        L.links_chamfer_first_under(ctx, qm[:Qx], ml, order, 0.03, 3, fidx[:Qx], fdist[:Qx])
+        e1.record(stream)
+        L.links_sync(ctx)
+        L.links_set_chamfer_prune(ctx, True)
+        fxms = e0.elapsed_time(e1) * Q / Qx
         return {
+            "normalize_maxline": {"curves": M, "T": T, "ms": mlms, "curves_per_s": M / (mlms * 1e-3),
+                                  "GB_per_s": nbytes / (mlms * 1e-3) / 1e9,
+                                  "hbm_frac": nbytes / (mlms * 1e-3) / 1e9 / hbm,
+                                  "circles_under_5e-4": int((cv < 5e-4).sum().item())},
+            "first_under": {"queries": Q, "database": M, "T": T, "k": 3, "threshold": 0.03, "ms": fms,
+                            "queries_per_s": Q / (fms * 1e-3), "no_bounds_ms": fxms,
+                            "queries_with_3": int((found == 3).sum().item()),
+                            "queries_with_none": int((found == 0).sum().item())},
             "normalize": {"curves": M, "T": T, "ms": nms, "curves_per_s": M / (nms * 1e-3),
                           "GB_per_s": nbytes / (nms * 1e-3) / 1e9, "hbm_frac": nbytes / (nms * 1e-3) / 1e9 / hbm},
             "chamfer_topk": {"queries": Q, "database": M, "T": T, "k": k, "ms": cms,
@@ -275,6 +318,71 @@ def paper_generator_stage(args, local, stream):
                          "ms_single": times["single"], "ms_two_stage": times["two_stage"]})
         torch.cuda.empty_cache()
     return {"topologies_per_n": K, "positions_per_topology": S, "T": T, "sweep": rows}
+
+
+def curation_stage(args, local, stream):
+    """The paper's dataset curation of every moving joint's path of the valid candidates:
+    the headline candidate mix (time per step of curation, arc / circle shares) and the
+    paper's own generator at three joint counts (shares, beside the paper's 28% arcs
+    and 34% circles)."""
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T = args.T
+    dev = torch.device("cuda", local)
+    ctx = L.links_create(local, stream)
+    res = {}
+    try:
+        for name, batch in (("dyad_6-8", I.dyad_batch(args.batch, 6, 8, seed=0)),
+                            ("paper_n6", I.paper_batch(256, 1024, 6, seed=6)),
+                            ("paper_n10", I.paper_batch(256, 1024, 10, seed=10)),
+                            ("paper_n15", I.paper_batch(256, 1024, 15, seed=15))):
+            db = to_device(batch, dev)
+            with Simulator(batch.B, batch.nmax, device=local, stream=stream) as s:
+                s.build(db)
+                probe = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+                s.sync()
+                nv = int(probe.n_out[0])
+                out = s.alloc(T, L.MIXED, L.OUT_VALID_ONLY, traj=True, path=False, out_capacity=max(nv, 1))
+                s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=out)
+                s.sync()
+                traj, rows = out.traj[:nv], out.out_index[:nv]
+                nm = batch.nmax
+                flags = torch.empty((nv, nm), dtype=torch.uint8, device=dev)
+                kidx = torch.empty(nv * nm, dtype=torch.int32, device=dev)
+                kpaths = torch.empty((nv * nm, T, 2), dtype=torch.float32, device=dev)
+                nk = torch.empty(1, dtype=torch.int32, device=dev)
+                call = lambda: L.links_curate_paths(ctx, traj, rows, db.n_joints, db.adj, db.jtype, flags, nk,
+                                                    kept_index=kidx, kept_paths=kpaths)
+                call()  # warm-up (workspace)
+                torch.cuda.synchronize(dev)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(3):
+                    call()
+                e1.record(stream)
+                L.links_sync(ctx)
+                ms = e0.elapsed_time(e1) / 3
+                f = flags
+                paths = int(((f & 1) != 0).sum().item())
+                arcs = int(((f & 2) != 0).sum().item())
+                circles = int(((f & 4) != 0).sum().item())
+                either = int(((f & 6) != 0).sum().item())
+                circ_not_arc = int((((f & 4) != 0) & ((f & 2) == 0)).sum().item())
+                res[name] = {"candidates": batch.B, "valid": nv, "paths": paths, "ms": ms,
+                             "paths_per_s": paths / (ms * 1e-3), "arc_share": arcs / max(paths, 1),
+                             "circle_share": circles / max(paths, 1),
+                             "circle_not_arc_share": circ_not_arc / max(paths, 1),
+                             "arc_or_circle_share": either / max(paths, 1), "kept": int(nk.item())}
+                del out, probe, traj, rows, flags, kidx, kpaths
+            del db
+            torch.cuda.empty_cache()
+    finally:
+        L.links_destroy(ctx)
+    return {"T": T, "circle_var": 5e-4, "keep_rate": 0.005, "paper_shares": {"arcs": 0.28, "circles": 0.34},
+            "workloads": res}
 
 
 def serve_stage(args, local, stream):
@@ -406,6 +514,7 @@ def main():
     ap.add_argument("--no-path-stage", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-generator", action="store_true")
+    ap.add_argument("--no-curation", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=600_000)
@@ -664,6 +773,7 @@ def main():
     ps = None if args.no_path_stage or world > 1 else path_stage(args, local, stream)
     sv = None if args.no_serve or world > 1 else serve_stage(args, local, stream)
     pg = None if args.no_paper_generator or world > 1 else paper_generator_stage(args, local, stream)
+    cu = None if args.no_curation or world > 1 else curation_stage(args, local, stream)
     cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -683,6 +793,7 @@ def main():
         "path_stage": ps,
         "serve": sv,
         "paper_generator": pg,
+        "curation": cu,
         "e2e": e2e,
         "e2e_full": e2e_full,
         "gpu_launches": int(launches * args.steps),

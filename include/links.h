@@ -222,14 +222,63 @@ LINKS_API int links_normalize_maxline(links_ctx ctx, int64_t M, int T, const flo
  * links_workspace_reserve before a graph capture).  Asynchronous. */
 LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
                                  const float* db, int k, int32_t* idx, float* dist);
-/* Switches the exact pruning of links_chamfer_topk on (1, default) or off (0).  With
- * it on, the column term of each database curve's CD is first bounded from below
- * through a table of the query's distance field (DT(c) >= DT(v) - |c - v| for a grid
- * node v), and the exact computation stops once its partial column sum passes the
- * smallest k-th distance found so far for the query (in any database chunk); curves
- * ruled out either way cannot enter the top-k, so the result is the same bit for
- * bit, only the work differs.  LINKS_EINVAL
- * for a NULL ctx or a flag other than 0 or 1. */
+/* The paper's retrieval (Sec. "A Case Study of Mechanism Retrieval": the curated
+ * database is shuffled and read until three curves lie within the chamfer cut-off of
+ * the target).  For each of the Q queries, going through the database in the scan
+ * order `order` (device, L int32 entries: position r reads database curve order[r];
+ * normally a permutation of 0..M-1), the first k curves whose chamfer distance (as
+ * in links_chamfer_topk) is below `threshold`.  Outputs (device, caller-owned):
+ * idx [Q,k] int32 database curves in scan order, -1 past the hits found; dist [Q,k]
+ * float32 their distances, +inf past the hits.  A distance within FP32 rounding of
+ * the threshold is recomputed in FP64 and the decision taken on that value.  The
+ * chunks of the scan run in parallel; a chunk stops reading once every query has k
+ * hits at earlier positions, which changes only the work.  Uses the workspace as
+ * links_chamfer_topk (with up to four times as many chunks) plus Q x 4 bytes.
+ * Asynchronous.  LINKS_EINVAL for a NULL pointer, Q, M, T, k out of range
+ * (as links_chamfer_topk), L outside [0, 2^31 - 1) or a NaN threshold; an order
+ * entry outside [0, M) is skipped and raises bit 2 of the device error word
+ * (LINKS_EDEVICE from links_sync). */
+LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
+                                        const float* db, int64_t L, const int32_t* order, double threshold,
+                                        int k, int32_t* idx, float* dist);
+/* The paper's dataset curation (Sec. "Dataset Curation & Processing").  For every
+ * joint j of every row r of traj [R, n_max, T, 2] float32 (device; the layout of
+ * links_simulate's trajectories, row r belonging to mechanism row_index[r], or to
+ * mechanism r when row_index is NULL), given the mechanisms' n_joints [B] int32,
+ * adj [B, n_max, n_max] uint8 and type [B, n_max] int8 (device; the layout of
+ * links_plan_build):
+ *   a joint below n_joints that is not fixed has a path; its path is normalised as
+ *   links_normalize_maxline does; it is an arc if the joint is linked to a fixed
+ *   joint and a circle if its circle statistic is below circle_var (the paper uses
+ *   5e-4); a path that is neither is kept, and an arc or a circle is kept when
+ *   draw(b * n_max + j) < keep_rate (the paper keeps 0.5%), where draw(i) is output
+ *   i (from 0) of splitmix64 started at `seed`, as (z >> 11) * 2^-53.
+ * Outputs (device, caller-owned): flags [R, n_max] uint8 (bit 0 path, bit 1 arc,
+ * bit 2 circle, bit 3 kept); circ_var [R, n_max] float32 and pair [R, n_max, 2]
+ * int32 (the normalising pair) may be NULL; kept_index [kept_capacity] int32 the
+ * entries r * n_max + j of the kept paths in increasing order, *n_kept (device)
+ * their count (entries past kept_capacity are dropped); kept_paths
+ * [kept_capacity, T, 2] float32 (may be NULL) their normalised paths.  Uses the
+ * workspace (R x n_max x 8 bytes when pair is NULL, plus R x n_max / 256 bytes).
+ * Asynchronous.  LINKS_EINVAL for a NULL pointer, R, B or kept_capacity negative,
+ * n_max outside [1, 64], T outside [1, 256], R x n_max >= 2^31 or a NaN
+ * threshold; a row index outside [0, B) gives that row no paths and raises bit 2
+ * of the device error word (LINKS_EDEVICE from links_sync). */
+LINKS_API int links_curate_paths(links_ctx ctx, int64_t R, int n_max, int T, const float* traj,
+                                 const int32_t* row_index, int64_t B, const int32_t* n_joints,
+                                 const uint8_t* adj, const int8_t* type, double circle_var, double keep_rate,
+                                 uint64_t seed, uint8_t* flags, float* circ_var, int32_t* pair,
+                                 int32_t* kept_index, float* kept_paths, int64_t kept_capacity,
+                                 int32_t* n_kept);
+/* Switches the exact pruning of links_chamfer_topk and links_chamfer_first_under on
+ * (1, default) or off (0).  With it on, the column term of each database curve's CD
+ * is first bounded from below through a table of the query's distance field
+ * (DT(c) >= DT(v) - |c - v| for a grid node v), and the exact computation stops once
+ * its partial column sum passes the pruning distance: the smallest k-th distance
+ * found so far for the query (in any database chunk) for the top-k, the threshold
+ * for the first-k scan.  Curves ruled out either way cannot enter the result, so it
+ * is the same bit for bit, only the work differs.  LINKS_EINVAL for a NULL ctx or a
+ * flag other than 0 or 1. */
 LINKS_API int links_set_chamfer_prune(links_ctx ctx, int on);
 /* Makes the context's workspace at least `bytes` large (allocates; not inside a
  * capture). */

@@ -197,6 +197,52 @@ def normalize_maxline(curves: np.ndarray, pairs: np.ndarray | None = None):
     return out, pair, var
 
 
+def splitmix64(seed: int, idx: np.ndarray) -> np.ndarray:
+    """Output idx (from 0) of splitmix64 started at ``seed`` (Steele, Lea and Flood,
+    OOPSLA 2014, with Vigna's published constants), as uint64."""
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (np.asarray(idx, dtype=np.uint64) + np.uint64(1)) \
+            * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+def curate_paths(traj: np.ndarray, row_index, batch, circle_var: float = 5e-4, keep_rate: float = 0.005,
+                 seed: int = 0, pairs: np.ndarray | None = None):
+    """The paper's dataset curation (Sec. "Dataset Curation & Processing") of the joint
+    paths traj [R, n_max, T, 2] (row r of mechanism row_index[r], or r if None): every
+    moving joint's path is normalised (normalize_maxline); it is an arc when the joint is
+    linked to a fixed joint, a circle when its circle variance is below circle_var; arcs
+    and circles are kept only when the keep draw of (b, j), output b * n_max + j of
+    splitmix64(seed) as a double in [0, 1), is below keep_rate.  ``pairs`` [R, n_max, 2]
+    imposes the normalising pairs.
+    -> dict(flags [R, n_max] uint8: 1 path, 2 arc, 4 circle, 8 kept; circ_var [R, n_max];
+            pair [R, n_max, 2]; kept_index (r * n_max + j, increasing); kept_paths)."""
+    R, n_max, T = traj.shape[0], traj.shape[1], traj.shape[2]
+    rows = np.arange(R) if row_index is None else np.asarray(row_index, dtype=np.int64)
+    flags = np.zeros((R, n_max), np.uint8)
+    cv = np.zeros((R, n_max))
+    pair = np.zeros((R, n_max, 2), np.int32)
+    normed = np.zeros((R, n_max, T, 2))
+    for r in range(R):
+        b = int(rows[r])
+        n = int(batch.n_joints[b])
+        for j in range(n):
+            if batch.jtype[b, j] == 0:
+                continue  # a fixed joint does not move
+            out, pr, var = normalize_maxline(traj[r, j][None], None if pairs is None else pairs[r, j][None])
+            normed[r, j], pair[r, j], cv[r, j] = out[0], pr[0], var[0]
+            arc = any(batch.adj[b, j, k] and batch.jtype[b, k] == 0 for k in range(n))
+            circle = var[0] < circle_var
+            u = float(splitmix64(seed, np.uint64(b * n_max + j)) >> np.uint64(11)) * 2.0 ** -53
+            kept = not (arc or circle) or u < keep_rate
+            flags[r, j] = 1 | (2 if arc else 0) | (4 if circle else 0) | (8 if kept else 0)
+    kept_index = np.nonzero((flags.reshape(-1) & 8) != 0)[0]
+    return dict(flags=flags, circ_var=cv, pair=pair, kept_index=kept_index,
+                kept_paths=normed.reshape(R * n_max, T, 2)[kept_index])
+
+
 def chamfer(p: np.ndarray, q: np.ndarray) -> float:
     p = np.ascontiguousarray(p, dtype=np.float64)
     q = np.ascontiguousarray(q, dtype=np.float64)
@@ -230,22 +276,21 @@ def chamfer_topk(queries: np.ndarray, db: np.ndarray, k: int, threads: int | Non
     return idx, dist
 
 
-def first_under(dist: np.ndarray, rank: np.ndarray, threshold: float, k: int):
+def first_under(dist: np.ndarray, order: np.ndarray, threshold: float, k: int):
     """The paper's retrieval (Sec. "A Case Study of Mechanism Retrieval"): going through
-    the database in the order given by ``rank`` (rank[i] = position of curve i in the
-    scan), the first k curves whose distance is below the threshold.
+    the database in the shuffled order ``order`` (order[r] = the curve looked at r-th),
+    the first k curves whose distance is below the threshold.
     -> (indices [<= k] in scan order, their distances)."""
-    hits = np.nonzero(dist < threshold)[0]
-    hits = hits[np.argsort(rank[hits], kind="stable")][:k]
+    hits = order[dist[order] < threshold][:k]
     return hits.astype(np.int64), dist[hits]
 
 
-def chamfer_first_under(queries: np.ndarray, db: np.ndarray, rank: np.ndarray, threshold: float, k: int,
+def chamfer_first_under(queries: np.ndarray, db: np.ndarray, order: np.ndarray, threshold: float, k: int,
                         threads: int | None = None):
     """first_under of each query's chamfer distances; -1 / inf past the hits found."""
     idx = np.full((queries.shape[0], k), -1, np.int64)
     dist = np.full((queries.shape[0], k), np.inf)
     for qi in range(queries.shape[0]):
-        i, d = first_under(chamfer_many(queries[qi], db, threads), rank, threshold, k)
+        i, d = first_under(chamfer_many(queries[qi], db, threads), order, threshold, k)
         idx[qi, :len(i)], dist[qi, :len(i)] = i, d
     return idx, dist

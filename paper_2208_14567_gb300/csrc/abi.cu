@@ -508,6 +508,38 @@ int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes) {
   return autotune_screen(ctx, plan, tab, lanes);
 }
 
+int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* queries, const float* db,
+                              int64_t L, const int32_t* order, double threshold, int k, int32_t* idx,
+                              float* dist) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_chamfer_first_under: NULL ctx");
+  if (Q < 0 || M < 0 || M > INT32_MAX || L < 0 || L >= INT32_MAX)
+    return set_error(LINKS_EINVAL, "links_chamfer_first_under: Q, M or L out of range");
+  if (T < 1 || T > 256) return set_error(LINKS_EINVAL, "links_chamfer_first_under: T must be in [1, 256]");
+  if (k < 1 || k > 32) return set_error(LINKS_EINVAL, "links_chamfer_first_under: k must be in [1, 32]");
+  if (threshold != threshold) return set_error(LINKS_EINVAL, "links_chamfer_first_under: threshold is NaN");
+  if (Q > 0 && (!queries || !idx || !dist || (L > 0 && (!order || !db))))
+    return set_error(LINKS_EINVAL, "links_chamfer_first_under: NULL pointer");
+  return chamfer_first_under(ctx, Q, M, T, queries, db, L, order, threshold, k, idx, dist, ctx->chamfer_prune);
+}
+
+int links_curate_paths(links_ctx ctx, int64_t R, int n_max, int T, const float* traj, const int32_t* row_index,
+                       int64_t B, const int32_t* n_joints, const uint8_t* adj, const int8_t* type,
+                       double circle_var, double keep_rate, uint64_t seed, uint8_t* flags, float* circ_var,
+                       int32_t* pair, int32_t* kept_index, float* kept_paths, int64_t kept_capacity,
+                       int32_t* n_kept) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_curate_paths: NULL ctx");
+  if (R < 0 || B < 0 || kept_capacity < 0) return set_error(LINKS_EINVAL, "links_curate_paths: negative size");
+  if (n_max < 1 || n_max > 64) return set_error(LINKS_EINVAL, "links_curate_paths: n_max must be in [1, 64]");
+  if (T < 1 || T > 256) return set_error(LINKS_EINVAL, "links_curate_paths: T must be in [1, 256]");
+  if (R * n_max > INT32_MAX) return set_error(LINKS_EINVAL, "links_curate_paths: R x n_max exceeds 2^31 - 1");
+  if (circle_var != circle_var || keep_rate != keep_rate)
+    return set_error(LINKS_EINVAL, "links_curate_paths: NaN threshold or keep rate");
+  if (!n_kept || (R > 0 && (!traj || !n_joints || !adj || !type || !flags)) || (kept_capacity > 0 && !kept_index))
+    return set_error(LINKS_EINVAL, "links_curate_paths: NULL pointer");
+  return curate_paths(ctx, R, n_max, T, traj, row_index, B, n_joints, adj, type, circle_var, keep_rate, seed, flags,
+                      circ_var, pair, kept_index, kept_paths, kept_capacity, n_kept);
+}
+
 int links_set_chamfer_prune(links_ctx ctx, int on) {
   if (!ctx) return set_error(LINKS_EINVAL, "links_set_chamfer_prune: NULL ctx");
   if (on != 0 && on != 1) return set_error(LINKS_EINVAL, "links_set_chamfer_prune: flag must be 0 or 1");

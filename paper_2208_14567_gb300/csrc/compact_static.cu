@@ -1,5 +1,6 @@
 // compact_static.cu -- valid-row compaction whose scratch lives in static device memory,
-// for callers that cannot allocate device memory.
+// for callers that cannot allocate device memory; its scan also serves other
+// flag compactions (compact_flags) with caller-provided scratch.
 //
 // Some callers cannot call cudaMalloc: code that runs while another framework owns the
 // device memory pool (an embedding host that forbids foreign allocations), callers
@@ -55,9 +56,11 @@ __device__ int static_block_scan(int v, int* total) {
   return excl;
 }
 
-__global__ void __launch_bounds__(kBlockRows) static_scan_count(int64_t B, const uint8_t* valid, int32_t* sums) {
+// Entry b counts when valid[b] & mask is nonzero.
+__global__ void __launch_bounds__(kBlockRows) static_scan_count(int64_t B, const uint8_t* valid, uint8_t mask,
+                                                                int32_t* sums) {
   int64_t b = (int64_t)blockIdx.x * kBlockRows + threadIdx.x;
-  int v = (b < B && valid[b]) ? 1 : 0;
+  int v = (b < B && (valid[b] & mask)) ? 1 : 0;
   int tot;
   static_block_scan(v, &tot);
   if (threadIdx.x == 0) sums[blockIdx.x] = tot;
@@ -78,10 +81,10 @@ __global__ void __launch_bounds__(kBlockRows) static_scan_top(int nblk, int32_t*
   if (threadIdx.x == 0 && n_out) *n_out = carry;
 }
 
-__global__ void __launch_bounds__(kBlockRows) static_scan_write(int64_t B, const uint8_t* valid, const int32_t* sums,
-                                                                int32_t* out_index, int64_t cap) {
+__global__ void __launch_bounds__(kBlockRows) static_scan_write(int64_t B, const uint8_t* valid, uint8_t mask,
+                                                                const int32_t* sums, int32_t* out_index, int64_t cap) {
   int64_t b = (int64_t)blockIdx.x * kBlockRows + threadIdx.x;
-  int v = (b < B && valid[b]) ? 1 : 0;
+  int v = (b < B && (valid[b] & mask)) ? 1 : 0;
   int ex = static_block_scan(v, nullptr) + sums[blockIdx.x];
   if (v && ex < cap && out_index) out_index[ex] = (int32_t)b;
 }
@@ -103,6 +106,21 @@ int static_sums(int32_t** out) {
 }
 
 }  // namespace
+
+int64_t compact_sums_count(int64_t n) { return (n + kBlockRows - 1) / kBlockRows; }
+
+int compact_flags(cudaStream_t s, const uint8_t* flags, uint8_t mask, int64_t n, int32_t* sums, int32_t* out_index,
+                  int64_t cap, int32_t* n_out) {
+  const int nblk = (int)compact_sums_count(n);
+  if (nblk > 0) static_scan_count<<<nblk, kBlockRows, 0, s>>>(n, flags, mask, sums);
+  LINKS_CUDA(cudaGetLastError());
+  static_scan_top<<<1, kBlockRows, 0, s>>>(nblk, sums, n_out);
+  LINKS_CUDA(cudaGetLastError());
+  if (nblk > 0) static_scan_write<<<nblk, kBlockRows, 0, s>>>(n, flags, mask, sums, out_index, cap);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
 }  // namespace links
 
 using namespace links;
@@ -117,13 +135,5 @@ extern "C" int links_compact_valid_static(const uint8_t* valid, int64_t B, int32
   int32_t* sums = nullptr;
   int st = static_sums(&sums);
   if (st) return st;
-  cudaStream_t s = (cudaStream_t)cuda_stream;
-  const int nblk = (int)((B + kBlockRows - 1) / kBlockRows);
-  if (nblk > 0) static_scan_count<<<nblk, kBlockRows, 0, s>>>(B, valid, sums);
-  LINKS_CUDA(cudaGetLastError());
-  static_scan_top<<<1, kBlockRows, 0, s>>>(nblk, sums, n_out);
-  LINKS_CUDA(cudaGetLastError());
-  if (nblk > 0) static_scan_write<<<nblk, kBlockRows, 0, s>>>(B, valid, sums, out_index, out_capacity);
-  LINKS_CUDA(cudaGetLastError());
-  return LINKS_OK;
+  return compact_flags((cudaStream_t)cuda_stream, valid, 0xff, B, sums, out_index, out_capacity, n_out);
 }

@@ -164,6 +164,18 @@ int normalize_maxline(links_ctx ctx, int64_t M, int T, const float* in, float* o
 int normalize_paths_count(links_ctx ctx, const int32_t* M_dev, int64_t M_cap, int T, const float* in, float* out);
 int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int k, int32_t* idx,
                  float* dist, int prune);
+// Indices of the n entries with flags[i] & mask != 0, in increasing order, into
+// out_index (up to cap) and their count into *n_out (device); sums holds
+// compact_sums_count(n) int32 of scratch.  Asynchronous on stream s.
+int64_t compact_sums_count(int64_t n);
+int compact_flags(cudaStream_t s, const uint8_t* flags, uint8_t mask, int64_t n, int32_t* sums, int32_t* out_index,
+                  int64_t cap, int32_t* n_out);
+int curate_paths(links_ctx ctx, int64_t R, int n_max, int T, const float* traj, const int32_t* row_index,
+                 int64_t B, const int32_t* n_joints, const uint8_t* adj, const int8_t* type, double circle_var,
+                 double keep_rate, uint64_t seed, uint8_t* flags, float* circ_var, int32_t* pair,
+                 int32_t* kept_index, float* kept_paths, int64_t kept_capacity, int32_t* n_kept);
+int chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int64_t L,
+                        const int32_t* order, double thr, int k, int32_t* idx, float* dist, int prune);
 
 // Brackets one kernel launch: counts it and, while profiling, records events around it.
 struct KernelScope {

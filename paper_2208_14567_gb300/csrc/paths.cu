@@ -116,123 +116,297 @@ __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const 
 
 // The paper's path normalisation (Sec. "Dataset Curation & Processing"): the farthest
 // pair of points (a, b), a < b, becomes a horizontal line of length 1 from a to b and
-// the bounding box is centred at (0.5, 0.5); circ_var is the variance of the points'
-// distances from (0.5, 0.5) (the paper's circle test).  One warp per curve: lane l holds
-// points l + 32 i; every lane compares its points with every later point broadcast in
-// turn (T^2 / 64 distances per lane), and the warp reduces the largest squared
-// distance, ties to the first pair in (a, b) order.
+// the bounding box is centred at (0.5, 0.5); the circle statistic is the variance of
+// the points' distances from (0.5, 0.5) (the paper's circle test).  One warp per curve,
+// staged in shared memory; lane l holds points u = l + 32 i.
+
+// Loads curve src (T points) into the lane's registers and the warp's shared copy.
+template <int PL>
+__device__ __forceinline__ void load_curve(const float2* __restrict__ src, int T, int lane, float2* sp,
+                                           float2 (&p)[PL]) {
+  __syncwarp();
+#pragma unroll
+  for (int i = 0; i < PL; ++i) {
+    const int t = lane + 32 * i;
+    p[i] = t < T ? src[t] : make_float2(0.f, 0.f);
+    sp[t] = p[i];
+  }
+  __syncwarp();
+}
+
+// The farthest pair, first in (a, b) order among equal distances, in two passes:
+// (1) each lane keeps, per point u, the largest squared distance to a later point v
+// (read as a broadcast from shared memory, two u at a time in packed f32x2 arithmetic,
+// blocks with every u > v skipped), and the warp takes the maximum; (2) a is the first
+// u whose maximum equals it and b the first v > a at that distance.  Both passes
+// evaluate the same expression on the same operands, so the equality test is exact.
+// One point gives the pair (0, 0).
+template <int PL>
+__device__ __forceinline__ void farthest_pair(const float2 (&p)[PL], const float2* sp, int T, int lane, int& ba,
+                                              int& bb) {
+  static_assert(PL % 2 == 0, "points are paired for the packed arithmetic");
+  f2 UX[PL / 2], UY[PL / 2];
+  float bu[PL];  // per point u: largest squared distance to a later point (-1: none)
+#pragma unroll
+  for (int k = 0; k < PL / 2; ++k) {
+    UX[k] = pk2(p[2 * k].x, p[2 * k + 1].x);
+    UY[k] = pk2(p[2 * k].y, p[2 * k + 1].y);
+    bu[2 * k] = bu[2 * k + 1] = -1.0f;
+  }
+#pragma unroll
+  for (int j = 0; j < PL; ++j) {  // v = 32 j + vl
+    const int nv = min(32, T - 32 * j);
+    for (int vl = 0; vl < nv; ++vl) {
+      const float2 c = sp[32 * j + vl];
+      const f2 VX = pk2(c.x, c.x), VY = pk2(c.y, c.y);
+#pragma unroll
+      for (int k = 0; k < PL / 2; ++k) {
+        if (2 * k > j) continue;  // u >= 32 (j + 1) > v
+        const f2 dx = sub2(VX, UX[k]), dy = sub2(VY, UY[k]);
+        const float2 d2 = up2(fma2(dx, dx, mul2(dy, dy)));
+        if (2 * k < j) bu[2 * k] = fmaxf(bu[2 * k], d2.x);
+        else if (lane < vl) bu[2 * k] = fmaxf(bu[2 * k], d2.x);
+        if (2 * k + 1 < j) bu[2 * k + 1] = fmaxf(bu[2 * k + 1], d2.y);
+        else if (2 * k + 1 == j && lane < vl) bu[2 * k + 1] = fmaxf(bu[2 * k + 1], d2.y);
+      }
+    }
+  }
+  float best = bu[0];
+#pragma unroll
+  for (int i = 1; i < PL; ++i) best = fmaxf(best, bu[i]);
+#pragma unroll
+  for (int o = 16; o; o >>= 1) best = fmaxf(best, __shfl_xor_sync(kFull, best, o));
+  ba = INT32_MAX;
+#pragma unroll
+  for (int i = PL - 1; i >= 0; --i)
+    if (best >= 0.f && bu[i] == best) ba = lane + 32 * i;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) ba = min(ba, __shfl_xor_sync(kFull, ba, o));
+  if (ba == INT32_MAX) ba = 0;
+  const float2 A = sp[ba];
+  bb = INT32_MAX;
+#pragma unroll
+  for (int i = PL - 1; i >= 0; --i) {
+    const int v = lane + 32 * i;
+    const float dx = p[i].x - A.x, dy = p[i].y - A.y;
+    if (v > ba && v < T && fmaf(dx, dx, dy * dy) == best) bb = v;
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) bb = min(bb, __shfl_xor_sync(kFull, bb, o));
+  if (bb == INT32_MAX) bb = ba;
+}
+
+// Normalises the curve on the pair (ba, bb) (points a and b read from the shared
+// copy), writes it to dst when dst is not NULL, and returns the circle statistic
+// (the same value in every lane).  Equal points give the centre of the box and 0.
+template <int PL>
+__device__ __forceinline__ float maxline_apply(float2 (&p)[PL], const float2* sp, int T, int lane, int ba, int bb,
+                                               float2* dst) {
+  const float invT = 1.0f / (float)T;
+  const float ax = sp[ba].x, ay = sp[ba].y;
+  const float dx = sp[bb].x - ax, dy = sp[bb].y - ay;
+  const float d = sqrtf(fmaf(dx, dx, dy * dy));
+  if (!(d > 0.0f)) {
+    if (dst) {
+#pragma unroll
+      for (int i = 0; i < PL; ++i)
+        if (lane + 32 * i < T) dst[lane + 32 * i] = make_float2(0.5f, 0.5f);
+    }
+    return 0.0f;
+  }
+  const float c = dx / d, s = dy / d, inv = 1.0f / d;
+  float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
+#pragma unroll
+  for (int i = 0; i < PL; ++i) {
+    const float x = p[i].x - ax, y = p[i].y - ay;
+    p[i] = make_float2(fmaf(c, x, s * y) * inv, fmaf(c, y, -s * x) * inv);
+    if (lane + 32 * i < T) {
+      x0 = fminf(x0, p[i].x);
+      x1 = fmaxf(x1, p[i].x);
+      y0 = fminf(y0, p[i].y);
+      y1 = fmaxf(y1, p[i].y);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
+    x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
+    y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
+    y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
+  }
+  const float sx = 0.5f - 0.5f * (x0 + x1), sy = 0.5f - 0.5f * (y0 + y1);
+  float r[PL], rs = 0.f;
+#pragma unroll
+  for (int i = 0; i < PL; ++i) {
+    p[i].x += sx;
+    p[i].y += sy;
+    r[i] = hypotf(p[i].x - 0.5f, p[i].y - 0.5f);
+    if (lane + 32 * i < T) {
+      if (dst) dst[lane + 32 * i] = p[i];
+      rs += r[i];
+    }
+  }
+  const float mean = warp_sum(rs) * invT;
+  float v = 0.f;
+#pragma unroll
+  for (int i = 0; i < PL; ++i)
+    if (lane + 32 * i < T) v = fmaf(r[i] - mean, r[i] - mean, v);
+  return warp_sum(v) * invT;
+}
+
 template <int PL>
 __global__ void __launch_bounds__(256) maxline_kernel(int64_t M, int T, const float2* __restrict__ in,
                                                       float2* __restrict__ out, int32_t* __restrict__ pair,
                                                       float* __restrict__ circ_var) {
+  __shared__ float2 curve_s[8][32 * PL];
   const int lane = threadIdx.x & 31;
+  float2* sp = curve_s[threadIdx.x >> 5];
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float invT = 1.0f / (float)T;
   for (int64_t m = w0; m < M; m += nw) {
-    const float2* src = in + m * T;
     float2 p[PL];
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      const int t = lane + 32 * i;
-      p[i] = t < T ? src[t] : make_float2(0.f, 0.f);
-    }
-    // farthest pair: (d2, a, b) largest d2, then smallest a, then smallest b
-    float best = -1.0f;
-    int ba = 0, bb = T > 1 ? 1 : 0;
-#pragma unroll
-    for (int j = 0; j < PL; ++j) {
-      for (int vl = 0; vl < 32; ++vl) {
-        const int v = 32 * j + vl;
-        const float vx = __shfl_sync(kFull, p[j].x, vl), vy = __shfl_sync(kFull, p[j].y, vl);
-        if (v >= T) continue;  // uniform in the warp
-#pragma unroll
-        for (int i = 0; i < PL; ++i) {
-          const int u = lane + 32 * i;
-          const float dx = vx - p[i].x, dy = vy - p[i].y;
-          const float d2 = fmaf(dx, dx, dy * dy);
-          if (u < v && (d2 > best || (d2 == best && (u < ba || (u == ba && v < bb))))) {
-            best = d2;
-            ba = u;
-            bb = v;
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      const float ob = __shfl_xor_sync(kFull, best, o);
-      const int oa = __shfl_xor_sync(kFull, ba, o), obb = __shfl_xor_sync(kFull, bb, o);
-      if (ob > best || (ob == best && (oa < ba || (oa == ba && obb < bb)))) {
-        best = ob;
-        ba = oa;
-        bb = obb;
-      }
-    }
-    float2 pa = p[0], pb = p[0];  // the pair's points, selected without indexing the array
-#pragma unroll
-    for (int i = 1; i < PL; ++i) {
-      if (i == (ba >> 5)) pa = p[i];
-      if (i == (bb >> 5)) pb = p[i];
-    }
-    const float ax = __shfl_sync(kFull, pa.x, ba & 31), ay = __shfl_sync(kFull, pa.y, ba & 31);
-    const float bx = __shfl_sync(kFull, pb.x, bb & 31), by = __shfl_sync(kFull, pb.y, bb & 31);
-    const float dx = bx - ax, dy = by - ay;
-    const float d = sqrtf(fmaf(dx, dx, dy * dy));
-    float2* dst = out + m * T;
-    if (!(d > 0.0f)) {  // equal points: the centre of the box
-#pragma unroll
-      for (int i = 0; i < PL; ++i)
-        if (lane + 32 * i < T) dst[lane + 32 * i] = make_float2(0.5f, 0.5f);
-      if (lane == 0) {
-        if (pair) pair[2 * m] = ba, pair[2 * m + 1] = bb;
-        if (circ_var) circ_var[m] = 0.0f;
-      }
-      continue;
-    }
-    const float c = dx / d, s = dy / d, inv = 1.0f / d;
-    float x0 = INFINITY, x1 = -INFINITY, y0 = INFINITY, y1 = -INFINITY;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      const float x = p[i].x - ax, y = p[i].y - ay;
-      p[i] = make_float2(fmaf(c, x, s * y) * inv, fmaf(c, y, -s * x) * inv);
-      if (lane + 32 * i < T) {
-        x0 = fminf(x0, p[i].x);
-        x1 = fmaxf(x1, p[i].x);
-        y0 = fminf(y0, p[i].y);
-        y1 = fmaxf(y1, p[i].y);
-      }
-    }
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      x0 = fminf(x0, __shfl_xor_sync(kFull, x0, o));
-      x1 = fmaxf(x1, __shfl_xor_sync(kFull, x1, o));
-      y0 = fminf(y0, __shfl_xor_sync(kFull, y0, o));
-      y1 = fmaxf(y1, __shfl_xor_sync(kFull, y1, o));
-    }
-    const float sx = 0.5f - 0.5f * (x0 + x1), sy = 0.5f - 0.5f * (y0 + y1);
-    float r[PL], rs = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      p[i].x += sx;
-      p[i].y += sy;
-      r[i] = hypotf(p[i].x - 0.5f, p[i].y - 0.5f);
-      if (lane + 32 * i < T) {
-        dst[lane + 32 * i] = p[i];
-        rs += r[i];
-      }
-    }
-    const float mean = warp_sum(rs) * invT;
-    float v = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i)
-      if (lane + 32 * i < T) v = fmaf(r[i] - mean, r[i] - mean, v);
-    v = warp_sum(v) * invT;
+    load_curve<PL>(in + m * T, T, lane, sp, p);
+    int ba, bb;
+    farthest_pair<PL>(p, sp, T, lane, ba, bb);
+    const float v = maxline_apply<PL>(p, sp, T, lane, ba, bb, out + m * T);
     if (lane == 0) {
       if (pair) pair[2 * m] = ba, pair[2 * m + 1] = bb;
       if (circ_var) circ_var[m] = v;
     }
   }
+}
+
+// ------------------------------------------------------------------------ curation
+//
+// The paper's dataset curation (Sec. "Dataset Curation & Processing"): the path of
+// every moving joint of every mechanism is normalised; a path is an arc when its joint
+// is linked to a fixed joint and a circle when its circle statistic is below a
+// threshold; arcs and circles are removed except for a random fraction kept.  The
+// keep draw of path (b, j) is output b * n_max + j of the splitmix64 generator (Steele,
+// Lea and Flood, OOPSLA 2014; Vigna's constants) started at the seed, as a double in
+// [0, 1) from its top 53 bits.
+
+enum : uint8_t { kPathBit = 1, kArcBit = 2, kCircleBit = 4, kKeptBit = 8 };
+
+__device__ __forceinline__ double splitmix_uniform(uint64_t seed, uint64_t idx) {
+  uint64_t z = seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1p-53;
+}
+
+struct CurateArgs {
+  int64_t R;                 // rows (mechanisms with trajectories)
+  int n_max, T;
+  const float2* traj;        // [R, n_max, T]
+  const int32_t* row_index;  // [R] mechanism of each row (NULL: row r is mechanism r)
+  int64_t B;                 // mechanisms (bound of the row_index entries)
+  int32_t* err;              // device error word (bit 2: a row index out of range)
+  const int32_t* n_joints;   // [B]
+  const uint8_t* adj;        // [B, n_max, n_max]
+  const int8_t* type;        // [B, n_max]
+  double circle_var, keep_rate;
+  uint64_t seed;
+  uint8_t* flags;            // [R, n_max]
+  float* circ_var;           // [R, n_max] or NULL
+  int32_t* pair;             // [R, n_max, 2]
+};
+
+// One warp per (row, joint): flags, circle statistic and the normalising pair.
+template <int PL>
+__global__ void __launch_bounds__(256) curate_flags_kernel(CurateArgs ca) {
+  __shared__ float2 curve_s[8][32 * PL];
+  const int lane = threadIdx.x & 31;
+  float2* sp = curve_s[threadIdx.x >> 5];
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t total = ca.R * ca.n_max;
+  for (int64_t e = w0; e < total; e += nw) {
+    const int64_t r = e / ca.n_max;
+    const int j = (int)(e - r * ca.n_max);
+    const int64_t b = ca.row_index ? ca.row_index[r] : r;
+    const bool bad = b < 0 || b >= ca.B;
+    if (bad && lane == 0 && j == 0) atomicOr(ca.err, 2);
+    const int n = bad ? 0 : min(ca.n_joints[b], ca.n_max);
+    const int8_t* tb = ca.type + (bad ? 0 : b) * ca.n_max;
+    if (j >= n || tb[j] == 0) {  // padding, a fixed joint or a bad row: no path
+      if (lane == 0) {
+        ca.flags[e] = 0;
+        if (ca.circ_var) ca.circ_var[e] = 0.f;
+        ca.pair[2 * e] = ca.pair[2 * e + 1] = 0;
+      }
+      continue;
+    }
+    float2 p[PL];
+    load_curve<PL>(ca.traj + e * ca.T, ca.T, lane, sp, p);
+    int ba, bb;
+    farthest_pair<PL>(p, sp, ca.T, lane, ba, bb);
+    const float v = maxline_apply<PL>(p, sp, ca.T, lane, ba, bb, nullptr);
+    const uint8_t* ab = ca.adj + (b * ca.n_max + j) * ca.n_max;
+    bool ground = false;
+    for (int k = lane; k < n; k += 32) ground = ground || (ab[k] && tb[k] == 0);
+    const bool arc = __any_sync(kFull, ground);
+    const bool circle = (double)v < ca.circle_var;
+    const bool kept = !(arc || circle) || splitmix_uniform(ca.seed, (uint64_t)(b * ca.n_max + j)) < ca.keep_rate;
+    if (lane == 0) {
+      ca.flags[e] = kPathBit | (arc ? kArcBit : 0) | (circle ? kCircleBit : 0) | (kept ? kKeptBit : 0);
+      if (ca.circ_var) ca.circ_var[e] = v;
+      ca.pair[2 * e] = ba;
+      ca.pair[2 * e + 1] = bb;
+    }
+  }
+}
+
+// One warp per kept path: its normalised curve at its place in the kept list.
+template <int PL>
+__global__ void __launch_bounds__(256) curate_write_kernel(int n_max, int T, const float2* __restrict__ traj,
+                                                           const int32_t* __restrict__ pair,
+                                                           const int32_t* __restrict__ kept_index,
+                                                           const int32_t* __restrict__ n_kept, int64_t cap,
+                                                           float2* __restrict__ out) {
+  __shared__ float2 curve_s[8][32 * PL];
+  const int lane = threadIdx.x & 31;
+  float2* sp = curve_s[threadIdx.x >> 5];
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t n = min((int64_t)*n_kept, cap);
+  for (int64_t q = w0; q < n; q += nw) {
+    const int64_t e = kept_index[q];
+    float2 p[PL];
+    load_curve<PL>(traj + e * T, T, lane, sp, p);
+    maxline_apply<PL>(p, sp, T, lane, pair[2 * e], pair[2 * e + 1], out + q * T);
+  }
+}
+
+template <int PL>
+static int launch_curate(links_ctx ctx, const CurateArgs& ca, int32_t* kept_index, float* kept_paths, int64_t cap,
+                         int32_t* n_kept, int32_t* sums) {
+  int per_sm = 0;
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, curate_flags_kernel<PL>, 256, 0));
+  const int64_t total = ca.R * ca.n_max;
+  unsigned grid = (unsigned)std::min<int64_t>((total + 7) / 8, (int64_t)ctx->num_sms * std::max(per_sm, 1));
+  if (grid > 0) {
+    KernelScope ks(ctx, "curate_flags");
+    curate_flags_kernel<PL><<<grid, 256, 0, ctx->stream>>>(ca);
+    LINKS_CUDA(cudaGetLastError());
+  }
+  {
+    KernelScope ks(ctx, "curate_compact");
+    int st = compact_flags(ctx->stream, ca.flags, kKeptBit, total, sums, kept_index, cap, n_kept);
+    if (st) return st;
+  }
+  if (kept_paths && cap > 0) {
+    LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, curate_write_kernel<PL>, 256, 0));
+    grid = (unsigned)std::min<int64_t>((std::min(cap, total) + 7) / 8, (int64_t)ctx->num_sms * std::max(per_sm, 1));
+    if (grid > 0) {
+      KernelScope ks(ctx, "curate_write");
+      curate_write_kernel<PL><<<grid, 256, 0, ctx->stream>>>(ca.n_max, ca.T, ca.traj, ca.pair, kept_index, n_kept,
+                                                             cap, reinterpret_cast<float2*>(kept_paths));
+      LINKS_CUDA(cudaGetLastError());
+    }
+  }
+  return LINKS_OK;
 }
 
 // ------------------------------------------------------------------------- chamfer
@@ -256,6 +430,54 @@ __device__ __forceinline__ void topk_insert(float& kd, int& ki, int k, float d, 
   int up_i = __shfl_up_sync(kFull, ki, 1);
   if (lane < k && lane > pos) { kd = up_d; ki = up_i; }
   if (lane == pos) { kd = d; ki = id; }
+}
+
+// Insertion into a warp's list of the first k hits in scan order: lane i < k holds the
+// i-th smallest scan position found so far (INT32_MAX when empty) and its distance.
+// Positions are unique, so the order is total.
+__device__ __forceinline__ void first_insert(float& kd, int& ki, int k, float d, int pos) {
+  const int lane = threadIdx.x & 31;
+  if (pos >= __shfl_sync(kFull, ki, k - 1)) return;
+  const unsigned gt = __ballot_sync(kFull, lane < k && pos < ki);
+  const int at = __ffs(gt) - 1;
+  float up_d = __shfl_up_sync(kFull, kd, 1);
+  int up_i = __shfl_up_sync(kFull, ki, 1);
+  if (lane < k && lane > at) { kd = up_d; ki = up_i; }
+  if (lane == at) { kd = d; ki = pos; }
+}
+
+// Chamfer distance in FP64 by a 16-lane group (all lanes return the value), for a
+// pair whose FP32 distance lies within its rounding band of a threshold, so that the
+// decision is the one the FP64 definition takes.  It is that definition evaluated
+// step for step: squared distances without fused multiply-adds, the nearest point's
+// distance per point, and each term's sum taken in point order (sixteen points at a
+// time, one per lane, added in lane order), so the value is the same to the last bit
+// as a plain sequential evaluation.
+__device__ __noinline__ double chamfer_f64(const float2* __restrict__ qp, const float2* cp, int T, int gl,
+                                           unsigned gmask) {
+  double sum[2] = {0.0, 0.0};
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {  // 0: query points to the curve, 1: the reverse
+    const float2* from = side ? cp : qp;
+    const float2* to = side ? qp : cp;
+    double s = 0.0;
+    for (int t0 = 0; t0 < T; t0 += 16) {
+      double v = 0.0;
+      if (t0 + gl < T) {
+        const double ax = from[t0 + gl].x, ay = from[t0 + gl].y;
+        double m = INFINITY;
+        for (int j = 0; j < T; ++j) {
+          const double dx = ax - (double)to[j].x, dy = ay - (double)to[j].y;
+          m = fmin(m, __dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)));
+        }
+        v = sqrt(m);
+      }
+      const int n = min(16, T - t0);
+      for (int l = 0; l < n; ++l) s = __dadd_rn(s, __shfl_sync(gmask, v, l, 16));
+    }
+    sum[side] = s;
+  }
+  return __dadd_rn(sum[0] / T, sum[1] / T);
 }
 
 __device__ __forceinline__ float min3(float a, float b, float c) {
@@ -492,12 +714,31 @@ __device__ __forceinline__ float chamfer_exact(const f2* QX, const f2* QY, const
 // Both bounds carry a relative rounding error below 2e-5 (sums of at most 256
 // terms), as does the exact CD; the comparison margin covers both.  Sharing the
 // pairs of a stage among all groups keeps the warps' work equal between barriers.
-template <int PL, int W>
+//
+// FIRST instead runs the paper's retrieval (Sec. "A Case Study of Mechanism
+// Retrieval"): the database is read in the scan order fa.order (position r holds
+// curve order[r]; M is then the number of positions), each query keeps the first k
+// positions whose CD is below the fixed threshold fa.thr, and the pruning distance
+// is that threshold.  A position at or past the k-th hit a query already has, in
+// this chunk or in any chunk that published one (fa.gpos), cannot be among its first
+// k, so it is skipped; a CTA stops once all its queries have their k hits before
+// the stage it would read next.  A pair whose FP32 CD lies within the rounding band
+// of the threshold is decided by the FP64 distance.
+struct FirstArgs {
+  const int32_t* order = nullptr;  // [M] database curve of each scan position
+  int64_t n_db = 0;                // database curves (bound of the order entries)
+  double thr = 0.0;                // hits are CD < thr
+  int32_t* gpos = nullptr;         // [Q] smallest k-th hit position published
+  int32_t* err = nullptr;          // device error word (bit 2: an order entry out of range)
+};
+
+template <int PL, int W, bool FIRST>
 __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T, const float2* __restrict__ qs,
                                                          const float2* __restrict__ db, int k, int64_t chunk,
                                                          float* __restrict__ part_d, int32_t* __restrict__ part_i,
                                                          const __half* __restrict__ grids,
-                                                         const float4* __restrict__ gparam, float* gthr) {
+                                                         const float4* __restrict__ gparam, float* gthr,
+                                                         FirstArgs fa) {
   static_assert(PL % 2 == 0, "query points are processed in pairs");
   constexpr int kGroups = W * 2;
   extern __shared__ __align__(16) float2 dyn[];
@@ -511,6 +752,7 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
   __shared__ int nA, nB, nres[W];
   __shared__ float res_d[W][kStage];
   __shared__ uint8_t res_s[W][kStage];
+  __shared__ int32_t ord_s[kStage];        // FIRST: curve of each staged position (-1: bad entry)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 4, gl = lane & 15, gid = warp * 2 + g;
   const unsigned gmask = 0xffffu << (g * 16);
@@ -532,10 +774,31 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
   float kd = INFINITY;
   int ki = INT32_MAX;
   float thr_pub = INFINITY;  // last k-th distance published (lane k-1)
+  int pos_pub = INT32_MAX;   // FIRST: last k-th position published
+  const float fthr = (float)fa.thr;
+  const float fband = fthr < INFINITY ? margin * fthr + 1e-6f : 0.f;
+  int cut = INT32_MAX;       // FIRST: positions from here on cannot be among the query's first k
   for (int64_t base = c0; base < c1; base += kStage) {
     const int nst = c1 - base < kStage ? (int)(c1 - base) : kStage;
-    __syncthreads();
-    for (int x = threadIdx.x; x < nst * T; x += blockDim.x) stage[x] = db[base * T + x];
+    if constexpr (FIRST) {
+      cut = __shfl_sync(kFull, ki, k - 1);
+      if (q < Q) cut = min(cut, __ldcg(fa.gpos + q));
+      if (!__syncthreads_or(q < Q && base < cut)) break;  // every query has its k hits
+      if (threadIdx.x < nst) {
+        const int64_t i = fa.order[base + threadIdx.x];
+        const bool ok = i >= 0 && i < fa.n_db;
+        if (!ok) atomicOr(fa.err, 2);
+        ord_s[threadIdx.x] = ok ? (int32_t)i : -1;
+      }
+      __syncthreads();
+      for (int x = threadIdx.x; x < nst * T; x += blockDim.x) {
+        const int s = x / T, i = ord_s[s];
+        stage[x] = i >= 0 ? db[(int64_t)i * T + (x - s * T)] : make_float2(0.f, 0.f);
+      }
+    } else {
+      __syncthreads();
+      for (int x = threadIdx.x; x < nst * T; x += blockDim.x) stage[x] = db[base * T + x];
+    }
     if (threadIdx.x < kStage) rho_s[threadIdx.x] = 0u;
     if (threadIdx.x < W) nres[threadIdx.x] = 0;
     if (threadIdx.x == 0) nA = nB = 0;
@@ -563,10 +826,16 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
     }
     // A: this warp's query against the staged curves
     if (q < Q) {
-      float thr = __shfl_sync(kFull, kd, k - 1);
-      if (prune) thr = fminf(thr, __ldcg(gthr + q));
+      float thr;
+      if constexpr (FIRST) {
+        thr = fthr;
+      } else {
+        thr = __shfl_sync(kFull, kd, k - 1);
+        if (prune) thr = fminf(thr, __ldcg(gthr + q));
+      }
       if (lane == 0) thr_w[warp] = thr;
       bool keep = lane < nst;
+      if constexpr (FIRST) keep = keep && base + lane < cut && ord_s[lane] >= 0;
       const bool bounded = prune && thr < INFINITY;
       float lb = 0.f;
       if (bounded && keep) {
@@ -623,19 +892,44 @@ __global__ void __launch_bounds__(W * 32) chamfer_kernel(int Q, int64_t M, int T
         const int w = listB[e] / kStage, s = listB[e] % kStage;
         load_query<PL>(qs + (int64_t)(qbase + w) * T, T, gl, QX, QY);
         const float thr = thr_w[w];
-        const float d = chamfer_exact<PL>(QX, QY, stage + s * T, T, gl, gmask, invT, prune ? thr : INFINITY);
-        if (gl == 0 && d <= thr) {
-          const int at = atomicAdd(&nres[w], 1);
-          res_d[w][at] = d;
-          res_s[w][at] = (uint8_t)s;
+        if constexpr (FIRST) {
+          const float d = chamfer_exact<PL>(QX, QY, stage + s * T, T, gl, gmask, invT,
+                                            prune ? fthr + fband : INFINITY);
+          bool hit = d < fthr - fband;
+          float dd = d;
+          if (!hit && !(d > fthr + fband)) {  // within the rounding band (uniform in the group)
+            const double d64 = chamfer_f64(qs + (int64_t)(qbase + w) * T, stage + s * T, T, gl, gmask);
+            hit = d64 < fa.thr;
+            dd = (float)d64;
+          }
+          if (gl == 0 && hit) {
+            const int at = atomicAdd(&nres[w], 1);
+            res_d[w][at] = dd;
+            res_s[w][at] = (uint8_t)s;
+          }
+        } else {
+          const float d = chamfer_exact<PL>(QX, QY, stage + s * T, T, gl, gmask, invT, prune ? thr : INFINITY);
+          if (gl == 0 && d <= thr) {
+            const int at = atomicAdd(&nres[w], 1);
+            res_d[w][at] = d;
+            res_s[w][at] = (uint8_t)s;
+          }
         }
       }
     }
     __syncthreads();
     if (q < Q) {
       const int n = nres[warp];
-      for (int r = 0; r < n; ++r) topk_insert(kd, ki, k, res_d[warp][r], (int)(base + res_s[warp][r]));
-      if (prune && lane == k - 1 && kd < thr_pub) {  // publish this chunk's k-th distance
+      if constexpr (FIRST) {
+        for (int r = 0; r < n; ++r) first_insert(kd, ki, k, res_d[warp][r], (int)(base + res_s[warp][r]));
+        if (lane == k - 1 && ki < pos_pub) {  // publish this chunk's k-th position
+          atomicMin(fa.gpos + q, ki);
+          pos_pub = ki;
+        }
+      } else {
+        for (int r = 0; r < n; ++r) topk_insert(kd, ki, k, res_d[warp][r], (int)(base + res_s[warp][r]));
+      }
+      if (!FIRST && prune && lane == k - 1 && kd < thr_pub) {  // publish this chunk's k-th distance
         atomicMin(reinterpret_cast<unsigned*>(gthr + q), __float_as_uint(kd));  // CDs are >= 0
         thr_pub = kd;
       }
@@ -675,9 +969,40 @@ __global__ void topk_merge_kernel(int Q, int nchunk, int k, const float* __restr
   }
 }
 
-template <int PL, int W>
+// One warp per query: the first k hits in scan order from the chunks' lists (chunks
+// cover increasing positions, and each list is ascending with its empty entries
+// last), mapped back to database curves.
+__global__ void first_merge_kernel(int Q, int nchunk, int k, const float* __restrict__ part_d,
+                                   const int32_t* __restrict__ part_i, const int32_t* __restrict__ order,
+                                   int32_t* __restrict__ idx, float* __restrict__ dist) {
+  const int lane = threadIdx.x & 31;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= Q) return;
+  int found = 0;
+  for (int c = 0; c < nchunk && found < k; ++c) {
+    const int64_t o = ((int64_t)q * nchunk + c) * k + lane;
+    const int pos = lane < k ? part_i[o] : INT32_MAX;
+    const bool hit = pos != INT32_MAX;
+    if (hit && found + lane < k) {
+      idx[(int64_t)q * k + found + lane] = order[pos];
+      dist[(int64_t)q * k + found + lane] = part_d[o];
+    }
+    found += __popc(__ballot_sync(kFull, hit));
+  }
+  if (lane >= found && lane < k) {
+    idx[(int64_t)q * k + lane] = -1;
+    dist[(int64_t)q * k + lane] = INFINITY;
+  }
+}
+
+__global__ void fill_i32_kernel(int n, int32_t v, int32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = v;
+}
+
+template <int PL, int W, bool FIRST>
 int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, const float2* db, int k,
-                   int32_t* idx, float* dist, int prune) {
+                   int32_t* idx, float* dist, int prune, FirstArgs fa) {
   const int qtiles = (Q + W - 1) / W;
   if (M == 0) {  // nothing to rank: idx = -1, dist = +inf
     KernelScope ks(ctx, "topk_merge");
@@ -685,11 +1010,13 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
     LINKS_CUDA(cudaGetLastError());
     return LINKS_OK;
   }
-  // database chunks: one CTA per SM at a time; at least four waves, the CTA count
-  // a multiple of the SM count where the chunk count allows
+  // database chunks: one CTA per SM at a time; at least four waves (sixteen for the
+  // scan, whose later chunks end early once the earlier ones have found the hits),
+  // the CTA count a multiple of the SM count where the chunk count allows
   const int64_t max_chunks = (M + kStage - 1) / kStage;
   const int64_t sms = ctx->num_sms;
-  int64_t nchunk = std::max<int64_t>(1, (4 * sms + qtiles - 1) / qtiles);
+  const int64_t waves = FIRST ? 16 : 4;
+  int64_t nchunk = std::max<int64_t>(1, (waves * sms + qtiles - 1) / qtiles);
   for (int64_t c = nchunk; c <= 2 * nchunk; ++c)
     if ((c * qtiles) % sms == 0) {
       nchunk = c;
@@ -704,7 +1031,8 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
   const size_t grid_bytes = prune ? (size_t)Q * kNG * kNG * sizeof(__half) : 0;
   const size_t param_off = grid_off + grid_bytes;
   const size_t thr_off = param_off + (prune ? (size_t)Q * sizeof(float4) : 0);
-  const size_t need = thr_off + (prune ? (size_t)Q * sizeof(float) : 0);
+  const size_t pos_off = (thr_off + (prune ? (size_t)Q * sizeof(float) : 0) + 15) / 16 * 16;
+  const size_t need = pos_off + (FIRST ? (size_t)Q * sizeof(int32_t) : 0);
   int st = ensure_workspace(ctx, need);
   if (st) return st;
   char* ws = reinterpret_cast<char*>(ctx->ws);
@@ -713,6 +1041,13 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
   __half* grids = prune ? reinterpret_cast<__half*>(ws + grid_off) : nullptr;
   float4* gparam = prune ? reinterpret_cast<float4*>(ws + param_off) : nullptr;
   float* gthr = prune ? reinterpret_cast<float*>(ws + thr_off) : nullptr;
+  if (FIRST) {
+    fa.gpos = reinterpret_cast<int32_t*>(ws + pos_off);
+    fa.err = ctx->d_err;
+    KernelScope ks(ctx, "first_init");
+    fill_i32_kernel<<<(Q + 255) / 256, 256, 0, ctx->stream>>>(Q, INT32_MAX, fa.gpos);
+    LINKS_CUDA(cudaGetLastError());
+  }
   if (prune) {
     KernelScope ks(ctx, "dt_grid");
     dt_grid_kernel<<<Q, 256, 0, ctx->stream>>>(Q, T, qs, grids, gparam, gthr);
@@ -720,14 +1055,19 @@ int launch_chamfer(links_ctx ctx, int Q, int64_t M, int T, const float2* qs, con
   }
   const size_t smem = (size_t)kStage * T * sizeof(float2) +
                       (prune ? (size_t)kStage * kMaxG * sizeof(float2) + (size_t)W * kNG * kNG * sizeof(__half) : 0);
-  LINKS_CUDA(cudaFuncSetAttribute(chamfer_kernel<PL, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  LINKS_CUDA(cudaFuncSetAttribute(chamfer_kernel<PL, W, FIRST>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem));
   {
-    KernelScope ks(ctx, "chamfer");
-    chamfer_kernel<PL, W><<<dim3(qtiles, (unsigned)nchunk), W * 32, smem, ctx->stream>>>(
-        Q, M, T, qs, db, k, chunk, part_d, part_i, grids, gparam, gthr);
+    KernelScope ks(ctx, FIRST ? "chamfer_first" : "chamfer");
+    chamfer_kernel<PL, W, FIRST><<<dim3(qtiles, (unsigned)nchunk), W * 32, smem, ctx->stream>>>(
+        Q, M, T, qs, db, k, chunk, part_d, part_i, grids, gparam, gthr, fa);
   }
   LINKS_CUDA(cudaGetLastError());
-  {
+  if (FIRST) {
+    KernelScope ks(ctx, "first_merge");
+    first_merge_kernel<<<(Q * 32 + 255) / 256, 256, 0, ctx->stream>>>(Q, (int)nchunk, k, part_d, part_i,
+                                                                       fa.order, idx, dist);
+  } else {
     KernelScope ks(ctx, "topk_merge");
     topk_merge_kernel<<<(Q * 32 + 255) / 256, 256, 0, ctx->stream>>>(Q, (int)nchunk, k, part_d, part_i, idx, dist);
   }
@@ -751,17 +1091,25 @@ static int normalize_launch(links_ctx ctx, int64_t M, const int32_t* M_dev, int 
   return LINKS_OK;
 }
 
+template <int PL>
+static int launch_maxline(links_ctx ctx, int64_t M, int T, const float2* in, float2* out, int32_t* pair,
+                          float* circ_var) {
+  int per_sm = 0;  // resident blocks per SM: the grid is one full wave
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, maxline_kernel<PL>, 256, 0));
+  const unsigned grid = (unsigned)std::min<int64_t>((M + 7) / 8, (int64_t)ctx->num_sms * std::max(per_sm, 1));
+  KernelScope ks(ctx, "normalize_maxline");
+  maxline_kernel<PL><<<grid, 256, 0, ctx->stream>>>(M, T, in, out, pair, circ_var);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
 int normalize_maxline(links_ctx ctx, int64_t M, int T, const float* in, float* out, int32_t* pair,
                       float* circ_var) {
   if (M == 0) return LINKS_OK;
-  const unsigned grid = (unsigned)std::min<int64_t>((M + 7) / 8, (int64_t)ctx->num_sms * 8);
-  KernelScope ks(ctx, "normalize_maxline");
   const float2* i2 = reinterpret_cast<const float2*>(in);
   float2* o2 = reinterpret_cast<float2*>(out);
-  if (T <= 64) maxline_kernel<2><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, pair, circ_var);
-  else maxline_kernel<8><<<grid, 256, 0, ctx->stream>>>(M, T, i2, o2, pair, circ_var);
-  LINKS_CUDA(cudaGetLastError());
-  return LINKS_OK;
+  if (T <= 64) return launch_maxline<2>(ctx, M, T, i2, o2, pair, circ_var);
+  return launch_maxline<8>(ctx, M, T, i2, o2, pair, circ_var);
 }
 
 int normalize_paths(links_ctx ctx, int64_t M, int T, const float* in, float* out) {
@@ -778,11 +1126,61 @@ int chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const float* q, const f
   const float2* q2 = reinterpret_cast<const float2*>(q);
   const float2* d2 = reinterpret_cast<const float2*>(db);
   const int pl = (T + 15) / 16;  // query points per lane of a 16-lane group
-  if (pl <= 2) return launch_chamfer<2, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
-  if (pl <= 4) return launch_chamfer<4, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
-  if (pl <= 8) return launch_chamfer<8, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
-  if (pl <= 14) return launch_chamfer<14, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
-  return launch_chamfer<16, 16>(ctx, Q, M, T, q2, d2, k, idx, dist, prune);
+  const FirstArgs fa{};
+  if (pl <= 2) return launch_chamfer<2, 16, false>(ctx, Q, M, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 4) return launch_chamfer<4, 16, false>(ctx, Q, M, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 8) return launch_chamfer<8, 16, false>(ctx, Q, M, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 14) return launch_chamfer<14, 16, false>(ctx, Q, M, T, q2, d2, k, idx, dist, prune, fa);
+  return launch_chamfer<16, 16, false>(ctx, Q, M, T, q2, d2, k, idx, dist, prune, fa);
+}
+
+int chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* q, const float* db, int64_t L,
+                        const int32_t* order, double thr, int k, int32_t* idx, float* dist, int prune) {
+  if (Q == 0) return LINKS_OK;
+  const float2* q2 = reinterpret_cast<const float2*>(q);
+  const float2* d2 = reinterpret_cast<const float2*>(db);
+  FirstArgs fa;
+  fa.order = order;
+  fa.n_db = M;
+  fa.thr = thr;
+  const int pl = (T + 15) / 16;
+  if (pl <= 2) return launch_chamfer<2, 16, true>(ctx, Q, L, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 4) return launch_chamfer<4, 16, true>(ctx, Q, L, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 8) return launch_chamfer<8, 16, true>(ctx, Q, L, T, q2, d2, k, idx, dist, prune, fa);
+  if (pl <= 14) return launch_chamfer<14, 16, true>(ctx, Q, L, T, q2, d2, k, idx, dist, prune, fa);
+  return launch_chamfer<16, 16, true>(ctx, Q, L, T, q2, d2, k, idx, dist, prune, fa);
+}
+
+int curate_paths(links_ctx ctx, int64_t R, int n_max, int T, const float* traj, const int32_t* row_index,
+                 int64_t B, const int32_t* n_joints, const uint8_t* adj, const int8_t* type, double circle_var,
+                 double keep_rate, uint64_t seed, uint8_t* flags, float* circ_var, int32_t* pair,
+                 int32_t* kept_index, float* kept_paths, int64_t kept_capacity, int32_t* n_kept) {
+  const int64_t total = R * n_max;
+  const size_t pair_bytes = pair ? 0 : ((size_t)total * 2 * sizeof(int32_t) + 255) / 256 * 256;
+  const size_t need = pair_bytes + (size_t)compact_sums_count(total) * sizeof(int32_t) + 256;
+  int st = ensure_workspace(ctx, need);
+  if (st) return st;
+  char* ws = reinterpret_cast<char*>(ctx->ws);
+  CurateArgs ca;
+  ca.R = R;
+  ca.n_max = n_max;
+  ca.T = T;
+  ca.traj = reinterpret_cast<const float2*>(traj);
+  ca.row_index = row_index;
+  ca.B = B;
+  ca.err = ctx->d_err;
+  ca.n_joints = n_joints;
+  ca.adj = adj;
+  ca.type = type;
+  ca.circle_var = circle_var;
+  ca.keep_rate = keep_rate;
+  ca.seed = seed;
+  ca.flags = flags;
+  ca.circ_var = circ_var;
+  ca.pair = pair ? pair : reinterpret_cast<int32_t*>(ws);
+  int32_t* sums = reinterpret_cast<int32_t*>(ws + pair_bytes);
+  if (T <= 64) return launch_curate<2>(ctx, ca, kept_index, kept_paths, kept_capacity, n_kept, sums);
+  return launch_curate<8>(ctx, ca, kept_index, kept_paths, kept_capacity, n_kept, sums);
 }
 
 }  // namespace links

@@ -33,6 +33,9 @@ Workload recipes (the paper's dataset is not available; these stand in for it):
   the oracle consume the rounded values.
 * ``perturb_curves``: query curves = stored curves + N(0, sigma^2) per
   coordinate (Box-Muller from the same generator).
+* ``fourier_curves``: closed curves from a random Fourier series of 4 harmonics
+  (coefficient h uniform on [-1, 1] / h^1.5 per coordinate), a database of path
+  shapes of any size drawn without simulating anything.
 * ``poisson_requests``: request arrival times with exponential gaps and
   candidate counts log-uniform on [1, c_max].
 """
@@ -75,7 +78,7 @@ class Stream:
 
 
 # Stream tags (one per purpose, so that changing one recipe leaves the others alone).
-_T_NJ, _T_GROUND, _T_PAIR, _T_POS, _T_PERM, _T_NOISE, _T_ARRIVE, _T_COUNT = range(1, 9)
+_T_NJ, _T_GROUND, _T_PAIR, _T_POS, _T_PERM, _T_NOISE, _T_ARRIVE, _T_COUNT, _T_SHAPE = range(1, 10)
 
 
 @dataclass
@@ -313,6 +316,23 @@ def perturb_curves(curves: np.ndarray, sigma: float, seed: int = 0, tag: int = 0
     r = np.sqrt(-2.0 * np.log(u1))
     z = np.concatenate([r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)])[:size]
     return (curves.astype(np.float64) + sigma * z.reshape(curves.shape)).astype(np.float32)
+
+
+def fourier_curves(M: int, T: int, seed: int = 0, harmonics: int = 4) -> np.ndarray:
+    """[M, T, 2] float32 closed curves sampled at T equally spaced parameters."""
+    st = Stream(seed, _T_SHAPE)
+    H = harmonics
+    c = st.uniform(np.arange(M * H * 4, dtype=np.uint64)).reshape(M, H, 4) * 2.0 - 1.0
+    c /= (np.arange(1, H + 1, dtype=np.float64) ** 1.5)[None, :, None]
+    ang = 2.0 * np.pi * np.arange(T, dtype=np.float64) / T
+    hs = np.arange(1, H + 1, dtype=np.float64)[:, None] * ang[None, :]  # [H, T]
+    cs, sn = np.cos(hs), np.sin(hs)
+    out = np.empty((M, T, 2), np.float32)
+    for lo in range(0, M, 65536):
+        cc = c[lo:lo + 65536]
+        out[lo:lo + 65536, :, 0] = cc[:, :, 0] @ cs + cc[:, :, 1] @ sn
+        out[lo:lo + 65536, :, 1] = cc[:, :, 2] @ cs + cc[:, :, 3] @ sn
+    return out
 
 
 def poisson_requests(n_req: int, rate_hz: float, c_max: int, seed: int = 0, tag: int = 0):

@@ -73,6 +73,9 @@ def lib():
             "links_normalize": ([P, i64, i32, P, P], i32),
             "links_normalize_maxline": ([P, i64, i32, P, P, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
+            "links_curate_paths": ([P, i64, i32, i32, P, P, i64, P, P, P, ctypes.c_double, ctypes.c_double,
+                                    ctypes.c_uint64, P, P, P, P, P, i64, P], i32),
+            "links_chamfer_first_under": ([P, i32, i64, i32, P, P, i64, P, ctypes.c_double, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
             "links_serve_start": ([P, ctypes.c_size_t, i32, i32, i32, i32], i32),
             "links_serve_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)], i32),
@@ -284,6 +287,41 @@ def links_chamfer_topk(ctx, queries, db, k: int, idx, dist):
     _check(lib().links_chamfer_topk(ctx, int(Q), int(M), int(T), _dev(queries, torch.float32, "queries"),
                                     _dev(db, torch.float32, "db"), int(k), _dev(idx, torch.int32, "idx"),
                                     _dev(dist, torch.float32, "dist")), "links_chamfer_topk")
+
+
+def links_chamfer_first_under(ctx, queries, db, order, threshold: float, k: int, idx, dist):
+    """queries [Q,T,2], db [M,T,2] float32, order [L] int32 scan order; idx [Q,k] int32 and
+    dist [Q,k] float32 outputs: the first k curves of the scan with CD < threshold (CUDA)."""
+    import torch
+    Q, T = queries.shape[0], queries.shape[1]
+    _check(lib().links_chamfer_first_under(ctx, int(Q), int(db.shape[0]), int(T),
+                                           _dev(queries, torch.float32, "queries"), _dev(db, torch.float32, "db"),
+                                           int(order.shape[0]), _dev(order, torch.int32, "order"),
+                                           float(threshold), int(k), _dev(idx, torch.int32, "idx"),
+                                           _dev(dist, torch.float32, "dist")), "links_chamfer_first_under")
+
+
+def links_curate_paths(ctx, traj, row_index, n_joints, adj, jtype, flags, n_kept, *, circle_var: float = 5e-4,
+                       keep_rate: float = 0.005, seed: int = 0, circ_var=None, pair=None, kept_index=None,
+                       kept_paths=None):
+    """traj [R, n_max, T, 2] float32, row_index [R] int32 (or None), n_joints [B] int32, adj
+    [B, n_max, n_max] uint8, jtype [B, n_max] int8; outputs flags [R, n_max] uint8, n_kept [1]
+    int32, optional circ_var [R, n_max] float32, pair [R, n_max, 2] int32, kept_index [cap]
+    int32 and kept_paths [cap, T, 2] float32 (all CUDA)."""
+    import torch
+    R, n_max, T = traj.shape[0], traj.shape[1], traj.shape[2]
+    cap = 0 if kept_index is None else int(kept_index.shape[0])
+    if kept_paths is not None and kept_paths.shape[0] < cap:
+        raise ValueError("kept_paths holds fewer rows than kept_index")
+    _check(lib().links_curate_paths(ctx, int(R), int(n_max), int(T), _dev(traj, torch.float32, "traj"),
+                                    _dev(row_index, torch.int32, "row_index"), int(n_joints.shape[0]),
+                                    _dev(n_joints, torch.int32, "n_joints"), _dev(adj, torch.uint8, "adj"),
+                                    _dev(jtype, torch.int8, "jtype"), float(circle_var), float(keep_rate),
+                                    int(seed) & 0xFFFFFFFFFFFFFFFF, _dev(flags, torch.uint8, "flags"),
+                                    _dev(circ_var, torch.float32, "circ_var"), _dev(pair, torch.int32, "pair"),
+                                    _dev(kept_index, torch.int32, "kept_index"),
+                                    _dev(kept_paths, torch.float32, "kept_paths"), cap,
+                                    _dev(n_kept, torch.int32, "n_kept")), "links_curate_paths")
 
 
 def links_workspace_reserve(ctx, nbytes: int):

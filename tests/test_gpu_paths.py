@@ -224,3 +224,200 @@ def test_normalize_maxline_matches_oracle(L, ctx, T):
         assert vr[-3] < 1e-6
     with pytest.raises(L.LinksError):
         L.links_normalize_maxline(ctx, x, x)
+
+
+def gpu_first(L, ctx, q32, db32, order, thr, k):
+    q = torch.from_numpy(np.ascontiguousarray(q32)).cuda()
+    d = torch.from_numpy(np.ascontiguousarray(db32)).cuda()
+    o = torch.from_numpy(np.ascontiguousarray(order, dtype=np.int32)).cuda()
+    idx = torch.empty((q.shape[0], k), dtype=torch.int32, device="cuda")
+    dist = torch.empty((q.shape[0], k), dtype=torch.float32, device="cuda")
+    L.links_chamfer_first_under(ctx, q, d, o, thr, k, idx, dist)
+    L.links_sync(ctx)
+    return idx.cpu().numpy(), dist.cpu().numpy()
+
+
+def check_first(q, db, order, thr, k, idx, dist, label):
+    """Indices bit-exact with the oracle (the decision at the threshold is taken on the
+    FP64 distance); distances within 1e-5 relative."""
+    ridx, rdist = O.chamfer_first_under(q.astype(np.float64), db.astype(np.float64), order, thr, k)
+    assert np.array_equal(idx, ridx), (label, idx, ridx)
+    hit = ridx >= 0
+    assert np.allclose(dist[hit], rdist[hit], rtol=1e-5, atol=1e-7)
+    assert np.isinf(dist[~hit]).all()
+    print(f"[{label}] queries {len(q)} db {len(db)} hits {int(hit.sum())} of {hit.size}")
+
+
+@pytest.mark.parametrize("T,M,Q,k", [(200, 3000, 24, 3), (37, 1500, 9, 5), (13, 700, 17, 32), (256, 400, 5, 1)])
+def test_chamfer_first_under_matches_oracle(L, ctx, T, M, Q, k):
+    """The paper's retrieval (first k under a cut-off in a shuffled scan) against the
+    oracle, at cut-offs from none to all of the database; pruning on and off agree."""
+    curves = O.normalize(coupler_curves(M + Q, T, seed=500 + T)).astype(np.float32)
+    db, held = curves[:M], curves[M:M + Q]
+    q = O.normalize(I.perturb_curves(held, 0.02, seed=T).astype(np.float64)).astype(np.float32)
+    q[0] = db[M // 3]
+    order = np.random.default_rng(T).permutation(M)
+    order = np.concatenate([[M // 3], order[order != M // 3]])  # the copy is scanned first
+    d0 = O.chamfer_many(q[1].astype(np.float64), db.astype(np.float64))
+    for thr in (0.0, float(np.quantile(d0, 0.002)), float(np.quantile(d0, 0.05)), float(np.quantile(d0, 0.5)),
+                float("inf")):
+        for prune in (True, False):
+            L.links_set_chamfer_prune(ctx, prune)
+            idx, dist = gpu_first(L, ctx, q, db, order, thr, k)
+            if prune:
+                ref = (idx, dist)
+            else:
+                assert np.array_equal(ref[0], idx) and np.array_equal(ref[1], dist)
+        check_first(q, db, order, thr, k, idx, dist, f"T={T} M={M} thr={thr:.3g}")
+        if thr > 0:  # the exact copy is the first hit, at distance 0
+            assert idx[0, 0] == M // 3 and dist[0, 0] == 0.0
+    L.links_set_chamfer_prune(ctx, True)
+
+
+def test_chamfer_first_under_threshold_band(L, ctx):
+    """Cut-offs placed exactly at the FP64 distance of a pair (a miss: the test is CD <
+    threshold) and just above it (a hit): the FP32 distance sits inside its rounding
+    band, so the FP64 recomputation decides, as the oracle does."""
+    T, M = 64, 500
+    curves = O.normalize(coupler_curves(M + 4, T, seed=77)).astype(np.float32)
+    db, q = curves[:M], curves[M:M + 4]
+    order = np.random.default_rng(5).permutation(M)
+    for a in range(4):
+        d = O.chamfer_many(q[a].astype(np.float64), db.astype(np.float64))
+        # the curve scanned first that has no nearer curve scanned before it
+        j = int(order[0])
+        for thr in (float(d[j]), float(np.nextafter(d[j], np.inf))):
+            idx, dist = gpu_first(L, ctx, q[a:a + 1], db, order, thr, 1)
+            check_first(q[a:a + 1], db, order, thr, 1, idx, dist, f"band query {a} thr={thr!r}")
+            assert (idx[0, 0] == j) == (thr > d[j])
+
+
+def test_chamfer_first_under_partial_scan_and_errors(L, ctx):
+    """A scan over part of the database (L < M, repeats allowed), an empty scan, and an
+    order entry out of range (skipped, raised on the device error word)."""
+    T, M = 50, 600
+    curves = O.normalize(coupler_curves(M + 3, T, seed=9)).astype(np.float32)
+    db, q = curves[:M], curves[M:]
+    rng = np.random.default_rng(1)
+    order = np.concatenate([rng.choice(M, 150, replace=False), rng.choice(M, 50)])
+    thr = float(np.quantile(O.chamfer_many(q[0].astype(np.float64), db.astype(np.float64)), 0.3))
+    idx, dist = gpu_first(L, ctx, q, db, order, thr, 8)
+    check_first(q, db, order, thr, 8, idx, dist, "partial scan")
+    idx, dist = gpu_first(L, ctx, q, db, order[:0], thr, 4)
+    assert (idx == -1).all() and np.isinf(dist).all()
+    bad = order.copy()
+    bad[3] = M + 5
+    with pytest.raises(L.LinksError) as e:
+        gpu_first(L, ctx, q, db, bad, thr, 4)
+    assert e.value.status == L.EDEVICE
+    L.links_sync(ctx)  # the error word was cleared
+    qq = torch.zeros((2, T, 2), dtype=torch.float32, device="cuda")
+    o = torch.zeros(4, dtype=torch.int32, device="cuda")
+    idx = torch.empty((2, 4), dtype=torch.int32, device="cuda")
+    dist = torch.empty((2, 4), dtype=torch.float32, device="cuda")
+    with pytest.raises(L.LinksError):
+        L.links_chamfer_first_under(ctx, qq, qq, o, float("nan"), 4, idx, dist)
+    with pytest.raises(L.LinksError):
+        L.links_chamfer_first_under(ctx, qq, qq, o, 0.1, 33, idx, dist)
+
+
+def test_chamfer_first_under_full_size_sampled(L, ctx):
+    """The scan at the retrieval benchmark's size (1M curves of 200 points, pruning on, the
+    bench's chunking), checked on sampled queries: over the scan prefix up to the k-th
+    hit (at most 4000 positions), the oracle's hits are exactly the kernel's."""
+    T, M, Q, k = 200, 1_000_000, 32, 3
+    db = I.fourier_curves(M, T, seed=21)
+    q = np.concatenate([I.perturb_curves(db[:Q // 2], 0.05, seed=22), I.fourier_curves(Q // 2, T, seed=23)])
+    order = np.random.default_rng(24).permutation(M)
+    sample = db[order[:2000]].astype(np.float64)
+    thr = float(np.quantile(O.chamfer_many(q[Q // 2].astype(np.float64), sample), 0.002))
+    idx, dist = gpu_first(L, ctx, q, db, order, thr, k)
+    rng = np.random.default_rng(25)
+    for a in sorted(set(rng.choice(Q, 5, replace=False).tolist()) | {0, Q // 2}):
+        hits = idx[a][idx[a] >= 0]
+        pos = np.array([int(np.nonzero(order == h)[0][0]) for h in hits], dtype=np.int64)
+        end = int(pos[-1]) + 1 if len(hits) == k else M
+        end = min(end, 4000)
+        pre = order[:end]
+        d = O.chamfer_many(q[a].astype(np.float64), db[pre].astype(np.float64))
+        ref = pre[d < thr][:k]
+        assert np.array_equal(hits[:len(ref)], ref), (a, hits, ref)
+        assert np.all(pos[len(ref):] >= end)
+        dd = O.chamfer_many(q[a].astype(np.float64), db[hits].astype(np.float64))
+        assert np.all(dd < thr) and np.allclose(dist[a][:len(hits)], dd, rtol=1e-5, atol=1e-7)
+        print(f"[full size] query {a}: hits {hits.tolist()} at positions {pos.tolist()}")
+
+
+@pytest.mark.parametrize("n_lo,n_hi,T,keep", [(6, 8, 200, 0.005), (5, 12, 64, 0.3), (6, 10, 33, 1.0)])
+def test_curation_matches_oracle(L, ctx, n_lo, n_hi, T, keep):
+    """The paper's curation of every moving joint's path, on the oracle's trajectories of
+    valid candidates (valid-only rows, so row r is mechanism row_index[r]): path and arc
+    flags bit-exact; the normalising pair a farthest pair up to float rounding; with it
+    imposed, the oracle's circle statistic within 2e-6 and the circle flag equal (a
+    statistic within 1e-6 of the threshold may go either way); kept flags exactly as
+    the keep rule gives from the flags and the splitmix64 draws; the kept list in order
+    and its normalised paths within 2e-5."""
+    batch = I.dyad_batch(1500, n_lo, n_hi, seed=T + n_hi, nmax=n_hi)
+    res = O.simulate(batch, T, traj=True, path=False)
+    rows = np.nonzero(res.valid == 1)[0].astype(np.int32)
+    traj = res.traj[rows].astype(np.float32)
+    R, n_max = traj.shape[0], traj.shape[1]
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    flags = torch.empty((R, n_max), dtype=torch.uint8, device="cuda")
+    cv = torch.empty((R, n_max), dtype=torch.float32, device="cuda")
+    pair = torch.empty((R, n_max, 2), dtype=torch.int32, device="cuda")
+    cap = R * n_max
+    kidx = torch.empty(cap, dtype=torch.int32, device="cuda")
+    kpaths = torch.empty((cap, T, 2), dtype=torch.float32, device="cuda")
+    nk = torch.empty(1, dtype=torch.int32, device="cuda")
+    L.links_curate_paths(ctx, dev(traj), dev(rows), dev(batch.n_joints.astype(np.int32)), dev(batch.adj),
+                         dev(batch.jtype), flags, nk, keep_rate=keep, seed=99, circ_var=cv, pair=pair,
+                         kept_index=kidx, kept_paths=kpaths)
+    L.links_sync(ctx)
+    f, v, pr = flags.cpu().numpy(), cv.cpu().numpy(), pair.cpu().numpy()
+    n_kept = int(nk.item())
+    ref = O.curate_paths(traj.astype(np.float64), rows, batch, keep_rate=keep, seed=99, pairs=pr)
+    assert np.array_equal(f & 3, ref["flags"] & 3)
+    _, opair, _ = O.normalize_maxline(traj.reshape(R * n_max, T, 2)[(f.reshape(-1) & 1) != 0].astype(np.float64))
+    c64 = traj.reshape(R * n_max, T, 2)[(f.reshape(-1) & 1) != 0].astype(np.float64)
+    gp = pr.reshape(-1, 2)[(f.reshape(-1) & 1) != 0]
+    d = lambda c, pq: np.hypot(*(c[pq[1]] - c[pq[0]]))
+    for m in range(len(c64)):
+        assert d(c64[m], gp[m]) >= d(c64[m], opair[m]) * (1 - 1e-5)
+    has = (f & 1) != 0
+    assert np.abs(v[has] - ref["circ_var"][has]).max() <= 2e-6
+    near = np.abs(ref["circ_var"] - 5e-4) <= 1e-6
+    assert np.array_equal((f & 4)[~near], (ref["flags"] & 4)[~near])
+    b = rows[:, None].astype(np.uint64) * np.uint64(n_max) + np.arange(n_max, dtype=np.uint64)[None, :]
+    u = (O.splitmix64(99, b) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    want = has & (((f & 6) == 0) | (u < keep))
+    assert np.array_equal((f & 8) != 0, want)
+    kl = np.nonzero(want.reshape(-1))[0]
+    assert n_kept == len(kl) and np.array_equal(kidx.cpu().numpy()[:n_kept], kl)
+    err = np.abs(kpaths.cpu().numpy()[:n_kept] - ref["kept_paths"]).max() if n_kept else 0.0
+    assert err <= 2e-5
+    arcs, circles = int(((f & 2) != 0).sum()), int(((f & 4) != 0).sum())
+    print(f"[curation n={n_lo}-{n_hi} T={T}] rows {R} paths {int(has.sum())} arcs {arcs} circles {circles} "
+          f"kept {n_kept} near-threshold {int((near & has).sum())} max path err {err:.2e}")
+
+
+def test_curation_bad_row_and_sizes(L, ctx):
+    """A row index out of range gives that row no paths and raises the device error word;
+    bad sizes are refused."""
+    batch = I.dyad_batch(64, 6, 6, seed=3)
+    res = O.simulate(batch, 50, traj=True, path=False)
+    traj = torch.from_numpy(np.nan_to_num(res.traj).astype(np.float32)).cuda()
+    rows = torch.arange(64, dtype=torch.int32, device="cuda")
+    rows[5] = 64
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    flags = torch.empty((64, 6), dtype=torch.uint8, device="cuda")
+    nk = torch.empty(1, dtype=torch.int32, device="cuda")
+    L.links_curate_paths(ctx, traj, rows, dev(batch.n_joints.astype(np.int32)), dev(batch.adj), dev(batch.jtype),
+                         flags, nk)
+    with pytest.raises(L.LinksError) as e:
+        L.links_sync(ctx)
+    assert e.value.status == L.EDEVICE
+    assert (flags[5].cpu().numpy() == 0).all()
+    with pytest.raises(L.LinksError):
+        L.links_curate_paths(ctx, traj, rows, dev(batch.n_joints.astype(np.int32)), dev(batch.adj),
+                             dev(batch.jtype), flags, nk, circle_var=float("nan"))

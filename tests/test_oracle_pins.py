@@ -507,19 +507,56 @@ def test_first_under_scan_order(oracle_lib):
     """The paper's retrieval: the first k curves below the threshold in scan order. A copy
     of the query placed first in the scan is returned first at distance 0; a threshold
     above every distance returns the first k curves of the scan whatever their
-    distances; one below every distance returns none."""
+    distances; one below every distance returns none; hits come in scan order."""
     O = oracle_lib
     rng = np.random.default_rng(8)
     s = np.linspace(0, 2 * np.pi, 40, endpoint=False)
     db = np.stack([np.stack([np.cos(s) * a, np.sin(s)], -1) for a in rng.uniform(0.5, 2, 30)])
     q = db[17].copy()
-    rank = rng.permutation(30)
-    rank[[17, int(np.argmin(rank))]] = rank[[int(np.argmin(rank)), 17]]  # curve 17 is scanned first
-    idx, dist = O.chamfer_first_under(q[None], db, rank, 0.3, 3)
+    order = rng.permutation(30)
+    order = np.concatenate([[17], order[order != 17]])  # curve 17 is scanned first
+    idx, dist = O.chamfer_first_under(q[None], db, order, 0.3, 3)
     assert idx[0, 0] == 17 and dist[0, 0] == 0.0
     d = O.chamfer_many(q, db)
-    assert np.all(d[idx[0][idx[0] >= 0]] < 0.3)
-    idx, _ = O.chamfer_first_under(q[None], db, rank, 1e9, 5)
-    assert np.array_equal(idx[0], np.argsort(rank)[:5])
-    idx, dist = O.chamfer_first_under(q[None], db, rank, 0.0, 3)
+    found = idx[0][idx[0] >= 0]
+    assert np.all(d[found] < 0.3)
+    pos = [int(np.nonzero(order == i)[0][0]) for i in found]
+    assert pos == sorted(pos)
+    skipped = order[:pos[-1]]  # every curve scanned before the last hit and not returned is >= 0.3
+    assert np.all(d[np.setdiff1d(skipped, found)] >= 0.3)
+    idx, _ = O.chamfer_first_under(q[None], db, order, 1e9, 5)
+    assert np.array_equal(idx[0], order[:5])
+    idx, dist = O.chamfer_first_under(q[None], db, order, 0.0, 3)
     assert np.all(idx == -1) and np.all(np.isinf(dist))
+
+
+def test_splitmix64_published_outputs(oracle_lib):
+    """The keep draws' generator against the published splitmix64 sequence started at 0."""
+    z = oracle_lib.splitmix64(0, np.arange(3))
+    assert [int(v) for v in z] == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+
+
+def test_curation_flags(oracle_lib):
+    """The paper's curation on a hand-built four-bar: the crank tip (linked to the
+    ground pivot) is an arc and, tracing a full circle, a circle too; the rocker joint
+    (linked to the second pivot) is an arc but not a circle; the coupler point is
+    neither and is always kept; fixed joints have no path; with keep rate 0 nothing
+    flagged is kept and with keep rate 1 everything is."""
+    O = oracle_lib
+    from paper_2208_14567_gb300 import inputs as I
+    fb = I.fourbar_batch(1)
+    fb.pos[0] = np.array([[0.0, 0.0], [0.3, 0.0], [1.0, 0.0], [0.8, 0.7], [0.5, 0.9]])
+    r = O.simulate(fb, 200, traj=True, path=False)
+    assert r.valid[0] == 1
+    c0 = O.curate_paths(r.traj, None, fb, keep_rate=0.0)
+    f = c0["flags"][0]
+    assert f[0] == 0 and f[2] == 0                      # fixed joints
+    assert f[1] == 1 | 2 | 4                            # crank tip: arc and circle, removed
+    assert f[3] & 2 and not f[3] & 4 and not f[3] & 8   # rocker: arc, removed
+    assert f[4] == 1 | 8                                # coupler point: kept
+    assert c0["circ_var"][0, 1] < 1e-12 and c0["circ_var"][0, 4] > 5e-4
+    assert list(c0["kept_index"]) == [4]
+    c1 = O.curate_paths(r.traj, None, fb, keep_rate=1.0)
+    assert list(c1["kept_index"]) == [1, 3, 4]
+    n0, _, _ = O.normalize_maxline(r.traj[0, 4][None])
+    assert np.array_equal(c1["kept_paths"][2], n0[0])
