@@ -9,8 +9,9 @@
 // (Sec. "1-DOF Operator"): apart from ground-ground links and the crank, every simple
 // joint owns exactly two links.
 //
-// The same builder runs as a CUDA kernel (one thread per mechanism) and on host
-// threads; both produce bit-identical plans.
+// The builder runs on host threads and in CUDA kernels: one thread per mechanism
+// (build_one) for n_max <= 8, a group of 16 or 32 lanes per mechanism (build_group)
+// for larger mechanisms.  All produce bit-identical plans.
 #include <algorithm>
 #include <thread>
 #include <vector>
@@ -301,6 +302,204 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
   return o;
 }
 
+// The same builder on a group of G lanes per mechanism (G >= n_max): lane a holds
+// joint a's neighbour mask and slot, lane s the bound of slot s, lane d the dyad d
+// found d-th.  The checks and the solve-order search are group votes, the dyads'
+// geometry is computed by their lanes in parallel, and the bound chain (each dyad's
+// bound from its parents') runs over the dyads in solve order through shuffles.  Each
+// value is the same expression on the same operands as in build_one, and the maxima
+// and minima do not depend on the order they are taken in, so the plan is the same
+// to the bit.
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int G>
+struct Group {
+  unsigned mask;
+  int base;
+  __device__ unsigned ballot(bool v) const { return (__ballot_sync(mask, v) & mask) >> base; }
+  __device__ bool any(bool v) const { return ballot(v) != 0; }
+  template <class V>
+  __device__ V bc(V v, int src) const { return __shfl_sync(mask, v, src, G); }
+  __device__ int sum(int v) const {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(mask, v, o, G);
+    return v;
+  }
+  __device__ float max(float v) const {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
+  __device__ float min(float v) const {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
+    return v;
+  }
+};
+
+template <typename PT, int G>
+__device__ int build_group(int n, int n_max, const uint8_t* __restrict__ adj, const int8_t* __restrict__ type,
+                           const PT* __restrict__ pos, BuildOut o, int gl, const Group<G>& grp, int* nd_out) {
+  MechHdr h{};
+  h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
+  int status = LINKS_MECH_OK;
+  if (n < 2 || n > n_max || n_max > G) status = LINKS_MECH_BAD_SIZE;
+  const bool joint = status == LINKS_MECH_OK && gl < n;
+  const int t = joint ? type[gl] : -1;
+  const uint32_t fixm = grp.ballot(joint && t == 0), simm = grp.ballot(joint && t == 1);
+  const uint32_t motm = grp.ballot(joint && t == 2);
+  if (grp.any(joint && (t < 0 || t > 2))) status = LINKS_MECH_BAD_TYPE;
+  uint32_t nb = 0;  // lane a: neighbours of joint a
+  if (status == LINKS_MECH_OK) {
+    if (gl < n) {
+      const uint8_t* row = adj + (size_t)gl * n_max;
+      for (int c = 0; c < n; ++c) nb |= (row[c] != 0 ? 1u : 0u) << c;
+    }
+    bool bad = gl < n && ((nb >> gl) & 1u);
+    for (int c = 0; c < n; ++c) {
+      const uint32_t nbc = grp.bc(nb, c);
+      if (gl < n && ((nb >> c) & 1u) && !((nbc >> gl) & 1u)) bad = true;
+    }
+    if (grp.any(bad)) status = LINKS_MECH_BAD_ADJ;
+  }
+  if (status == LINKS_MECH_OK && popc32(motm) != 1) status = LINKS_MECH_NO_MOTOR;
+  int motor = -1, pivot = -1, nd = 0;
+  if (status == LINKS_MECH_OK) {
+    motor = ffs32(motm);
+    const uint32_t pm = grp.bc(nb, motor) & fixm;
+    if (!pm) status = LINKS_MECH_NO_PIVOT;
+    else pivot = ffs32(pm);
+  }
+  int dk = 0, di = 0, dj = 0, my_d = -1;  // lane d: dyad d; lane a: the dyad solving joint a
+  if (status == LINKS_MECH_OK) {
+    uint32_t known = fixm | motm, unknown = simm;
+    while (unknown) {
+      const int c = popc32(nb & known);
+      const uint32_t cand = grp.ballot(gl < n && ((unknown >> gl) & 1u) && c >= 2);
+      if (!cand) {
+        status = LINKS_MECH_NOT_DYAD_SOLVABLE;
+        break;
+      }
+      const int pick = ffs32(cand);
+      if (grp.bc(c, pick) > 2) {
+        status = LINKS_MECH_OVERCONSTRAINED;
+        break;
+      }
+      const uint32_t par = grp.bc(nb, pick) & known;
+      if (gl == nd) {
+        dk = pick;
+        di = ffs32(par);
+        dj = ffs32(par & (par - 1));
+      }
+      if (gl == pick) my_d = nd;
+      ++nd;
+      known |= 1u << pick;
+      unknown &= ~(1u << pick);
+    }
+  }
+  if (status == LINKS_MECH_OK) {
+    const int e2 = grp.sum(gl < n ? popc32(nb) : 0);
+    const int ff2 = grp.sum(gl < n && ((fixm >> gl) & 1u) ? popc32(nb & fixm) : 0);
+    if ((e2 - ff2) / 2 - 1 != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
+  }
+  h.status = status;
+  if (status != LINKS_MECH_OK) {
+    h.nd = 0;
+    if (gl == 0) *o.hdr = h;
+    return status;
+  }
+
+  // Slots: fixed joints by index, then the actuated joint, then dyads in solve order.
+  const int nf = popc32(fixm);
+  int slot = 0;  // lane a: slot of joint a
+  if ((fixm >> gl) & 1u) slot = popc32(fixm & ((1u << gl) - 1u));
+  else if (gl == motor) slot = nf;
+  else if (my_d >= 0) slot = nf + 1 + my_d;
+  if (gl < n) {
+    o.slot_joint[slot] = (uint8_t)gl;
+    o.pos64[slot] = make_double2((double)pos[2 * gl], (double)pos[2 * gl + 1]);
+  }
+  float bound = 0.0f, bmax = 0.0f;  // lane s: bound of slot s
+  if (gl < nf) {
+    uint32_t m = fixm;
+    for (int q = 0; q < gl; ++q) m &= m - 1;
+    const dw2 r = rel(pos, ffs32(m), pivot);
+    o.fixpos[gl] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
+    bound = hyp_up(r.x.h, r.y.h);
+    bmax = bound;
+  }
+  const dw2 u = rel(pos, motor, pivot);
+  const float crank = hyp_up(u.x.h, u.y.h);
+  if (gl == nf) bound = crank;
+  bmax = fmaxf(bmax, crank);
+
+  int i = di, j = dj;
+  float r1h = 0.0f, r2h = 0.0f;
+  DyadRec rec;
+  if (gl < nd) {
+    const int k = dk;
+    dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
+    dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
+    if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
+      int tt = i; i = j; j = tt;
+      dw2 tv = vi; vi = vj; vj = tv;
+    }
+    dw r1sq = norm2(vi), r2sq = norm2(vj);
+    dw r1 = dw_sqrt_exact(r1sq), r2 = dw_sqrt_exact(r2sq);
+    dw R12 = dw_add(r1, r2);
+    dw Rm = dw_sub(r1, r2);
+    if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
+    dw c = dw_sub(r1sq, r2sq);
+    r1h = r1.h;
+    r2h = r2.h;
+    rec.r0 = make_float4(0.0f, R12.h, Rm.h, c.h);
+    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), fmul(kAmpErr * kU, R12.h), 0.0f, 0.0f);
+    rec.r2 = make_float4(r1sq.h, r1sq.l, c.l, 0.0f);
+  }
+  const int si = grp.bc(slot, i), sj = grp.bc(slot, j);  // slots of the lane's dyad's parents
+  if (gl < nd) {
+    const int sk = nf + 1 + gl;
+    const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)dk << 16) | ((uint32_t)sk << 24);
+    const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
+    const uint32_t offK = ((uint32_t)sk * 256u) | (((uint32_t)sk * 128u) << 16);
+    const uint32_t offEij = ((uint32_t)si * 128u) | (((uint32_t)sj * 128u) << 16);
+    rec.r0.x = u2f(offPij);
+    rec.r1.z = u2f(offK);
+    rec.r1.w = u2f(offEij);
+    rec.r2.w = u2f(slots);
+    o.dyad[gl] = rec;
+  }
+  for (int d = 0; d < nd; ++d) {  // the bound chain, in solve order
+    const float bi = grp.bc(bound, grp.bc(si, d)), bj = grp.bc(bound, grp.bc(sj, d));
+    const float bk = fmul(fminf(fadd(bi, grp.bc(r1h, d)), fadd(bj, grp.bc(r2h, d))), 1.0f + 4.0f * kU);
+    if (gl == nf + 1 + d) bound = bk;
+    bmax = fmaxf(bmax, bk);
+  }
+  bmax = grp.max(bmax);
+  const float x = gl < n ? (float)pos[2 * gl] : INFINITY, y = gl < n ? (float)pos[2 * gl + 1] : INFINITY;
+  const float lo_x = grp.min(x), lo_y = grp.min(y);
+  const float hi_x = grp.max(gl < n ? x : -INFINITY), hi_y = grp.max(gl < n ? y : -INFINITY);
+  const int pivot_slot = grp.bc(slot, pivot);
+  if (gl == 0) {
+    h.nd = (uint8_t)nd;
+    h.nf = (uint8_t)nf;
+    h.motor_joint = (uint8_t)motor;
+    h.pivot_joint = (uint8_t)pivot;
+    h.pad0 = (uint8_t)pivot_slot;
+    h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
+    h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
+    dw px = abs_dw(pos, 2 * pivot), py = abs_dw(pos, 2 * pivot + 1);
+    h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
+    h.bmax = bmax;
+    h.lbox = hyp_up(fsub(hi_x, lo_x), fsub(hi_y, lo_y));
+    h.e_motor = fmul(4.0f * kU, crank);
+    h.e_fixed = fmul(kU, bmax);
+    *o.hdr = h;
+  }
+  if (nd_out) *nd_out = nd;
+  return status;
+}
+
 // Inputs of the block's 256 mechanisms (n_max <= 8) staged in shared memory with
 // coalesced loads: each mechanism's adjacency, type and position rows padded to an odd
 // number of words, so that the threads' reads of their own rows fall in distinct banks.
@@ -362,6 +561,35 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
 }
 
+// G lanes per mechanism (build_group); 256 / G mechanisms per block.
+template <typename PT, int G>
+__global__ void __launch_bounds__(256) build_group_kernel(int64_t B, const int32_t* __restrict__ n_joints,
+                                                          const uint8_t* __restrict__ adj,
+                                                          const int8_t* __restrict__ type,
+                                                          const PT* __restrict__ pos, PlanDev p,
+                                                          int32_t* __restrict__ status_out) {
+  __shared__ int hist[32];
+  if (threadIdx.x < 32) hist[threadIdx.x] = 0;
+  __syncthreads();
+  const int nm = p.n_max;
+  const int lane = threadIdx.x & 31, gl = lane % G;
+  Group<G> grp;
+  grp.base = lane - gl;
+  grp.mask = G == 32 ? kFull : (((1u << G) - 1u) << grp.base);
+  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
+  if (b < B) {  // uniform in the group
+    int nd = 0;
+    const int st = build_group<PT, G>(n_joints[b], nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2,
+                                      out_of(p, b), gl, grp, &nd);
+    if (gl == 0) {
+      if (status_out) status_out[b] = st;
+      if (st == LINKS_MECH_OK) atomicAdd(&hist[nd], 1);
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
+}
+
 // Counting sort of the OK mechanisms by dyad count (a processing order only: warps then
 // meet mechanisms of equal length together).
 __global__ void __launch_bounds__(256) scatter_kernel(int64_t B, PlanDev p) {
@@ -400,17 +628,23 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
   if (B == 0) return LINKS_OK;
   unsigned grid = (unsigned)((B + 255) / 256);
   {
-  KernelScope ks(ctx, "plan_build");
-  const bool small = p.n_max <= 8;
-  if (pos_dtype == LINKS_F32) {
-    const float* ps = (const float*)pos0;
-    if (small) build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-    else build_kernel<float, kMaxJ><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-  } else {
-    const double* ps = (const double*)pos0;
-    if (small) build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-    else build_kernel<double, kMaxJ><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-  }
+    KernelScope ks(ctx, "plan_build");
+    // n_max <= 8: a thread per mechanism, scratch in registers (measured faster than a
+    // lane group at this size); larger: a group of 16 or 32 lanes per mechanism
+    const int G = p.n_max <= 16 ? 16 : 32;
+    const unsigned ggrid = (unsigned)((B * G + 255) / 256);
+    const bool small = p.n_max <= 8;
+    if (pos_dtype == LINKS_F32) {
+      const float* ps = (const float*)pos0;
+      if (small) build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      else if (G == 16) build_group_kernel<float, 16><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      else build_group_kernel<float, 32><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+    } else {
+      const double* ps = (const double*)pos0;
+      if (small) build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      else if (G == 16) build_group_kernel<double, 16><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      else build_group_kernel<double, 32><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+    }
   }
   LINKS_CUDA(cudaGetLastError());
   {

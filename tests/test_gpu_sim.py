@@ -130,6 +130,22 @@ def planted_bad(batch):
     return b
 
 
+@pytest.mark.parametrize("n_lo,n_hi,nmax,f64", [(6, 8, 8, False), (5, 8, 8, True), (6, 16, 16, False),
+                                                 (6, 20, 20, True), (3, 6, 32, False)])
+def test_device_and_host_plans_simulate_identically(L, n_lo, n_hi, nmax, f64):
+    """The device builder (a lane group per mechanism: 8, 16 or 32 lanes by n_max) and the
+    host builder give the same plans: every output of a mixed simulation on them is
+    the same to the bit, the planted ill-formed mechanisms included."""
+    batch = planted_bad(I.dyad_batch(4000, n_lo, n_hi, seed=n_hi + nmax, permute=True, nmax=nmax,
+                                     pos_dtype=np.float64 if f64 else np.float32))
+    a = run(batch, 64, L.MIXED, L.OUT_FULL, L, host_build=False)
+    b = run(batch, 64, L.MIXED, L.OUT_FULL, L, host_build=True)
+    for k in ("status", "valid", "lock_step", "min_disc", "traj", "path"):
+        assert np.array_equal(a[k], b[k], equal_nan=True), k
+    print(f"[plans n={n_lo}-{n_hi} n_max={nmax} {'f64' if f64 else 'f32'}] valid {a['valid'].mean():.3f} "
+          f"statuses {sorted(set(a['status'].tolist()))}")
+
+
 def test_plan_matches_oracle_device_and_host(L):
     from paper_2208_14567_gb300.api import Simulator, to_device
     batch = planted_bad(I.dyad_batch(3000, 6, 16, seed=2, permute=True, nmax=20))
