@@ -77,6 +77,7 @@ extern "C" {
 typedef struct links_ctx_s* links_ctx;
 typedef struct links_plan_s* links_plan;
 typedef struct links_graph_s* links_graph;
+typedef struct links_topo_s* links_topo;
 
 /* Text of the calling thread's last failure ("" if none).  Static storage. */
 LINKS_API const char* links_last_error(void);
@@ -241,6 +242,37 @@ LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const f
 LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
                                         const float* db, int64_t L, const int32_t* order, double threshold,
                                         int k, int32_t* idx, float* dist);
+/* ---- Topology-specialised screen (the paper's solver specific to one topology, Sec.
+ * "Graphical Simulator": the solve path is found once and serves every position
+ * sample).  links_topo_create plans the topology given by one mechanism's n joints,
+ * adj [n_max, n_max] and type [n_max] (HOST memory, the layout of links_plan_build),
+ * writes CUDA source for its solve path (joint positions and error bounds in
+ * registers, parent slots as compile-time names), compiles it for sm_103a with NVRTC
+ * and loads it on the context's device; synchronous (tens to hundreds of ms).
+ * LINKS_EINVAL for bad sizes or a topology that does not plan (status in the text),
+ * LINKS_ECUDA if the compilation or the load fails. */
+LINKS_API int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t* adj, const int8_t* type,
+                                links_topo* out);
+/* The CUDA source links_topo_create compiles for that topology (host, no device
+ * needed): NUL-terminated into buf (cap bytes, truncated if shorter), *len (may be
+ * NULL) the size it needs including the NUL.  LINKS_EINVAL as links_topo_create. */
+LINKS_API int links_topo_source(int n, int n_max, const uint8_t* adj, const int8_t* type, char* buf, size_t cap,
+                                size_t* len);
+/* Fixed joints and dyads of the compiled solve path, and the time create took. */
+LINKS_API int links_topo_info(links_topo topo, int* n_fixed, int* n_dyads, double* compile_ms);
+LINKS_API int links_topo_free(links_topo topo);
+/* links_simulate with precision LINKS_MIXED (same arguments and outputs), its screen
+ * first run by the topology's kernel: mechanisms whose plan follows the compiled path
+ * and whose FP32 bounds decide every step up to the first certain lock get their
+ * flags, lock step and min_disc from it (the generic screen's values: the same
+ * operations in the same order); the others (another topology, or an uncertain step)
+ * go to the generic screen, *n_escaped (device int32, may be NULL) their count.
+ * Compaction and emit follow as in links_simulate.  Asynchronous. */
+LINKS_API int links_simulate_topology(links_ctx ctx, links_plan plan, links_topo topo, int T, int out_mode,
+                                      float* traj, float* path, uint8_t* valid, int16_t* lock_step,
+                                      float* min_disc, int32_t* out_index, int64_t out_capacity,
+                                      int32_t* n_out, int32_t* n_escaped);
+
 /* The paper's dataset curation (Sec. "Dataset Curation & Processing").  For every
  * joint j of every row r of traj [R, n_max, T, 2] float32 (device; the layout of
  * links_simulate's trajectories, row r belonging to mechanism row_index[r], or to

@@ -116,6 +116,18 @@ class Simulator:
                          out.min_disc, out.out_index, cap, out.n_out)
         return out
 
+    def simulate_topology(self, topo, T: int, out_mode: int = L.OUT_FULL, out: SimOut | None = None, traj=True,
+                          path=True, out_capacity=None, n_escaped=None) -> SimOut:
+        """Mixed simulation with the screen of a topology-specialised kernel first
+        (links_simulate_topology; topo from links_topo_create)."""
+        if out is None:
+            out = self.alloc(T, L.MIXED, out_mode, traj, path, out_capacity)
+        cap = 0 if out.out_index is None else (out.traj.shape[0] if out.traj is not None else
+                                               (out.path.shape[0] if out.path is not None else out.out_index.shape[0]))
+        L.links_simulate_topology(self.ctx, self.plan, topo, T, out_mode, out.traj, out.path, out.valid,
+                                  out.lock_step, out.min_disc, out.out_index, cap, out.n_out, n_escaped)
+        return out
+
     def simulate_two_stage(self, T: int, T_low: int, out: SimOut | None = None, traj=True, path=True,
                            out_capacity=None, n_low_valid=None) -> SimOut:
         """Low-fidelity screen on T_low positions, confirmation on T of the survivors,

@@ -68,7 +68,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     with ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-lpthread"]
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "shared", "-lpthread",
+           # run-time compilation of topology-specialised kernels
+           "-L", cuda_lib, "-lnvrtc", "-Xlinker", "-rpath", "-Xlinker", cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

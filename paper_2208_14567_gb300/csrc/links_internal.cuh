@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <cmath>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -211,6 +212,15 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
 // the fastest for this n_max (allocates scratch; not inside a capture).
 int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes);
 // Shared by both precisions: rows of the valid mechanisms in index order.
+// A first screen of the OK mechanisms (see simulate_prescreened).
+using Prescreen = std::function<int(links_ctx, links_plan, const TTable*, uint8_t*, int16_t*, float*)>;
+int simulate_prescreened(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
+                         float* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                         int64_t out_capacity, int32_t* n_out, int32_t* n_escaped, const Prescreen& prescreen);
+// The plan of one mechanism built on the host (status returned; hdr and dyad records
+// [n_max - 2] written).
+int plan_one_host(int n, int n_max, const uint8_t* adj, const int8_t* type, const double* pos, MechHdr* hdr,
+                  DyadRec* dyad);
 int compact_valid(links_ctx ctx, links_plan plan, const uint8_t* valid, int32_t* out_index,
                   int64_t out_capacity, int32_t* n_out);
 int fill_unsimulated(links_ctx ctx, links_plan plan, uint8_t* valid, int16_t* lock_step,

@@ -619,6 +619,15 @@ __global__ void __launch_bounds__(256) scatter_kernel(int64_t B, PlanDev p) {
 
 }  // namespace
 
+int plan_one_host(int n, int n_max, const uint8_t* adj, const int8_t* type, const double* pos, MechHdr* hdr,
+                  DyadRec* dyad) {
+  std::vector<uint8_t> sj(kMaxJ);
+  std::vector<float4> fix(std::max(n_max, 1));
+  std::vector<double2> p64(std::max(n_max, 1));
+  BuildOut o{hdr, sj.data(), fix.data(), p64.data(), dyad};
+  return build_one<double, kMaxJ>(n, n_max, adj, type, pos, o);
+}
+
 int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                       const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
                       int32_t* status_out) {

@@ -685,6 +685,34 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
   return LINKS_OK;
 }
 
+// The mixed simulation with the screen done first by `prescreen`, which decides the OK
+// mechanisms it can and lists the others in p.order2 (their count in
+// p.ctrs[kNConfirm]); the generic screen takes that list, then compaction and emit.
+int simulate_prescreened(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
+                         float* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                         int64_t out_capacity, int32_t* n_out, int32_t* n_escaped, const Prescreen& prescreen) {
+  PlanDev& p = plan->d;
+  int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
+  if (st) return st;
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kNConfirm, 0, sizeof(int32_t), ctx->stream));
+  st = prescreen(ctx, plan, tab, valid, lock_step, min_disc);
+  if (st) return st;
+  if (n_escaped)
+    LINKS_CUDA(cudaMemcpyAsync(n_escaped, p.ctrs + kNConfirm, sizeof(int32_t), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+  st = launch_screen_lanes(ctx, plan, tab->T, tab, valid, lock_step, min_disc, screen_lanes(ctx, plan), p.order2,
+                           p.ctrs + kNConfirm);
+  if (st) return st;
+  const bool full = out_mode == LINKS_OUT_FULL;
+  if (!full) {
+    st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
+    if (st) return st;
+  }
+  if (traj || path)
+    return launch_emit<false>(ctx, plan, tab, full, lock_step, out_index, out_capacity, traj, path, "mixed_emit");
+  return LINKS_OK;
+}
+
 // Low-fidelity screen on the coarse grid (tab_lo), confirmation on the fine grid (tab)
 // of the mechanisms valid on the coarse one, then valid-row compaction and emit.
 int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, const TTable* tab, float* traj,

@@ -75,6 +75,11 @@ def lib():
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_curate_paths": ([P, i64, i32, i32, P, P, i64, P, P, P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_uint64, P, P, P, P, P, i64, P], i32),
+            "links_topo_create": ([P, i32, i32, P, P, P], i32),
+            "links_topo_info": ([P, P, P, P], i32),
+            "links_topo_source": ([i32, i32, P, P, P, ctypes.c_size_t, P], i32),
+            "links_topo_free": ([P], i32),
+            "links_simulate_topology": ([P, P, P, i32, i32, P, P, P, P, P, P, i64, P, P], i32),
             "links_chamfer_first_under": ([P, i32, i64, i32, P, P, i64, P, ctypes.c_double, i32, P, P], i32),
             "links_workspace_reserve": ([P, ctypes.c_size_t], i32),
             "links_serve_start": ([P, ctypes.c_size_t, i32, i32, i32, i32], i32),
@@ -237,6 +242,53 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
                                 _dev(out_index, torch.int32, "out_index"), int(out_capacity),
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_topo_create(ctx, n: int, adj, jtype):
+    """Compile the screen specialised to one topology: adj [n_max, n_max] uint8 and jtype [n_max]
+    int8 of one mechanism with n joints (numpy, host).  Returns the handle."""
+    import numpy as np
+    a = np.ascontiguousarray(adj, dtype=np.uint8)
+    t = np.ascontiguousarray(jtype, dtype=np.int8)
+    h = ctypes.c_void_p()
+    _check(lib().links_topo_create(ctx, int(n), int(a.shape[0]), a.ctypes.data_as(ctypes.c_void_p),
+                                   t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "links_topo_create")
+    return h
+
+
+def links_topo_source(n: int, adj, jtype) -> str:
+    """The CUDA source links_topo_create compiles for this topology (host only)."""
+    import numpy as np
+    a = np.ascontiguousarray(adj, dtype=np.uint8)
+    t = np.ascontiguousarray(jtype, dtype=np.int8)
+    need = ctypes.c_size_t()
+    args = (int(n), int(a.shape[0]), a.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p))
+    _check(lib().links_topo_source(*args, None, 0, ctypes.byref(need)), "links_topo_source")
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().links_topo_source(*args, buf, need.value, None), "links_topo_source")
+    return buf.value.decode()
+
+
+def links_topo_info(topo) -> dict:
+    nf, nd, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    _check(lib().links_topo_info(topo, ctypes.byref(nf), ctypes.byref(nd), ctypes.byref(ms)), "links_topo_info")
+    return {"fixed": nf.value, "dyads": nd.value, "compile_ms": ms.value}
+
+
+def links_topo_free(topo):
+    _check(lib().links_topo_free(topo), "links_topo_free")
+
+
+def links_simulate_topology(ctx, plan, topo, T: int, out_mode: int, traj, path, valid, lock_step, min_disc,
+                            out_index=None, out_capacity: int = 0, n_out=None, n_escaped=None):
+    import torch
+    _check(lib().links_simulate_topology(ctx, plan, topo, int(T), int(out_mode), _dev(traj, torch.float32, "traj"),
+                                         _dev(path, torch.float32, "path"), _dev(valid, torch.uint8, "valid"),
+                                         _dev(lock_step, torch.int16, "lock_step"),
+                                         _dev(min_disc, torch.float32, "min_disc"),
+                                         _dev(out_index, torch.int32, "out_index"), int(out_capacity),
+                                         _dev(n_out, torch.int32, "n_out"), _dev(n_escaped, torch.int32, "n_escaped")),
+           "links_simulate_topology")
 
 
 def links_simulate_two_stage(ctx, plan, T: int, T_low: int, traj, path, valid, lock_step, min_disc,

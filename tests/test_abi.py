@@ -53,3 +53,28 @@ def test_null_arguments_are_rejected_without_a_gpu(so):
     assert so.links_plan_free(None) == 1  # LINKS_EINVAL
     so.links_destroy.argtypes = [ctypes.c_void_p]
     assert so.links_destroy(None) == 1
+
+
+def test_topology_source_compiles():
+    """The generated source of a topology-specialised screen compiles for sm_103a (host
+    side only: code generation and nvcc, no device)."""
+    import shutil
+
+    import numpy as np
+    import subprocess
+    import tempfile
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links
+    nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    for n in (6, 12):
+        b = I.paper_topologies(2, n, seed=n)
+        src = links.links_topo_source(int(b.n_joints[0]), b.adj[0], b.jtype[0])
+        assert "topo_screen" in src and src.count("rsqrtf(d2)") == int(n - 2 - (b.jtype[0] == 0).sum() + 1)
+        with tempfile.TemporaryDirectory() as d:
+            p = f"{d}/t.cu"
+            open(p, "w").write(src)
+            r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-c", p, "-o", f"{d}/t.o"],
+                               capture_output=True, text=True)
+            assert r.returncode == 0, r.stderr[-2000:]
+    with pytest.raises(links.LinksError):
+        links.links_topo_source(6, np.zeros((6, 6), np.uint8), np.array([0, 2, 1, 1, 1, 1], np.int8))
