@@ -278,6 +278,73 @@ def path_stage(args, local, stream):
         L.links_destroy(ctx)
 
 
+def topology_stage(args, local, stream):
+    """The paper's shared-topology workload: 1M position samples of one topology of the
+    paper's generator, simulated by the generic mixed path and by the path whose screen
+    is compiled for that topology (links_topo_create / links_simulate_topology); same
+    outputs, times per step and the compile time."""
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T, S = args.T, args.topology_samples
+    dev = torch.device("cuda", local)
+    rows = []
+    for n in (6, 8, 12):
+        batch = I.paper_batch(1, S, n, seed=100 + n)
+        with Simulator(batch.B, n, device=local, stream=stream) as s:
+            db = to_device(batch, dev)
+            st = s.build(db)
+            probe = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+            s.sync()
+            nv = int(probe.n_out[0])
+            ga = s.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=nv + 1)
+            gb = s.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=nv + 1)
+            esc = torch.zeros(1, dtype=torch.int32, device=dev)
+
+            def timed(fn):
+                for _ in range(2):
+                    s.build(db, st)
+                    fn()
+                s.sync()
+                L.links_profile(s.ctx, True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    s.build(db, st)
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                prof = L.links_profile_read(s.ctx)
+                L.links_profile(s.ctx, False)
+                screen = sum(v[0] / v[1] for k, v in prof.items() if k in ("mixed_screen", "topo_screen"))
+                return e0.elapsed_time(e1) / 5, screen
+
+            times = {"generic": timed(lambda: s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=ga))}
+            same, compile_ms = True, {}
+            for lanes in (8, 16, 32):
+                topo = L.links_topo_create(s.ctx, int(batch.n_joints[0]), batch.adj[0], batch.jtype[0], lanes)
+                try:
+                    times[f"lanes{lanes}"] = timed(
+                        lambda: s.simulate_topology(topo, T, L.OUT_VALID_ONLY, out=gb, n_escaped=esc))
+                    same = same and bool(torch.equal(ga.valid, gb.valid) and torch.equal(ga.lock_step, gb.lock_step)
+                                         and torch.equal(ga.min_disc.nan_to_num(-1.0), gb.min_disc.nan_to_num(-1.0)))
+                    info = L.links_topo_info(topo)
+                    compile_ms[lanes] = info["compile_ms"]
+                finally:
+                    L.links_topo_free(topo)
+        best = min((k for k in times if k != "generic"), key=lambda k: times[k][1])
+        rows.append({"joints": n, "dyads": info["dyads"], "samples": S, "valid": nv, "compile_ms": compile_ms,
+                     "ms_per_step_generic": times["generic"][0], "screen_ms_generic": times["generic"][1],
+                     "screen_ms_topology": {k: v[1] for k, v in times.items() if k != "generic"},
+                     "ms_per_step_topology_best": times[best][0], "best": best,
+                     "escaped": int(esc.item()), "same_flags_lock_min_disc": same})
+        del db, ga, gb, probe
+        torch.cuda.empty_cache()
+    return {"T": T, "rows": rows}
+
+
 def paper_generator_stage(args, local, stream):
     """The paper's own candidates (standardised positions, topology rules) for a sweep of
     joint counts: the valid rate (and random samples per valid candidate, the paper's
@@ -515,6 +582,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-paper-generator", action="store_true")
     ap.add_argument("--no-curation", action="store_true")
+    ap.add_argument("--no-topology", action="store_true")
+    ap.add_argument("--topology-samples", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=600_000)
@@ -774,6 +843,7 @@ def main():
     sv = None if args.no_serve or world > 1 else serve_stage(args, local, stream)
     pg = None if args.no_paper_generator or world > 1 else paper_generator_stage(args, local, stream)
     cu = None if args.no_curation or world > 1 else curation_stage(args, local, stream)
+    tp = None if args.no_topology or world > 1 else topology_stage(args, local, stream)
     cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -794,6 +864,7 @@ def main():
         "serve": sv,
         "paper_generator": pg,
         "curation": cu,
+        "topology_kernels": tp,
         "e2e": e2e,
         "e2e_full": e2e_full,
         "gpu_launches": int(launches * args.steps),

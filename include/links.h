@@ -249,25 +249,29 @@ LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, 
  * writes CUDA source for its solve path (joint positions and error bounds in
  * registers, parent slots as compile-time names), compiles it for sm_103a with NVRTC
  * and loads it on the context's device; synchronous (tens to hundreds of ms).
- * LINKS_EINVAL for bad sizes or a topology that does not plan (status in the text),
+ * lanes: steps of one mechanism computed side by side (a group of 8, 16 or 32 lanes;
+ * 0 = 16). 
+ * LINKS_EINVAL for bad sizes or lanes, or a topology that does not plan (status in the text),
  * LINKS_ECUDA if the compilation or the load fails. */
 LINKS_API int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t* adj, const int8_t* type,
-                                links_topo* out);
+                                int lanes, links_topo* out);
 /* The CUDA source links_topo_create compiles for that topology (host, no device
- * needed): NUL-terminated into buf (cap bytes, truncated if shorter), *len (may be
- * NULL) the size it needs including the NUL.  LINKS_EINVAL as links_topo_create. */
+ * needed; it includes the library's step.cuh, which the library embeds):
+ * NUL-terminated into buf (cap bytes, truncated if shorter), *len (may be NULL) the
+ * size it needs including the NUL.  LINKS_EINVAL as links_topo_create. */
 LINKS_API int links_topo_source(int n, int n_max, const uint8_t* adj, const int8_t* type, char* buf, size_t cap,
                                 size_t* len);
 /* Fixed joints and dyads of the compiled solve path, and the time create took. */
 LINKS_API int links_topo_info(links_topo topo, int* n_fixed, int* n_dyads, double* compile_ms);
 LINKS_API int links_topo_free(links_topo topo);
 /* links_simulate with precision LINKS_MIXED (same arguments and outputs), its screen
- * first run by the topology's kernel: mechanisms whose plan follows the compiled path
- * and whose FP32 bounds decide every step up to the first certain lock get their
- * flags, lock step and min_disc from it (the generic screen's values: the same
- * operations in the same order); the others (another topology, or an uncertain step)
- * go to the generic screen, *n_escaped (device int32, may be NULL) their count.
- * Compaction and emit follow as in links_simulate.  Asynchronous. */
+ * first run by the topology's kernel: every mechanism whose plan follows the compiled
+ * path gets its flags, lock step and min_disc from it (the generic screen's values:
+ * the same operations in the same order, uncertain steps decided by the same
+ * double-word chain); the others go to the generic screen, *n_escaped (device
+ * int32, may be NULL) their count.
+ * Compaction and emit follow as in links_simulate.  Asynchronous.  LINKS_EINVAL as
+ * links_simulate, or for a topology with more joints than the plan's n_max. */
 LINKS_API int links_simulate_topology(links_ctx ctx, links_plan plan, links_topo topo, int T, int out_mode,
                                       float* traj, float* path, uint8_t* valid, int16_t* lock_step,
                                       float* min_disc, int32_t* out_index, int64_t out_capacity,

@@ -39,6 +39,30 @@ def _deps():
                                                                  os.path.abspath(__file__)]
 
 
+# Device headers that the run-time compiled (topology-specialised) kernels include,
+# embedded in the library as string literals.
+EMBEDDED = ("dw_core.cuh", "step.cuh")
+
+
+def embed_headers():
+    out = ["// Generated by build.py from csrc/ headers: the run-time compiler's include files."]
+    for i, name in enumerate(EMBEDDED):
+        text = open(os.path.join(CSRC, name)).read()
+        if ')LINKSRAW"' in text:
+            raise RuntimeError(f"{name} contains the raw-string delimiter")
+        out.append(f'static const char kEmbeddedName{i}[] = "{name}";')
+        out.append(f'static const char kEmbeddedText{i}[] = R"LINKSRAW({text})LINKSRAW";')
+    out.append(f"static const int kEmbeddedCount = {len(EMBEDDED)};")
+    out.append("static const char* const kEmbeddedNames[] = {" +
+               ", ".join(f"kEmbeddedName{i}" for i in range(len(EMBEDDED))) + "};")
+    out.append("static const char* const kEmbeddedTexts[] = {" +
+               ", ".join(f"kEmbeddedText{i}" for i in range(len(EMBEDDED))) + "};")
+    path = os.path.join(OUT_DIR, "embedded_headers.inc")
+    text = "\n".join(out) + "\n"
+    if not os.path.exists(path) or open(path).read() != text:
+        open(path, "w").write(text)
+
+
 def up_to_date() -> bool:
     if not os.path.exists(LIB):
         return False
@@ -65,6 +89,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
             print(r.stdout, r.stderr)
         return obj
 
+    embed_headers()
+    flags = flags + ["-I", OUT_DIR]
     with ThreadPoolExecutor(max(1, min(8, os.cpu_count() or 1))) as ex:
         objs = list(ex.map(compile_one, sources()))
     tmp = LIB + f".tmp{os.getpid()}"

@@ -19,6 +19,7 @@
 //           mechanism of a work list sorted by dyad count.
 //   emit    every requested trajectory step in double-word arithmetic, written as
 //           float32 (one warp per output row, 32 consecutive steps per store).
+#include "step.cuh"
 #include "links_internal.cuh"
 #include "packed.cuh"
 
@@ -44,22 +45,6 @@ __device__ __forceinline__ void add_stat(int32_t* ctrs, int slot, unsigned v) {
     atomicAdd(reinterpret_cast<unsigned long long*>(ctrs + slot), (unsigned long long)v);
 }
 
-struct dwp {
-  dw x, y;
-};
-
-// Double-word chain of one step into loc[slot].  fix holds the fixed slots as
-// (x_h, x_l, y_h, y_l); with ABS the positions are absolute (fix absolute, the
-// actuated joint offset by the pivot), otherwise relative to the pivot.
-// Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
-// Inlined: as a call it cost the emit 12% (argument passing and saved registers
-// around it).
-struct LocLocal {  // thread-local array; the fixed slots are copied in
-  static constexpr bool kFixInLoc = true;
-  dwp* v;
-  __device__ dwp get(int s) const { return v[s]; }
-  __device__ void set(int s, const dwp& x) const { v[s] = x; }
-};
 struct LocShared {  // the lane's columns of shared slot arrays (x, y: 256 B per slot)
   static constexpr bool kFixInLoc = false;  // fixed slots stay in fix
   char* xb;
@@ -74,70 +59,6 @@ struct LocShared {  // the lane's columns of shared slot arrays (x, y: 256 B per
     *reinterpret_cast<float2*>(yb + s * 256) = make_float2(v.y.h, v.y.l);
   }
 };
-template <class Loc>
-__device__ __forceinline__ dwp slot_pos(const Loc& loc, const float4* fix, int nf, int s) {
-  if (!Loc::kFixInLoc && s < nf) {
-    const float4 f = fix[s];
-    return {{f.x, f.y}, {f.z, f.w}};
-  }
-  return loc.get(s);
-}
-
-template <bool ABS, class Loc>
-__device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
-                                         float4 csv, Loc loc, float* qmin) {
-  const int nf = h.nf, nd = h.nd;
-  if (Loc::kFixInLoc)
-    for (int s = 0; s < nf; ++s) {
-      float4 f = fix[s];
-      loc.set(s, {{f.x, f.y}, {f.z, f.w}});
-    }
-  dw c = {csv.x, csv.y}, s = {csv.z, csv.w};
-  dw ux = {h.ux_h, h.ux_l}, uy = {h.uy_h, h.uy_l};
-  dwp m = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
-  if (ABS) {
-    m.x = dw_add(m.x, dw{h.px_h, h.px_l});
-    m.y = dw_add(m.y, dw{h.py_h, h.py_l});
-  }
-  loc.set(nf, m);
-  float q = INFINITY;
-  for (int d = 0; d < nd; ++d) {
-    const float c_h = dy[d].r0.w, w2 = dy[d].r1.x;  // records in global or shared memory
-    const float4 r2 = dy[d].r2;
-    uint32_t sl = __float_as_uint(r2.w);
-    const dwp pi = slot_pos(loc, fix, nf, sl & 0xff), pj = slot_pos(loc, fix, nf, (sl >> 8) & 0xff);
-    dw dx = dw_sub(pj.x, pi.x), dy_ = dw_sub(pj.y, pi.y);
-    dw d2 = dw_sum_sq(dx, dy_);
-    dw e = dw_add(d2, dw{c_h, r2.z});
-    dw D = dw_4ab_minus_sq(d2, dw{r2.x, r2.y}, e);
-    if (!(dw_sign(D) > 0.0f)) {
-      *qmin = q;
-      return true;
-    }
-    q = fminf(q, __fdividef(D.h, w2 * w2));
-    dw sq = dw_sqrt(D);
-    dw hinv = dw_scale2(dw_rcp(d2), 0.5f);
-    dw a = dw_mul(e, hinv), bq = dw_mul(sq, hinv);
-    dwp pk;
-    pk.x = dw_axpby(pi.x, a, dx, bq, dy_, -1.0f);
-    pk.y = dw_axpby(pi.y, a, dy_, bq, dx, 1.0f);
-    loc.set(sl >> 24, pk);
-  }
-  *qmin = q;
-  return false;
-}
-
-__device__ __forceinline__ float min3(float a, float b, float c) {
-  float r;
-  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-propagating
-  float r;
-  asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-
 // One FP32 dyad of the screen for this lane.  Pb / Eb point at the lane's column of
 // the warp's slot arrays (positions, error bounds); the record holds byte offsets.
 // lockw = min over dyads of slack + bound (< 0: certainly locked), zmin = min of
@@ -151,31 +72,18 @@ __device__ __forceinline__ void fp32_dyad_rec(const float4& r0, const float4& r1
   const float2 pj = *reinterpret_cast<const float2*>(Pb + (oij >> 16));
   const float ei = *reinterpret_cast<const float*>(Eb + (oe & 0xffffu));
   const float ej = *reinterpret_cast<const float*>(Eb + (oe >> 16));
-  const float dx = pj.x - pi.x, dy = pj.y - pi.y;
-  const float d2 = fmaf(dx, dx, dy * dy);
-  const float rd = rsqrtf(d2);
-  const float dd = d2 * rd;
-  const float s2 = r0.y - dd, s3 = dd - r0.z;
-  const float D = ((dd + r0.y) * s2) * (s3 * (dd + r0.z));
-  const float rD = rsqrtf(D);
-  const float isg = r1.x * rD;
-  const float del = ei + ej + r1.y;
-  lockw = min3(lockw, s2 + del, s3 + del);
-  zmin = min3_nan(zmin, s2 - del, s3 - del);
-  isgmax = fmaxf(isgmax, isg);
-  const float hinv = 0.5f * (rd * rd);
-  const float a = (d2 + r0.w) * hinv, bq = (D * rD) * hinv;
-  const float kx = fmaf(a, dx, fmaf(-bq, dy, pi.x)), ky = fmaf(a, dy, fmaf(bq, dx, pi.y));
+  float kx, ky, ek;
+  fp32_dyad_core(pi.x, pi.y, pj.x, pj.y, ei, ej, r0, r1, lockw, zmin, isgmax, kx, ky, ek);
   *reinterpret_cast<float2*>(Pb + (ok & 0xffffu)) = make_float2(kx, ky);
-  const float ek = fmaf(del, isg, (kAddErr * kU) * (r0.y + (fabsf(kx) + fabsf(ky))));
   *reinterpret_cast<float*>(Eb + (ok >> 16)) = ek;
   if (EMAX) *emax = fmaxf(*emax, ek);
 }
 
-// The same dyad for two steps of one lane at once, in packed f32x2 arithmetic (each
-// result rounded as the scalar code rounds it, so both steps get the scalar values).
-// Slot layout: per slot and lane a float4 (x of both steps, y of both steps) at
-// P2 + 2 * (position offset), the two bounds at E2 + 2 * (bound offset).
+// The same dyad for two steps of one lane (the two-step slot layout: per slot and lane
+// a float4 (x of both steps, y of both steps) at P2 + 2 * (position offset), the two
+// bounds at E2 + 2 * (bound offset)), one record load serving both.  The arithmetic is
+// the scalar core twice: packed f32x2 arithmetic was measured to give other values at
+// near-singular steps (and so another minimum discriminant) for a 3% gain.
 __device__ __forceinline__ void fp32_dyad2(const float4& r0, const float4& r1, char* P2, char* E2, float* lockw,
                                            float* zmin, float* isgmax) {
   const uint32_t oij = __float_as_uint(r0.x), oe = __float_as_uint(r1.w), ok = __float_as_uint(r1.z);
@@ -183,35 +91,11 @@ __device__ __forceinline__ void fp32_dyad2(const float4& r0, const float4& r1, c
   const float4 pj = *reinterpret_cast<const float4*>(P2 + 2 * (oij >> 16));
   const float2 ei = *reinterpret_cast<const float2*>(E2 + 2 * (oe & 0xffffu));
   const float2 ej = *reinterpret_cast<const float2*>(E2 + 2 * (oe >> 16));
-  const f2 PIX = pk2(pi.x, pi.y), PIY = pk2(pi.z, pi.w);
-  const f2 DX = sub2(pk2(pj.x, pj.y), PIX), DY = sub2(pk2(pj.z, pj.w), PIY);
-  const f2 D2 = fma2(DX, DX, mul2(DY, DY));
-  const float2 d2 = up2(D2);
-  const f2 RD = pk2(rsqrtf(d2.x), rsqrtf(d2.y));
-  const f2 DD = mul2(D2, RD);
-  const f2 R12 = pk2(r0.y, r0.y), RM = pk2(r0.z, r0.z);
-  const f2 S2 = sub2(R12, DD), S3 = sub2(DD, RM);
-  const f2 D = mul2(mul2(add2(DD, R12), S2), mul2(S3, add2(DD, RM)));
-  const float2 dv = up2(D);
-  const f2 RDD = pk2(rsqrtf(dv.x), rsqrtf(dv.y));
-  const f2 ISG = mul2(pk2(r1.x, r1.x), RDD);
-  const f2 DEL = add2(add2(pk2(ei.x, ei.y), pk2(ej.x, ej.y)), pk2(r1.y, r1.y));
-  const float2 lo = up2(add2(S2, DEL)), hi = up2(add2(S3, DEL));
-  lockw[0] = min3(lockw[0], lo.x, hi.x);
-  lockw[1] = min3(lockw[1], lo.y, hi.y);
-  const float2 zl = up2(sub2(S2, DEL)), zh = up2(sub2(S3, DEL));
-  zmin[0] = min3_nan(zmin[0], zl.x, zh.x);
-  zmin[1] = min3_nan(zmin[1], zl.y, zh.y);
-  const float2 isg = up2(ISG);
-  isgmax[0] = fmaxf(isgmax[0], isg.x);
-  isgmax[1] = fmaxf(isgmax[1], isg.y);
-  const f2 HINV = mul2(pk2(0.5f, 0.5f), mul2(RD, RD));
-  const f2 A = mul2(add2(D2, pk2(r0.w, r0.w)), HINV), BQ = mul2(mul2(D, RDD), HINV);
-  const f2 KX = fma2(A, DX, fma2(neg2(BQ), DY, PIX)), KY = fma2(A, DY, fma2(BQ, DX, PIY));
-  const float2 kx = up2(KX), ky = up2(KY);
-  *reinterpret_cast<float4*>(P2 + 2 * (ok & 0xffffu)) = make_float4(kx.x, kx.y, ky.x, ky.y);
-  const f2 EK = fma2(DEL, ISG, mul2(pk2(kAddErr * kU, kAddErr * kU), add2(R12, add2(abs2(KX), abs2(KY)))));
-  *reinterpret_cast<float2*>(E2 + 2 * (ok >> 16)) = up2(EK);
+  float kx0, ky0, ek0, kx1, ky1, ek1;
+  fp32_dyad_core(pi.x, pi.z, pj.x, pj.z, ei.x, ej.x, r0, r1, lockw[0], zmin[0], isgmax[0], kx0, ky0, ek0);
+  fp32_dyad_core(pi.y, pi.w, pj.y, pj.w, ei.y, ej.y, r0, r1, lockw[1], zmin[1], isgmax[1], kx1, ky1, ek1);
+  *reinterpret_cast<float4*>(P2 + 2 * (ok & 0xffffu)) = make_float4(kx0, kx1, ky0, ky1);
+  *reinterpret_cast<float2*>(E2 + 2 * (ok >> 16)) = make_float2(ek0, ek1);
 }
 
 template <bool EMAX = false>
@@ -328,7 +212,9 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       isgmax[u] = 0.0f;
       const int t = chunk * CH + u * G + gl;
       const float4 csv = __ldg(cs + min(t, T - 1));
-      mpos[u] = make_float2(csv.x * ux - csv.z * uy, csv.z * ux + csv.x * uy);
+      // rounded intrinsics: the topology-specialised screens compute the same values
+      mpos[u] = make_float2(__fsub_rn(__fmul_rn(csv.x, ux), __fmul_rn(csv.z, uy)),
+                            __fadd_rn(__fmul_rn(csv.z, ux), __fmul_rn(csv.x, uy)));
     }
     if (has) {
       if (S == 2) {

@@ -6,14 +6,13 @@
 // joint's position and error bound live in registers of the lane that computes one
 // step, the dyads' parent slots are compile-time names, and each mechanism's link data
 // (R12, Rm, c, 2 r1 r2, the local error constant and which parent comes first) are
-// loaded into registers once per mechanism.  The arithmetic is that of the generic
-// screen's two-step form, operation for operation with round-to-nearest intrinsics (no
-// contraction), so a decided mechanism gets the generic screen's flags, lock step and
-// minimum discriminant.  A group of G lanes takes one mechanism, G consecutive steps at
-// a time; a mechanism whose plan does not follow the compiled path, or that meets an
-// uncertain step (neither certainly locked nor certainly free by the FP32 bounds)
-// before its first certain lock, is listed for the generic screen, which decides it
-// with its double-word rescue.
+// loaded into registers once per mechanism.  The dyad is the library's own FP32 core
+// (step.cuh, compiled into the same program), so a mechanism gets the generic
+// screen's flags, lock step and minimum discriminant.  A group of G lanes takes one mechanism, G consecutive steps at
+// a time; a step that the FP32 bounds leave uncertain (neither certainly locked nor
+// certainly free) is decided by the library's double-word chain (step.cuh), as in the
+// generic screen.  A mechanism whose plan does not
+// follow the compiled path is listed for the generic screen.
 #include <nvrtc.h>
 
 #include <algorithm>
@@ -25,11 +24,12 @@
 #include <string>
 #include <vector>
 
+#include "embedded_headers.inc"  // dw_core.cuh and step.cuh as text (written by build.py)
 #include "links_internal.cuh"
 
 struct links_topo_s {
   links_ctx ctx = nullptr;
-  int nf = 0, nd = 0, G = 16;
+  int n = 0, nf = 0, nd = 0, G = 16;
   std::vector<int> sa, sb;  // parent slots of each dyad, in the reference plan's order
   cudaLibrary_t lib = nullptr;  // the compiled kernel, loaded through the runtime
   cudaKernel_t fn = nullptr;
@@ -40,117 +40,132 @@ struct links_topo_s {
 namespace links {
 namespace {
 
-std::string topo_source(int nf, int nd, const std::vector<int>& sa, const std::vector<int>& sb, int G) {
+// The per-step part of the generated kernel: the lane's step of its group's mechanism
+// (slots in registers, the FP32 core per dyad, the double-word rescue of an uncertain
+// step), then the group's decisions for the chunk.
+std::string topo_source_step(int nf, int nd, const std::vector<int>& sa, const std::vector<int>& sb) {
   std::ostringstream o;
-  o << "typedef unsigned int u32;\n"
-       "struct Hdr { int status; unsigned char n, nd, nf, motor; unsigned char cs, pj, p0, p1;\n"
-       "  float ux_h, ux_l, uy_h, uy_l, px_h, px_l, py_h, py_l, bmax, e_motor, e_fixed, lbox; };\n"
-       "__device__ __forceinline__ float min3(float a, float b, float c) {\n"
-       "  float r; asm(\"min.f32 %0, %1, %2, %3;\" : \"=f\"(r) : \"f\"(a), \"f\"(b), \"f\"(c)); return r; }\n"
-       "__device__ __forceinline__ float min3_nan(float a, float b, float c) {\n"
-       "  float r; asm(\"min.NaN.f32 %0, %1, %2, %3;\" : \"=f\"(r) : \"f\"(a), \"f\"(b), \"f\"(c)); return r; }\n";
-  o << "#define G " << G << "\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(256) topo_screen(\n"
-       "    const Hdr* __restrict__ hdr, const float4* __restrict__ dyad, int max_dyads,\n"
-       "    const float4* __restrict__ fixpos, int n_max, const int* __restrict__ order,\n"
-       "    const int* __restrict__ hist, int T, const float4* __restrict__ cs,\n"
-       "    unsigned char* __restrict__ valid, short* __restrict__ lock_step, float* __restrict__ min_disc,\n"
-       "    int* __restrict__ esc, int* __restrict__ n_esc) {\n"
-       "  const int lane = threadIdx.x & 31, gl = lane % G, base = lane - gl;\n"
-       "  const u32 gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << base);\n"
-       "  int n_ok = hist[lane];\n"
-       "  for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(0xffffffffu, n_ok, o);\n"
-       "  const int ngroups = (int)(gridDim.x * blockDim.x / G);\n"
-       "  for (int item = (int)((blockIdx.x * blockDim.x + threadIdx.x) / G); item < n_ok; item += ngroups) {\n"
-       "    const int b = order[item];\n"
-       "    const Hdr h = hdr[b];\n"
-       "    bool match = h.nf == " << nf << " && h.nd == " << nd << ";\n";
-  for (int s = 0; s < nf; ++s)
-    o << "    const float4 f" << s << " = __ldg(fixpos + (long long)b * n_max + " << s << ");\n";
-  for (int d = 0; d < nd; ++d) {
-    const unsigned direct = (unsigned)sa[d] * 256u | ((unsigned)sb[d] * 256u) << 16;
-    const unsigned swapped = (unsigned)sb[d] * 256u | ((unsigned)sa[d] * 256u) << 16;
-    o << "    const float4 ra" << d << " = __ldg(dyad + ((long long)b * max_dyads + " << d << ") * 3);\n"
-      << "    const float4 rb" << d << " = __ldg(dyad + ((long long)b * max_dyads + " << d << ") * 3 + 1);\n"
-      << "    const bool sw" << d << " = __float_as_uint(ra" << d << ".x) == " << swapped << "u;\n"
-      << "    match = match && (sw" << d << " || __float_as_uint(ra" << d << ".x) == " << direct << "u);\n";
-  }
-  o << "    if (!match) {\n"
-       "      if (gl == 0) esc[atomicAdd(n_esc, 1)] = b;\n"
-       "      continue;\n"
-       "    }\n"
-       "    float qacc = __int_as_float(0x7f800000);\n"
-       "    for (int c0 = 0; c0 < T; c0 += G) {\n"
-       "      const int t = c0 + gl;\n"
-       "      const bool act = t < T;\n"
-       "      const float4 csv = __ldg(cs + (act ? t : T - 1));\n"
-       "      float lockw = __int_as_float(0x7f800000), zmin = lockw, isgmax = 0.0f;\n";
-  for (int s = 0; s < nf; ++s)
-    o << "      const float x" << s << " = f" << s << ".x, y" << s << " = f" << s << ".z, e" << s
+  for (int s2 = 0; s2 < nf; ++s2)
+    o << "      const float x" << s2 << " = f" << s2 << ".x, y" << s2 << " = f" << s2 << ".z, e" << s2
       << " = h.e_fixed;\n";
-  o << "      const float x" << nf << " = csv.x * h.ux_h - csv.z * h.uy_h, y" << nf
-    << " = csv.z * h.ux_h + csv.x * h.uy_h, e" << nf << " = h.e_motor;\n";
+  o << "      const float x" << nf << " = __fsub_rn(__fmul_rn(csv.x, h.ux_h), __fmul_rn(csv.z, h.uy_h)), y" << nf
+    << " = __fadd_rn(__fmul_rn(csv.z, h.ux_h), __fmul_rn(csv.x, h.uy_h)), e" << nf << " = h.e_motor;\n";
   for (int d = 0; d < nd; ++d) {
     const int k = nf + 1 + d, A = sa[d], Bq = sb[d];
     const std::string D = std::to_string(d);
     o << "      float x" << k << ", y" << k << ", e" << k << ";\n"
-      << "      {\n"
-      << "        const float pix = sw" << D << " ? x" << Bq << " : x" << A << ", piy = sw" << D << " ? y" << Bq
-      << " : y" << A << ";\n"
-      << "        const float pjx = sw" << D << " ? x" << A << " : x" << Bq << ", pjy = sw" << D << " ? y" << A
-      << " : y" << Bq << ";\n"
-      << "        const float ei = sw" << D << " ? e" << Bq << " : e" << A << ", ej = sw" << D << " ? e" << A
-      << " : e" << Bq << ";\n"
-      << "        const float R12 = ra" << D << ".y, Rm = ra" << D << ".z, C = ra" << D << ".w, W2 = rb" << D
-      << ".x, LO = rb" << D << ".y;\n"
-      << "        const float dx = __fsub_rn(pjx, pix), dy = __fsub_rn(pjy, piy);\n"
-      << "        const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));\n"
-      << "        const float rd = rsqrtf(d2);\n"
-      << "        const float dd = __fmul_rn(d2, rd);\n"
-      << "        const float s2 = __fsub_rn(R12, dd), s3 = __fsub_rn(dd, Rm);\n"
-      << "        const float D = __fmul_rn(__fmul_rn(__fadd_rn(dd, R12), s2), __fmul_rn(s3, __fadd_rn(dd, Rm)));\n"
-      << "        const float rD = rsqrtf(D);\n"
-      << "        const float isg = __fmul_rn(W2, rD);\n"
-      << "        const float del = __fadd_rn(__fadd_rn(ei, ej), LO);\n"
-      << "        lockw = min3(lockw, __fadd_rn(s2, del), __fadd_rn(s3, del));\n"
-      << "        zmin = min3_nan(zmin, __fsub_rn(s2, del), __fsub_rn(s3, del));\n"
-      << "        isgmax = fmaxf(isgmax, isg);\n"
-      << "        const float hinv = __fmul_rn(0.5f, __fmul_rn(rd, rd));\n"
-      << "        const float a = __fmul_rn(__fadd_rn(d2, C), hinv), bq = __fmul_rn(__fmul_rn(D, rD), hinv);\n"
-      << "        x" << k << " = __fmaf_rn(a, dx, __fmaf_rn(-bq, dy, pix));\n"
-      << "        y" << k << " = __fmaf_rn(a, dy, __fmaf_rn(bq, dx, piy));\n"
-      << "        e" << k << " = __fmaf_rn(del, isg, __fmul_rn(" << std::hexfloat << (kAddErr * kU)
-      << std::defaultfloat << "f, __fadd_rn(R12, __fadd_rn(fabsf(x" << k << "), fabsf(y" << k << ")))));\n"
-      << "      }\n";
+      << "      links::fp32_dyad_core(sw" << D << " ? x" << Bq << " : x" << A << ", sw" << D << " ? y" << Bq
+      << " : y" << A << ", sw" << D << " ? x" << A << " : x" << Bq << ", sw" << D << " ? y" << A << " : y" << Bq
+      << ", sw" << D << " ? e" << Bq << " : e" << A << ", sw" << D << " ? e" << A << " : e" << Bq << ", ra" << D
+      << ", rb" << D << ", lockw, zmin, isgmax, x" << k << ", y" << k << ", e" << k << ");\n";
   }
-  // the last slot's bound is not read by any dyad: keep the compiler quiet about it
-  o << "      (void)e" << nf + nd << ";\n";
-  o << "      const bool certain_lock = lockw < 0.0f;\n"
-       "      const bool amb = act && !certain_lock && !(zmin >= 0.0f);\n"
-       "      const float q = __fdividef(1.0f, isgmax * isgmax);\n"
-       "      const u32 lb = (__ballot_sync(gmask, act && certain_lock) & gmask) >> base;\n"
-       "      const u32 ab = (__ballot_sync(gmask, amb) & gmask) >> base;\n"
-       "      const int first = lb ? __ffs(lb) - 1 : G;\n"
-       "      const u32 before = first >= 32 ? 0xffffffffu : ((1u << first) - 1u);\n"
-       "      if (ab & before) {\n"
-       "        if (gl == 0) esc[atomicAdd(n_esc, 1)] = b;\n"
-       "        break;\n"
+  o << "      (void)e" << nf + nd << ";  // the last slot's bound feeds no dyad\n"
+       "      const bool certain_lock = lockw < 0.0f;\n"
+       "      q = __fdividef(1.0f, isgmax * isgmax);\n"
+       "      locked = act && certain_lock;\n"
+       "      if (act && !certain_lock && !(zmin >= 0.0f)) {  // uncertain: double-word decides\n"
+       "        links::dwp loc[" << nf + 1 + nd << "];\n"
+       "        float qd;\n"
+       "        locked = links::dw_chain<false>(h, fixpos + (long long)b * n_max, dyad + (long long)b * max_dyads,\n"
+       "                                        __ldg(cs + t), links::LocLocal{loc}, &qd);\n"
+       "        q = qd;\n"
        "      }\n"
-       "      if (act && gl < first) qacc = fminf(qacc, q);\n"
-       "      if (first < G || c0 + G >= T) {\n"
-       "        float qr = qacc;\n"
-       "        for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(gmask, qr, o));\n"
-       "        if (gl == 0) {\n"
-       "          valid[b] = first == G;\n"
-       "          lock_step[b] = (short)(first < G ? c0 + first : -1);\n"
-       "          min_disc[b] = qr;\n"
-       "        }\n"
-       "        break;\n"
+       "    }\n"
+       "    const u32 lb = (__ballot_sync(full, locked) >> base) & (G == 32 ? full : ((1u << G) - 1u));\n"
+       "    const int first = lb ? __ffs(lb) - 1 : G;\n"
+       "    if (act && gl < first) qacc = fminf(qacc, q);\n"
+       "    const bool done = has && (first < G || c0 + G >= T);\n"
+       "    float qr = qacc;\n"
+       "    for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(full, qr, o));\n"
+       "    if (done) {\n"
+       "      if (gl == 0) {\n"
+       "        valid[b] = first == G;\n"
+       "        lock_step[b] = (short)(first < G ? c0 + first : -1);\n"
+       "        min_disc[b] = qr;\n"
        "      }\n"
+       "      item = -1;\n"
+       "    } else if (has) {\n"
+       "      c0 += G;\n"
        "    }\n"
        "  }\n"
        "}\n";
   return o.str();
+}
+
+std::string topo_source(int nf, int nd, const std::vector<int>& sa, const std::vector<int>& sb, int G) {
+  std::ostringstream o;
+  const int ns = nf + 1 + nd;
+  o << "#include \"step.cuh\"\n"
+       "typedef unsigned int u32;\n"
+       "#define G " << G << "\n"
+       "extern \"C\" __global__ void __launch_bounds__(256) topo_screen(\n"
+       "    const links::MechHdr* __restrict__ hdr, const links::DyadRec* __restrict__ dyad, int max_dyads,\n"
+       "    const float4* __restrict__ fixpos, int n_max, const int* __restrict__ order,\n"
+       "    const int* __restrict__ hist, int* __restrict__ work, int T, const float4* __restrict__ cs,\n"
+       "    unsigned char* __restrict__ valid, short* __restrict__ lock_step, float* __restrict__ min_disc,\n"
+       "    int* __restrict__ esc, int* __restrict__ n_esc) {\n"
+       "  const u32 full = 0xffffffffu;\n"
+       "  const int lane = threadIdx.x & 31, gl = lane % G, g = lane / G, base = g * G;\n"
+       "  int n_ok = hist[lane];\n"
+       "  for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(full, n_ok, o);\n"
+       "  int qhead = 0, qend = 0, item = -1, c0 = 0, b = 0;\n"
+       "  bool exhausted = false;\n"
+       "  float qacc = 0.0f;\n"
+       "  links::MechHdr h = {};\n";
+  for (int s2 = 0; s2 < nf; ++s2) o << "  float4 f" << s2 << " = {};\n";
+  for (int d = 0; d < nd; ++d) o << "  float4 ra" << d << " = {}, rb" << d << " = {};\n  bool sw" << d << " = false;\n";
+  // the warp advances all its groups one chunk per iteration (converged); idle groups
+  // take the next mechanisms of a batch the warp claims from the shared work counter
+  o << "  while (true) {\n"
+       "    u32 need = __ballot_sync(full, gl == 0 && item < 0);\n"
+       "    bool fresh = false;\n"
+       "    while (need) {\n"
+       "      if (qhead >= qend) {\n"
+       "        if (exhausted) break;\n"
+       "        int bs = 0;\n"
+       "        if (lane == 0) bs = atomicAdd(work, 32);\n"
+       "        bs = __shfl_sync(full, bs, 0);\n"
+       "        if (bs >= n_ok) { exhausted = true; break; }\n"
+       "        qhead = bs;\n"
+       "        qend = min(bs + 32, n_ok);\n"
+       "      }\n"
+       "      const int leader = __ffs(need) - 1;\n"
+       "      need &= need - 1;\n"
+       "      if (g == leader / G) { item = qhead; fresh = true; }\n"
+       "      ++qhead;\n"
+       "    }\n"
+       "    if (__ballot_sync(full, item >= 0) == 0) break;\n";
+  o << "    if (fresh) {\n"
+       "      b = order[item];\n"
+       "      h = hdr[b];\n"
+       "      bool match = h.nf == " << nf << " && h.nd == " << nd << ";\n";
+  for (int s2 = 0; s2 < nf; ++s2)
+    o << "      f" << s2 << " = __ldg(fixpos + (long long)b * n_max + " << s2 << ");\n";
+  for (int d = 0; d < nd; ++d) {
+    const unsigned direct = (unsigned)sa[d] * 256u | ((unsigned)sb[d] * 256u) << 16;
+    const unsigned swapped = (unsigned)sb[d] * 256u | ((unsigned)sa[d] * 256u) << 16;
+    o << "      ra" << d << " = __ldg(&dyad[(long long)b * max_dyads + " << d << "].r0);\n"
+      << "      rb" << d << " = __ldg(&dyad[(long long)b * max_dyads + " << d << "].r1);\n"
+      << "      sw" << d << " = __float_as_uint(ra" << d << ".x) == " << swapped << "u;\n"
+      << "      match = match && (sw" << d << " || __float_as_uint(ra" << d << ".x) == " << direct << "u);\n";
+  }
+  o << "      c0 = 0;\n"
+       "      qacc = __int_as_float(0x7f800000);\n"
+       "      if (!match) {  // another solve path: the generic screen takes it\n"
+       "        if (gl == 0) esc[atomicAdd(n_esc, 1)] = b;\n"
+       "        item = -1;\n"
+       "      }\n"
+       "    }\n"
+       "    const bool has = item >= 0;\n"
+       "    const int t = c0 + gl;\n"
+       "    const bool act = has && t < T;\n"
+       "    bool locked = false;\n"
+       "    float q = 0.0f;\n"
+       "    if (has) {\n"
+       "      const float4 csv = __ldg(cs + (t < T ? t : T - 1));\n"
+       "      float lockw = __int_as_float(0x7f800000), zmin = lockw, isgmax = 0.0f;\n";
+  (void)ns;
+  return o.str() + topo_source_step(nf, nd, sa, sb);
 }
 
 // Plans the topology (positions on a spiral: the solve path does not depend on them)
@@ -214,11 +229,15 @@ extern "C" int links_topo_source(int n, int n_max, const uint8_t* adj, const int
 }
 
 extern "C" int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t* adj, const int8_t* type,
-                                 links_topo* out) {
+                                 int lanes, links_topo* out) {
   if (!ctx || !out) return set_error(LINKS_EINVAL, "links_topo_create: NULL ctx or out");
   *out = nullptr;
+  if (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)
+    return set_error(LINKS_EINVAL, "links_topo_create: lanes must be 0, 8, 16 or 32");
   links_topo t = new links_topo_s();
+  t->G = lanes ? lanes : 16;
   t->ctx = ctx;
+  t->n = n;
   const int pst = plan_topology(n, n_max, adj, type, &t->nf, &t->nd, &t->sa, &t->sb, "links_topo_create");
   if (pst) {
     delete t;
@@ -227,7 +246,8 @@ extern "C" int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t*
   const auto t0 = std::chrono::steady_clock::now();
   const std::string src = topo_source(t->nf, t->nd, t->sa, t->sb, t->G);
   nvrtcProgram prog;
-  if (nvrtcCreateProgram(&prog, src.c_str(), "topo_screen.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+  if (nvrtcCreateProgram(&prog, src.c_str(), "topo_screen.cu", kEmbeddedCount, kEmbeddedTexts, kEmbeddedNames) !=
+      NVRTC_SUCCESS) {
     delete t;
     return set_error(LINKS_ECUDA, "links_topo_create: nvrtcCreateProgram failed");
   }
@@ -292,6 +312,8 @@ extern "C" int links_simulate_topology(links_ctx ctx, links_plan plan, links_top
   if (plan->ctx != ctx || topo->ctx != ctx)
     return set_error(LINKS_EINVAL, "links_simulate_topology: plan or topo belongs to another context");
   if (T < 1 || T > LINKS_MAX_T) return set_error(LINKS_EINVAL, "links_simulate_topology: T out of [1, 32767]");
+  if (topo->n > plan->d.n_max)  // the kernel reads the compiled path's rows of each mechanism's plan
+    return set_error(LINKS_EINVAL, "links_simulate_topology: the topology has more joints than the plan's n_max");
   if (out_mode != LINKS_OUT_FULL && out_mode != LINKS_OUT_VALID_ONLY)
     return set_error(LINKS_EINVAL, "links_simulate_topology: unknown out_mode");
   if (plan->B > 0 && (!valid || !lock_step || !min_disc))
@@ -310,9 +332,11 @@ extern "C" int links_simulate_topology(links_ctx ctx, links_plan plan, links_top
     if (pl->B == 0) return (int)LINKS_OK;
     const float4* dy = reinterpret_cast<const float4*>(p.dyad);
     const int32_t* hist = p.ctrs + kHist;
+    int32_t* work = p.ctrs + kWork;
     int32_t* n_esc = p.ctrs + kNConfirm;
     int max_dyads = p.max_dyads, n_max = p.n_max, Tv = tb->T;
-    void* args[] = {&p.hdr, &dy, &max_dyads, &p.fixpos, &n_max, &p.order, &hist, &Tv,
+    LINKS_CUDA(cudaMemsetAsync(work, 0, sizeof(int32_t), c->stream));
+    void* args[] = {&p.hdr, &dy, &max_dyads, &p.fixpos, &n_max, &p.order, &hist, &work, &Tv,
                     const_cast<float4**>(&tb->cs), &v, &ls, &md, &p.order2, &n_esc};
     KernelScope ks(c, "topo_screen");
     LINKS_CUDA(cudaLaunchKernel(reinterpret_cast<const void*>(topo->fn), dim3((unsigned)(c->num_sms * topo->per_sm)),

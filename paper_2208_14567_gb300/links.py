@@ -75,7 +75,7 @@ def lib():
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
             "links_curate_paths": ([P, i64, i32, i32, P, P, i64, P, P, P, ctypes.c_double, ctypes.c_double,
                                     ctypes.c_uint64, P, P, P, P, P, i64, P], i32),
-            "links_topo_create": ([P, i32, i32, P, P, P], i32),
+            "links_topo_create": ([P, i32, i32, P, P, i32, P], i32),
             "links_topo_info": ([P, P, P, P], i32),
             "links_topo_source": ([i32, i32, P, P, P, ctypes.c_size_t, P], i32),
             "links_topo_free": ([P], i32),
@@ -244,7 +244,7 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
 
 
-def links_topo_create(ctx, n: int, adj, jtype):
+def links_topo_create(ctx, n: int, adj, jtype, lanes: int = 0):
     """Compile the screen specialised to one topology: adj [n_max, n_max] uint8 and jtype [n_max]
     int8 of one mechanism with n joints (numpy, host).  Returns the handle."""
     import numpy as np
@@ -252,7 +252,8 @@ def links_topo_create(ctx, n: int, adj, jtype):
     t = np.ascontiguousarray(jtype, dtype=np.int8)
     h = ctypes.c_void_p()
     _check(lib().links_topo_create(ctx, int(n), int(a.shape[0]), a.ctypes.data_as(ctypes.c_void_p),
-                                   t.ctypes.data_as(ctypes.c_void_p), ctypes.byref(h)), "links_topo_create")
+                                   t.ctypes.data_as(ctypes.c_void_p), int(lanes), ctypes.byref(h)),
+           "links_topo_create")
     return h
 
 

@@ -69,12 +69,13 @@ def test_topology_source_compiles():
     for n in (6, 12):
         b = I.paper_topologies(2, n, seed=n)
         src = links.links_topo_source(int(b.n_joints[0]), b.adj[0], b.jtype[0])
-        assert "topo_screen" in src and src.count("rsqrtf(d2)") == int(n - 2 - (b.jtype[0] == 0).sum() + 1)
+        assert "topo_screen" in src and src.count("fp32_dyad_core(") == int(n - 2 - (b.jtype[0] == 0).sum() + 1)
         with tempfile.TemporaryDirectory() as d:
             p = f"{d}/t.cu"
             open(p, "w").write(src)
-            r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-c", p, "-o", f"{d}/t.o"],
-                               capture_output=True, text=True)
+            csrc = os.path.join(os.path.dirname(os.path.abspath(links.__file__)), "csrc")
+            r = subprocess.run([nvcc, "-gencode", "arch=compute_103a,code=sm_103a", "-I", csrc, "-c", p, "-o",
+                                f"{d}/t.o"], capture_output=True, text=True)
             assert r.returncode == 0, r.stderr[-2000:]
     with pytest.raises(links.LinksError):
         links.links_topo_source(6, np.zeros((6, 6), np.uint8), np.array([0, 2, 1, 1, 1, 1], np.int8))
