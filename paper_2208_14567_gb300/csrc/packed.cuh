@@ -1,6 +1,9 @@
 // packed.cuh -- packed float pairs (sm_100+ f32x2 arithmetic): one instruction computes
-// two independent single-precision results, each rounded as the scalar operation would
-// be (round to nearest even; denormals kept).
+// two independent single-precision results, rounded to nearest even.  A dyad chain
+// evaluated with these and the same chain in scalar round-to-nearest intrinsics were
+// measured to differ at near-singular steps, so code whose values must equal another
+// kernel's bit for bit uses the scalar forms; the path kernels use these for speed and
+// compare only values computed the same way.
 #pragma once
 
 namespace links {
