@@ -185,11 +185,14 @@ __device__ __forceinline__ void farthest_pair(const float2 (&p)[PL], const float
   if (ba == INT32_MAX) ba = 0;
   const float2 A = sp[ba];
   bb = INT32_MAX;
+  const f2 AX = pk2(A.x, A.x), AY = pk2(A.y, A.y);
 #pragma unroll
-  for (int i = PL - 1; i >= 0; --i) {
-    const int v = lane + 32 * i;
-    const float dx = p[i].x - A.x, dy = p[i].y - A.y;
-    if (v > ba && v < T && fmaf(dx, dx, dy * dy) == best) bb = v;
+  for (int k = PL / 2 - 1; k >= 0; --k) {  // the first pass's packed operations, v - u
+    const f2 dx = sub2(UX[k], AX), dy = sub2(UY[k], AY);
+    const float2 d2 = up2(fma2(dx, dx, mul2(dy, dy)));
+    const int v0 = lane + 64 * k, v1 = v0 + 32;
+    if (v1 > ba && v1 < T && d2.y == best) bb = v1;
+    if (v0 > ba && v0 < T && d2.x == best) bb = v0;
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) bb = min(bb, __shfl_xor_sync(kFull, bb, o));
