@@ -565,6 +565,50 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def profile_kernels(args):
+    """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
+    (no timing): plan build, screen and emit of args.batch 6-8-joint candidates; max-line
+    normalisation of their valid coupler paths; curation of their trajectories; a first-3
+    scan of 16 queries over those paths; the screen compiled for one topology of the
+    paper's generator on args.batch samples."""
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T, B = args.T, args.batch
+    dev = torch.device("cuda", 0)
+    batch = I.dyad_batch(B, 6, 8, seed=0)
+    db = to_device(batch, dev)
+    with Simulator(B, 8) as s:
+        s.build(db)
+        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=True, path=True, out_capacity=B // 3)
+        s.sync()
+        nv = min(int(o.n_out[0]), B // 3)
+        paths, traj, rows = o.path[:nv], o.traj[:nv], o.out_index[:nv]
+        ml = torch.empty_like(paths)
+        L.links_normalize_maxline(s.ctx, paths, ml)
+        flags = torch.empty((nv, 8), dtype=torch.uint8, device=dev)
+        nk = torch.empty(1, dtype=torch.int32, device=dev)
+        L.links_curate_paths(s.ctx, traj, rows, db.n_joints, db.adj, db.jtype, flags, nk)
+        q = ml[:16].clone()
+        order = torch.randperm(nv, generator=torch.Generator().manual_seed(5)).to(torch.int32).to(dev)
+        idx = torch.empty((16, 3), dtype=torch.int32, device=dev)
+        dist = torch.empty((16, 3), dtype=torch.float32, device=dev)
+        L.links_chamfer_first_under(s.ctx, q, ml, order, 0.03, 3, idx, dist)
+        s.sync()
+    pb = I.paper_batch(1, B, 8, seed=108)
+    with Simulator(pb.B, 8) as s:
+        s.build(to_device(pb, dev))
+        topo = L.links_topo_create(s.ctx, int(pb.n_joints[0]), pb.adj[0], pb.jtype[0], 16)
+        try:
+            s.simulate_topology(topo, T, L.OUT_VALID_ONLY, traj=False, path=False)
+            s.sync()
+        finally:
+            L.links_topo_free(topo)
+    print(json.dumps({"profile_kernels": "done", "batch": B, "valid_rows": nv}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -588,7 +632,11 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=600_000)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB of device arena")
+    ap.add_argument("--profile-kernels", action="store_true",
+                    help="launch each hot kernel once on a mid-size case (for a profiler) and exit")
     args = ap.parse_args()
+    if args.profile_kernels:
+        return profile_kernels(args)
     args.warmup = max(args.warmup, 3)
     world, rank, local = dist_setup()
     if args.impl == "reference":
@@ -704,8 +752,8 @@ def main():
     roof = dict(tv.get(bind, {}))
     # DRAM bytes per launch from the committed ncu capture of the same kernels
     # (300,000 candidates; 74,163 valid rows), scaled by the units this launch processed
-    per_unit = {"mixed_emit": (1053.9e6 / 74163, rows), "mixed_screen": (142.2e6 / 300000, B),
-                "plan_build": (158.7e6 / 300000, B)}
+    per_unit = {"mixed_emit": (1053.7e6 / 74163, rows), "mixed_screen": (141.7e6 / 300000, B),
+                "plan_build": (158.2e6 / 300000, B)}
     traffic = per_unit[top][0] * per_unit[top][1] if top in per_unit else None
     roof.update({"traffic": traffic, "traffic_source": "ncu dram bytes of a 300k-candidate capture, scaled",
                  "kernel": top, "peak_source": pk["src"]})
