@@ -250,7 +250,7 @@ LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, 
  * registers, parent slots as compile-time names), compiles it for sm_103a with NVRTC
  * and loads it on the context's device; synchronous (tens to hundreds of ms).
  * lanes: steps of one mechanism computed side by side (a group of 8, 16 or 32 lanes;
- * 0 = 16). 
+ * 0 chooses by the number of dyads: up to 3 -> 8, up to 6 -> 16, more -> 32). 
  * LINKS_EINVAL for bad sizes or lanes, or a topology that does not plan (status in the text),
  * LINKS_ECUDA if the compilation or the load fails. */
 LINKS_API int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t* adj, const int8_t* type,

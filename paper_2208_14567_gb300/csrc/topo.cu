@@ -235,7 +235,7 @@ extern "C" int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t*
   if (lanes != 0 && lanes != 8 && lanes != 16 && lanes != 32)
     return set_error(LINKS_EINVAL, "links_topo_create: lanes must be 0, 8, 16 or 32");
   links_topo t = new links_topo_s();
-  t->G = lanes ? lanes : 16;
+  t->G = lanes;
   t->ctx = ctx;
   t->n = n;
   const int pst = plan_topology(n, n_max, adj, type, &t->nf, &t->nd, &t->sa, &t->sb, "links_topo_create");
@@ -243,6 +243,10 @@ extern "C" int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t*
     delete t;
     return pst;
   }
+  // default group size by path length (measured on 1M samples of one topology, T = 200:
+  // 3 dyads fastest at 8 lanes, 5 at 16, 9 at 32): longer paths keep more registers per
+  // lane, and wider groups then keep enough steps in flight
+  if (t->G == 0) t->G = t->nd <= 3 ? 8 : (t->nd <= 6 ? 16 : 32);
   const auto t0 = std::chrono::steady_clock::now();
   const std::string src = topo_source(t->nf, t->nd, t->sa, t->sb, t->G);
   nvrtcProgram prog;
