@@ -255,7 +255,7 @@ LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, 
  * LINKS_ECUDA if the compilation or the load fails. */
 LINKS_API int links_topo_create(links_ctx ctx, int n, int n_max, const uint8_t* adj, const int8_t* type,
                                 int lanes, links_topo* out);
-/* The CUDA source links_topo_create compiles for that topology (host, no device
+/* The CUDA source links_topo_create compiles for that topology with lanes = 0 (host, no device
  * needed; it includes the library's step.cuh, which the library embeds):
  * NUL-terminated into buf (cap bytes, truncated if shorter), *len (may be NULL) the
  * size it needs including the NUL.  LINKS_EINVAL as links_topo_create. */

@@ -218,7 +218,7 @@ extern "C" int links_topo_source(int n, int n_max, const uint8_t* adj, const int
   std::vector<int> sa, sb;
   const int st = plan_topology(n, n_max, adj, type, &nf, &nd, &sa, &sb, "links_topo_source");
   if (st) return st;
-  const std::string src = topo_source(nf, nd, sa, sb, 16);
+  const std::string src = topo_source(nf, nd, sa, sb, nd <= 3 ? 8 : (nd <= 6 ? 16 : 32));  // the default lanes
   if (len) *len = src.size() + 1;
   if (buf && cap > 0) {
     const size_t m = std::min(cap - 1, src.size());
