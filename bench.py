@@ -37,7 +37,7 @@ WORKLOAD = ("1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U
             "mixed precision, valid-only trajectories + paths + flags")
 SM_COUNT = 152
 FP32_LANES_PER_CLK_SM = 128  # FP32 pipe lanes per SM per clock (an FMA is one op)
-# Algorithmic FP32 operation counts of the formulations (kernels and rooflines):
+# Algorithmic FP32 operation counts of the formulations (an FMA is one op, a MUFU op is one op):
 DW_DYAD_OPS = 221      # one double-word dyad (sub, squares, D, sqrt, reciprocal, update)
 DW_STEP_OPS = 72       # double-word crank rotation and pivot offset, per step
 SCREEN_DYAD_OPS = 35   # one certified FP32 dyad (product-form D, bounds, update)

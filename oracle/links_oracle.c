@@ -24,7 +24,7 @@
  *     the bidirectional chamfer distance (Sec. "A Case Study of Mechanism
  *     Retrieval").
  *
- * Readings where the paper is silent (each is restated in the design doc):
+ * Readings where the paper is silent:
  *   - the crank pivot is the lowest-index fixed neighbour of the actuated joint;
  *   - among unknown joints with >= 2 known neighbours, the lowest index is solved
  *     first; its two known neighbours are its parents i < j; > 2 known
