@@ -3,7 +3,7 @@
 Curves are coupler paths of valid four-bars simulated by the oracle (never by the
 CUDA path), under random similarity transforms, plus degenerate cases.
 
-Tolerances (restated in DESIGN.md):
+Tolerances:
   * normalise: |gpu - oracle| <= 2e-5 (curves have unit RMS radius) where the
     oracle's principal-axis gap (lambda1 - lambda2)/(lambda1 + lambda2) >= 1e-3 and
     |mean x^3| >= 1e-3; otherwise (axis or sign ill-determined) the per-point radii

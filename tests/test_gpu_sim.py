@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (restated in the design doc):
+Tolerances:
   * plan: statuses, solve order and parents bit-exact; lengths within 1e-14 relative;
     host and device builders bit-identical;
   * valid / lock_step: identical, except mechanisms whose oracle margin indicator
