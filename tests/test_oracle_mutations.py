@@ -88,3 +88,63 @@ def test_pins_catch_mutant(name, tmp_path):
 def test_unmutated_oracle_passes_all(tmp_path):
     lib = O.compile_variant(O.source(), os.path.join(str(tmp_path), "same.so"))
     assert run_pins(lib) == []
+
+
+# Mistakes planted in the oracle's Python functions (the paper's retrieval and curation,
+# and the keep draws' generator): the function's source with one replacement, run in
+# the oracle module's namespace, must fail one of the pins that cover it.
+PY_MUTANTS = {
+    "scan in index order": ("first_under", "hits = order[dist[order] < threshold][:k]",
+                            "hits = np.sort(order[dist[order] < threshold])[:k]"),
+    "cut-off inclusive": ("first_under", "hits = order[dist[order] < threshold][:k]",
+                          "hits = order[dist[order] <= threshold][:k]"),
+    "arc when linked to any joint": ("curate_paths", "arc = any(batch.adj[b, j, k] and batch.jtype[b, k] == 0 for k in range(n))",
+                                     "arc = any(batch.adj[b, j, k] for k in range(n))"),
+    "circle test reversed": ("curate_paths", "circle = var[0] < circle_var", "circle = var[0] > circle_var"),
+    "arcs and circles always kept": ("curate_paths", "kept = not (arc or circle) or u < keep_rate",
+                                     "kept = not (arc or circle) or u <= 1.0"),
+    "generator constant": ("splitmix64", "0xBF58476D1CE4E5B9", "0xBF58476D1CE4E5B7"),
+}
+
+
+def _mutated_oracle(fn_name, old, new):
+    import inspect
+    import types
+    src = inspect.getsource(getattr(O, fn_name))
+    assert src.count(old) == 1, (fn_name, old)
+    ns = dict(vars(O))
+    exec(compile(src.replace(old, new), f"<mutant {fn_name}>", "exec"), ns)
+    mod = types.SimpleNamespace(**{k: v for k, v in vars(O).items() if not k.startswith("__")})
+    setattr(mod, fn_name, ns[fn_name])
+    # functions that call the mutated one must see it too
+    for name in ("chamfer_first_under", "curate_paths"):
+        if name != fn_name:
+            f = ns[name] if name in ns else getattr(O, name)
+            g = types.FunctionType(f.__code__, ns, f.__name__, f.__defaults__, f.__closure__)
+            setattr(mod, name, g)
+    ns.update({fn_name: ns[fn_name]})
+    return mod
+
+
+@pytest.mark.parametrize("name", sorted(PY_MUTANTS))
+def test_pins_catch_python_mutant(name):
+    fn_name, old, new = PY_MUTANTS[name]
+    mod = _mutated_oracle(fn_name, old, new)
+    checks = [lambda: pins.test_first_under_scan_order(mod), lambda: pins.test_curation_flags(mod),
+              lambda: pins.test_splitmix64_published_outputs(mod)]
+    caught = 0
+    for c in checks:
+        try:
+            c()
+        except AssertionError:
+            caught += 1
+    assert caught > 0, f"no pin catches the mutant '{name}'"
+
+
+def test_python_mutation_harness_control():
+    """The unmutated functions, run through the same harness, pass every pin."""
+    for fn_name, old, _ in PY_MUTANTS.values():
+        mod = _mutated_oracle(fn_name, old, old)
+        pins.test_first_under_scan_order(mod)
+        pins.test_curation_flags(mod)
+        pins.test_splitmix64_published_outputs(mod)
