@@ -421,3 +421,36 @@ def test_curation_bad_row_and_sizes(L, ctx):
     with pytest.raises(L.LinksError):
         L.links_curate_paths(ctx, traj, rows, dev(batch.n_joints.astype(np.int32)), dev(batch.adj),
                              dev(batch.jtype), flags, nk, circle_var=float("nan"))
+
+
+def test_curation_and_scan_edge_cases(L, ctx):
+    """Empty inputs and one-point paths: no rows curate to nothing; paths of one point are
+    circles of variance 0 (the oracle agrees); a scan with no queries or a k larger than
+    the database returns -1 past the hits."""
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    batch = I.dyad_batch(16, 6, 6, seed=4)
+    nk = torch.full((1,), 7, dtype=torch.int32, device="cuda")
+    empty = torch.empty((0, 6, 5, 2), dtype=torch.float32, device="cuda")
+    L.links_curate_paths(ctx, empty, None, dev(batch.n_joints.astype(np.int32)), dev(batch.adj), dev(batch.jtype),
+                         torch.empty((0, 6), dtype=torch.uint8, device="cuda"), nk)
+    L.links_sync(ctx)
+    assert int(nk.item()) == 0
+    res = O.simulate(batch, 1, traj=True, path=False)
+    traj = res.traj.astype(np.float32)
+    flags = torch.empty((16, 6), dtype=torch.uint8, device="cuda")
+    cv = torch.empty((16, 6), dtype=torch.float32, device="cuda")
+    L.links_curate_paths(ctx, dev(traj), None, dev(batch.n_joints.astype(np.int32)), dev(batch.adj),
+                         dev(batch.jtype), flags, nk, circ_var=cv, keep_rate=0.0)
+    L.links_sync(ctx)
+    ref = O.curate_paths(traj.astype(np.float64), None, batch, keep_rate=0.0)
+    f = flags.cpu().numpy()
+    assert np.array_equal(f, ref["flags"])
+    assert (cv.cpu().numpy() == 0).all() and ((f & 1) == 0).sum() + ((f & 4) != 0).sum() == f.size
+    T = 20
+    db = O.normalize(coupler_curves(5, T, seed=8)).astype(np.float32)
+    q = db[:2].copy()
+    idx, dist = gpu_first(L, ctx, q, db, np.arange(5), float("inf"), 8)
+    assert np.array_equal(idx[:, :5], np.tile(np.arange(5), (2, 1))) and (idx[:, 5:] == -1).all()
+    assert np.isinf(dist[:, 5:]).all()
+    idx, dist = gpu_first(L, ctx, q[:0], db, np.arange(5), 1.0, 3)
+    assert idx.shape == (0, 3)

@@ -93,3 +93,19 @@ def test_dyad_workload_and_bad_topology(L):
             L.links_topo_create(s.ctx, 6, adj, jt)
         with pytest.raises(L.LinksError):
             L.links_topo_create(s.ctx, int(batch.n_joints[0]), batch.adj[0], batch.jtype[0], 12)
+
+
+def test_topology_plan_mismatch_refused(L):
+    """A topology with more joints than the plan's n_max is refused (its kernel would read
+    past the plan's rows)."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    small = I.paper_batch(1, 64, 6, seed=1)
+    big = I.paper_batch(1, 4, 8, seed=2)
+    with Simulator(small.B, small.nmax) as s:
+        s.build(to_device(small))
+        topo = L.links_topo_create(s.ctx, int(big.n_joints[0]), big.adj[0], big.jtype[0])
+        try:
+            with pytest.raises(L.LinksError):
+                s.simulate_topology(topo, 50, L.OUT_FULL)
+        finally:
+            L.links_topo_free(topo)
