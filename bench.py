@@ -913,6 +913,15 @@ def main():
         "paper_generator": pg,
         "curation": cu,
         "topology_kernels": tp,
+        # the paper's own figures (Table 1 and its summary of the solver), other hardware and an
+        # unstated step count: context only, never a ratio target
+        "paper_context": {
+            "speedup_quoted": "~800x: 454.864 s single-thread non-vectorised vs 0.5557 s on one 80-thread "
+                              "CPU node, 10,000 mechanisms",
+            "v100_seconds_per_10k": 0.1823,
+            "v100_mech_steps_per_s_if_T200": 10000 * 200 / 0.1823,
+            "this_run_over_that": value / (10000 * 200 / 0.1823),
+        },
         "e2e": e2e,
         "e2e_full": e2e_full,
         "gpu_launches": int(launches * args.steps),
