@@ -7,12 +7,13 @@
 // step, the dyads' parent slots are compile-time names, and each mechanism's link data
 // (R12, Rm, c, 2 r1 r2, the local error constant and which parent comes first) are
 // loaded into registers once per mechanism.  The dyad is the library's own FP32 core
-// (step.cuh, compiled into the same program), so a mechanism gets the generic
-// screen's flags, lock step and minimum discriminant.  A group of G lanes takes one mechanism, G consecutive steps at
-// a time; a step that the FP32 bounds leave uncertain (neither certainly locked nor
-// certainly free) is decided by the library's double-word chain (step.cuh), as in the
-// generic screen.  A mechanism whose plan does not
-// follow the compiled path is listed for the generic screen.
+// and an uncertain step (neither certainly locked nor certainly free by the FP32
+// bounds) is decided by the library's double-word chain (both in step.cuh, compiled
+// into the same program), so every mechanism gets the generic screen's flags, lock
+// step and minimum discriminant.  As in the generic screen, a group of G lanes takes
+// one mechanism, G consecutive steps at a time; a warp advances its groups together
+// and refills idle groups from batches of the work list.  A mechanism whose plan does
+// not follow the compiled path is listed for the generic screen.
 #include <nvrtc.h>
 
 #include <algorithm>
