@@ -242,9 +242,9 @@ LINKS_API int links_chamfer_topk(links_ctx ctx, int Q, int64_t M, int T, const f
 LINKS_API int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* queries,
                                         const float* db, int64_t L, const int32_t* order, double threshold,
                                         int k, int32_t* idx, float* dist);
-/* ---- Topology-specialised screen (the paper's solver specific to one topology, Sec.
- * "Graphical Simulator": the solve path is found once and serves every position
- * sample).  links_topo_create plans the topology given by one mechanism's n joints,
+/* ---- Topology-specialised screen (Sec. "Computational Cost of Simulations": the paper
+ * vectorises its solver per topology; Sec. "Graphical Simulator": the solve path is
+ * found once and serves every position sample).  links_topo_create plans the topology given by one mechanism's n joints,
  * adj [n_max, n_max] and type [n_max] (HOST memory, the layout of links_plan_build),
  * writes CUDA source for its solve path (joint positions and error bounds in
  * registers, parent slots as compile-time names), compiles it for sm_103a with NVRTC

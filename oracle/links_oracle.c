@@ -11,14 +11,14 @@
  * What it computes, and where the paper defines it (LINKS, arXiv 2208.14567):
  *   - mechanism representation: n x n adjacency A, per-joint type (0 fixed,
  *     1 simple, 2 actuated) and initial positions (Sec. "Mechanism
- *     Representation"; Sec. "Dataset Features", item Mechanisms);
+ *     Representation"; Sec. "Dataset Features & Statistics", item Mechanisms);
  *   - solve order (Sec. "Graphical Simulator", Fig. "solver"): starting from the
  *     known joints (fixed + actuated), repeatedly solve a joint with two known
  *     neighbours; fail on complex loops;
  *   - 1-DOF check from the mobility equation (Eq. 1) and the J-operator argument
  *     (Sec. "1-DOF Operator"): every simple joint consumes exactly two links;
  *   - simulation over T equally spaced actuator positions of one full turn
- *     (Sec. "Dataset Features", item Simulation Data) with the locking test
+ *     (Sec. "Dataset Features & Statistics", item Simulation Data) with the locking test
  *     (Sec. "Finding Valid Initial Positions", Infeasibility rule);
  *   - path normalisation (centroid, unit RMS radius, principal axis on +x) and
  *     the bidirectional chamfer distance (Sec. "A Case Study of Mechanism

@@ -1,7 +1,7 @@
 // sim_mixed.cu -- mixed-precision simulation of planned mechanisms (LINKS_MIXED).
 //
 // What is computed (Sec. "Graphical Simulator"; Sec. "Finding Valid Initial Positions",
-// Infeasibility rule; Sec. "Dataset Features", item Simulation Data): at step t the
+// Infeasibility rule; Sec. "Dataset Features & Statistics", item Simulation Data): at step t the
 // crank is turned by 2*pi*t/T about its pivot and each dyad joint k with parents i, j
 // is placed at the intersection of the circles |p - p_i| = r1 and |p - p_j| = r2 on the
 // branch of the initial configuration.  The step locks when a dyad has no

@@ -1,6 +1,7 @@
 // topo.cu -- screen kernels specialised to one topology, generated and compiled at run
-// time (the paper's "vectorised solver specific to a given topology", Sec. "Graphical
-// Simulator": one solve path serves every position sample of a topology).
+// time (Sec. "Computational Cost of Simulations": the paper vectorises its solver for one
+// topology once its solve path is known, and Sec. "Graphical Simulator": that path serves
+// every position sample of the topology).
 //
 // For a topology the generator writes straight-line CUDA for its solve path: every
 // joint's position and error bound live in registers of the lane that computes one

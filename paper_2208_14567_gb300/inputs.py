@@ -201,7 +201,7 @@ def dyad_batch(B: int, n_lo: int, n_hi: int, seed: int = 0, *, ground_max: int =
 
 
 def topology_rules(batch: MechBatch) -> tuple[np.ndarray, np.ndarray]:
-    """The paper's topology rules (Sec. "Dataset Features", rules of topology creation)
+    """The paper's topology rules (Sec. "Dataset Features & Statistics", rules of topology creation)
     for candidates built by ``dyad_batch`` without permutation, where joint k's parents
     are its neighbours of lower index and the last joint is the last one solved:
 
@@ -276,7 +276,7 @@ def paper_topologies(K: int, n: int, seed: int = 0, *, ground_max: int = 3, p_gr
 
 
 def paper_batch(n_topologies: int, samples: int, n: int, seed: int = 0) -> MechBatch:
-    """The paper's own candidates (Sec. "Dataset Features"): ``n_topologies`` topologies of
+    """The paper's own candidates (Sec. "Dataset Features & Statistics"): ``n_topologies`` topologies of
     n joints meeting the topology rules (``paper_topologies``), each with ``samples``
     random initial positions standardised as the paper does: the actuator's ground
     joint at (0.5, 0.5), the actuator arm of length 0.05 and horizontal (actuated joint
