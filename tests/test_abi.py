@@ -65,6 +65,7 @@ def test_topology_source_compiles():
     import tempfile
     from paper_2208_14567_gb300 import inputs as I
     from paper_2208_14567_gb300 import links
+    B.build()
     nvcc = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
     for n in (6, 12):
         b = I.paper_topologies(2, n, seed=n)
