@@ -54,35 +54,61 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region: the
+    sampler starts first (wait_ready returns once it reports), and only the samples read
+    between mark_start and mark_end are kept."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
+    PERIOD_MS = 50
 
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.samples = []  # (host time, line)
+        self.t0 = self.t1 = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            if ln.strip():
+                self.samples.append((time.perf_counter(), ln))
 
     def __enter__(self):
+        import threading
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(self.dev)], stdout=subprocess.PIPE,
+                                          "-lms", str(self.PERIOD_MS), "-i", str(self.dev)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
+            self.reader = threading.Thread(target=self._read, daemon=True)
+            self.reader.start()
         except Exception:
             self.proc = None
         return self
+
+    def wait_ready(self, timeout=10.0):
+        end = time.perf_counter() + timeout
+        while self.proc is not None and not self.samples and time.perf_counter() < end:
+            time.sleep(0.01)
+
+    def mark_start(self):
+        self.t0 = time.perf_counter()
+
+    def mark_end(self):
+        self.t1 = time.perf_counter()
 
     def __exit__(self, *exc):
         self.lines = []
         if self.proc is not None:
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
-                out = ""
-            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+            self.reader.join(timeout=5)
+            t0 = self.t0 if self.t0 is not None else float("-inf")
+            t1 = self.t1 if self.t1 is not None else float("inf")
+            self.lines = [ln for t, ln in self.samples if t0 <= t <= t1]
 
     def summary(self):
         sm, mx, reasons = [], [], set()
@@ -612,7 +638,7 @@ def profile_kernels(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--batch", type=int, default=1_000_000)
@@ -680,11 +706,14 @@ def main():
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as clk:
+        clk.wait_ready()
+        clk.mark_start()
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize(dev)
+        clk.mark_end()
     barrier(world)
     ms = e0.elapsed_time(e1) / args.steps
     launches = (L.links_launch_count(sim.ctx) - launches0) // args.steps
