@@ -555,7 +555,6 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
-  const int64_t B = plan->B;
   const int T = tab->T;
   int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
   if (st) return st;
