@@ -595,8 +595,8 @@ def profile_kernels(args):
     """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
     (no timing): plan build, screen and emit of args.batch 6-8-joint candidates; max-line
     normalisation of their valid coupler paths; curation of their trajectories; a first-3
-    scan of 16 queries over those paths; the screen compiled for one topology of the
-    paper's generator on args.batch samples."""
+    scan of 16 queries over those paths; the generic screen and the screen compiled for
+    one topology of the paper's generator on the same args.batch samples."""
     import torch
 
     from paper_2208_14567_gb300 import inputs as I
@@ -626,6 +626,8 @@ def profile_kernels(args):
     pb = I.paper_batch(1, B, 8, seed=108)
     with Simulator(pb.B, 8) as s:
         s.build(to_device(pb, dev))
+        s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)  # the generic screen, same samples
+        s.sync()
         topo = L.links_topo_create(s.ctx, int(pb.n_joints[0]), pb.adj[0], pb.jtype[0], 16)
         try:
             s.simulate_topology(topo, T, L.OUT_VALID_ONLY, traj=False, path=False)
