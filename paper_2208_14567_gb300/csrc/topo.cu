@@ -94,13 +94,16 @@ std::string topo_source_step(int nf, int nd, const std::vector<int>& sa, const s
   return o.str();
 }
 
+// Paths of up to 6 dyads are compiled for 3 blocks per SM (80 registers: at 8 joints the screen
+// ran 2.39 -> 2.18 ms per 1M samples); longer ones keep their registers (capped, 9 dyads spilled
+// and ran 3.14 -> 3.24 ms).
 std::string topo_source(int nf, int nd, const std::vector<int>& sa, const std::vector<int>& sb, int G) {
   std::ostringstream o;
   const int ns = nf + 1 + nd;
   o << "#include \"step.cuh\"\n"
        "typedef unsigned int u32;\n"
        "#define G " << G << "\n"
-       "extern \"C\" __global__ void __launch_bounds__(256) topo_screen(\n"
+       "extern \"C\" __global__ void __launch_bounds__(256" << (nd <= 6 ? ", 3" : "") << ") topo_screen(\n"
        "    const links::MechHdr* __restrict__ hdr, const links::DyadRec* __restrict__ dyad, int max_dyads,\n"
        "    const float4* __restrict__ fixpos, int n_max, const int* __restrict__ order,\n"
        "    const int* __restrict__ hist, int* __restrict__ work, int T, const float4* __restrict__ cs,\n"
