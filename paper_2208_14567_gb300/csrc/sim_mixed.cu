@@ -21,7 +21,6 @@
 //           float32 (one warp per output row, 32 consecutive steps per store).
 #include "step.cuh"
 #include "links_internal.cuh"
-#include "packed.cuh"
 
 namespace links {
 namespace {
