@@ -1,8 +1,8 @@
 // sim_mixed.cu -- mixed-precision simulation of planned mechanisms (LINKS_MIXED).
 //
 // What is computed (Sec. "Graphical Simulator"; Sec. "Finding Valid Initial Positions",
-// Infeasibility rule; Sec. "Dataset Features & Statistics", item Simulation Data): at step t the
-// crank is turned by 2*pi*t/T about its pivot and each dyad joint k with parents i, j
+// Infeasibility rule; Sec. "Dataset Features & Statistics", item Simulation Data): at step
+// t the crank is turned by 2*pi*t/T about its pivot and each dyad joint k with parents i, j
 // is placed at the intersection of the circles |p - p_i| = r1 and |p - p_j| = r2 on the
 // branch of the initial configuration.  The step locks when a dyad has no
 // intersection.  Steps are independent of each other (the branch is fixed by the
@@ -17,8 +17,12 @@
 //           which decides.  Groups of G lanes take consecutive steps of one mechanism,
 //           a ballot finds the first locking step, and the group moves on to the next
 //           mechanism of a work list sorted by dyad count.
-//   emit    every requested trajectory step in double-word arithmetic, written as
-//           float32 (one warp per output row, 32 consecutive steps per store).
+//   emit    every requested trajectory step through the same certified FP32 chain; a
+//           step whose bounds are all within the tolerance writes its FP32 positions,
+//           any other is recomputed in double-word arithmetic (one warp per output row,
+//           32 consecutive steps per store).
+// The FP32 dyad and the double-word chain are in step.cuh, shared with the screens
+// compiled per topology at run time (topo.cu).
 #include "step.cuh"
 #include "links_internal.cuh"
 
