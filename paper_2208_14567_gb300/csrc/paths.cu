@@ -1,4 +1,4 @@
-// paths.cu -- path normalisation and bidirectional chamfer top-k retrieval
+// paths.cu -- path normalisation, dataset curation and chamfer retrieval
 // (LINKS, Sec. "Dataset Curation & Processing" and Sec. "A Case Study of Mechanism
 // Retrieval").
 //
@@ -7,14 +7,21 @@
 //   that do this take the one with sum(x^3) >= 0; an isotropic covariance
 //   (lambda1 - lambda2 <= 1e-9 (lambda1 + lambda2)) is not rotated; a curve of equal
 //   points maps to zeros.  One warp per curve, points in registers: HBM-bound.
-// chamfer top-k: CD(P, C) = mean_p min_c |p - c| + mean_c min_p |c - p| (Euclidean),
-//   the k smallest per query, ascending, ties to the lower database index.  Each
-//   warp owns one query; its four 8-lane groups take four database curves at a time
-//   from a shared-memory stage, each lane holding PL query points in registers; the
-//   200 x 200 point pairs are reduced to row minima (registers) and column minima
-//   (an 8-lane min per database point).  No tensor cores: the inner dimension is 2.
-//   Each warp keeps a running top-k in registers; a second kernel merges the partial
-//   lists of the database chunks.
+// normalize_maxline: the paper's normalisation (farthest pair onto a unit horizontal
+//   line, bounding box centred at (0.5, 0.5)) and its circle statistic; one warp per
+//   curve, the farthest pair in two passes of packed arithmetic.
+// curation: the same per joint path of the simulated rows, arc and circle flags, the
+//   keep draws, and an ordered compaction of the kept paths.
+// chamfer: CD(P, C) = mean_p min_c |p - c| + mean_c min_p |c - p| (Euclidean).  A CTA
+//   takes 16 queries (a warp each) against a chunk of the database staged in shared
+//   memory 32 curves at a time; 16-lane groups compute exact CDs with the query's points
+//   in registers (packed pairs), after lower bounds (a distance table of the query and
+//   runs of 4 database points) drop the curves that cannot qualify.  No tensor cores: the
+//   inner dimension is 2.  Top-k mode keeps each query's k smallest (ascending, ties to
+//   the lower index), pruning at the k-th distance found so far; first-k mode scans the
+//   database in a given order and keeps the first k curves under a cut-off, pruning at
+//   the cut-off and skipping positions past the k-th hit.  A second kernel merges the
+//   chunks' lists.
 #include <cuda_fp16.h>
 
 #include <algorithm>
