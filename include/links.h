@@ -6,7 +6,7 @@
  * adjacency matrix, a type per joint (0 fixed, 1 simple, 2 actuated) and the
  * initial joint positions (Sec. "Mechanism Representation").  It is simulated
  * over T equally spaced positions of one full actuator turn (Sec. "Dataset
- * Features", item Simulation Data) with the graphical solver: from the known
+ * Features & Statistics", item Simulation Data) with the graphical solver: from the known
  * joints (fixed + actuated), repeatedly solve a joint with two known neighbours
  * by intersecting two circles (Sec. "Graphical Simulator", Fig. "solver").  A
  * candidate is valid when the actuator completes the turn without locking
@@ -19,10 +19,12 @@
  *   - "device" pointers are CUDA device memory owned by the caller (any
  *     allocator); "host" pointers are caller-owned host memory;
  *   - calls taking device pointers are asynchronous on the context's stream
- *     and make no allocation, so a sequence of them can be captured in a CUDA
- *     graph between links_capture_begin and links_capture_end;
- *   - the library owns contexts, plans and graphs and frees them in the
- *     matching *_free / links_destroy call.
+ *     and make no allocation (except the context workspace, which the path
+ *     calls grow on demand and links_workspace_reserve sizes ahead), so a
+ *     sequence of them can be captured in a CUDA graph between
+ *     links_capture_begin and links_capture_end;
+ *   - the library owns contexts, plans, graphs and compiled topology screens
+ *     and frees them in the matching *_free / links_destroy call.
  */
 #ifndef LINKS_H
 #define LINKS_H
