@@ -80,3 +80,13 @@ def test_topology_source_compiles():
             assert r.returncode == 0, r.stderr[-2000:]
     with pytest.raises(links.LinksError):
         links.links_topo_source(6, np.zeros((6, 6), np.uint8), np.array([0, 2, 1, 1, 1, 1], np.int8))
+
+
+def test_embedded_headers_match_the_sources():
+    """The run-time compiled screens include step.cuh and dw_core.cuh from text the build
+    embeds in the library: after a build that text is the current source."""
+    B.build()
+    inc = open(os.path.join(B.OUT_DIR, "embedded_headers.inc")).read()
+    for name in B.EMBEDDED:
+        text = open(os.path.join(B.CSRC, name)).read()
+        assert f'"{name}"' in inc and text in inc, name
