@@ -33,6 +33,20 @@ MUTANTS = {
     "max line pair not the farthest": ("if (d > best) { best = d; a = u; b = v; }",
                                        "if (d > best && v == u + 1) { best = d; a = u; b = v; }"),
     "circle variance of squared radii": ("m2 += r * r;", "m2 += r * r * r * r;"),
+    # the margin indicator q = D / (4 r1^2 r2^2) and its running minima
+    "q with r1 squared twice": ("double q = D / (4.0 * P->r1sq[d] * P->r2sq[d]);",
+                                "double q = D / (4.0 * P->r1sq[d] * P->r1sq[d]);"),
+    "min |q| skips the locking dyad": ("        double aq = fabs(q);\n        if (aq < qabs || aq != aq) qabs = aq;\n"
+                                       "        if (!(q > 0.0)) {",
+                                       "        double aq = fabs(q);\n        if (!(q > 0.0)) {"),
+    "min q includes the locking step": ("            if (locked) { lock = t; break; }\n"
+                                        "            if (qmin < qmin_all) qmin_all = qmin;",
+                                        "            if (qmin < qmin_all) qmin_all = qmin;\n"
+                                        "            if (locked) { lock = t; break; }"),
+    "min |q| skips the locking step": ("            if (qabs < qabs_all || qabs != qabs) qabs_all = qabs;\n"
+                                       "            if (locked) { lock = t; break; }",
+                                       "            if (locked) { lock = t; break; }\n"
+                                       "            if (qabs < qabs_all || qabs != qabs) qabs_all = qabs;"),
 }
 
 
@@ -55,6 +69,8 @@ def run_pins(lib):
             lambda: pins.test_nan_from_lock_and_flags(dyads),
             lambda: pins.test_closure_at_full_turn(O, dyads),
             lambda: pins.test_fourbar_matches_trigonometric_solution(fourbars),
+            lambda: pins.test_fourbar_margin_indicator_closed_form(fourbars),
+            lambda: pins.test_margin_indicator_from_positions(O, dyads),
             lambda: pins.test_full_rotation_criterion(fourbars),
             lambda: pins.test_brute_force_branches(O),
             lambda: pins.test_special_cases(O),

@@ -256,6 +256,94 @@ def test_full_rotation_criterion(fourbars):
     assert 0.05 < r.valid.mean() < 0.95
 
 
+def test_fourbar_margin_indicator_closed_form(fourbars):
+    """The margin indicator q of each dyad is sin^2 of the angle at the joint it solves,
+    which the law of cosines gives independently of the oracle's algebra.  For the
+    four-bar, dyad 0 solves the rocker joint B (coupler b = |B - A|, rocker c = |B - B0|,
+    diagonal delta(t) = |A(t) - B0|): q0 = 1 - cos^2 with cos = (b^2 + c^2 - delta^2) /
+    (2 b c), negative exactly when the triangle cannot close.  Dyad 1 solves the coupler
+    point P on the rigid triangle (A, B, P): q1 is constant.  min_disc = min over the
+    steps before the lock of min(q0, q1) (+inf if the lock is at step 0); min_abs_q also
+    takes |q0| of the locking step, where dyad 1 is not reached."""
+    f, r = fourbars
+    th = 2 * np.pi * np.arange(T) / T
+    locked = 0
+    for m in range(f.B):
+        A0, A, B0, B, P = f.pos[m].astype(np.float64)
+        u = A - A0
+        At = A0 + np.stack([np.cos(th) * u[0] - np.sin(th) * u[1], np.sin(th) * u[0] + np.cos(th) * u[1]], -1)
+        b, c = np.linalg.norm(B - A), np.linalg.norm(B - B0)
+        delta = np.linalg.norm(At - B0, axis=-1)
+        q0 = 1 - ((b * b + c * c - delta * delta) / (2 * b * c)) ** 2
+        pa, pb = np.linalg.norm(P - A), np.linalg.norm(P - B)
+        q1 = 1 - ((pa * pa + pb * pb - b * b) / (2 * pa * pb)) ** 2
+        scale = ((b * b + c * c + delta * delta) ** 2 / (4 * b * b * c * c)).max() + 1.0 / (pa * pb) ** 2
+        lk = int(r.lock_step[m])
+        stop = T if lk < 0 else lk
+        if stop == 0:
+            assert r.min_disc[m] == np.inf
+            md, ab = np.inf, np.inf
+        else:
+            md = min(q0[:stop].min(), q1)
+            ab = min(np.abs(q0[:stop]).min(), abs(q1))
+            assert abs(r.min_disc[m] - md) <= 1e-12 * scale
+        if lk >= 0:
+            locked += 1
+            assert q0[lk] <= 1e-12 * scale  # the lock is the triangle failing to close
+            ab = min(ab, abs(q0[lk]))
+        assert abs(r.min_abs_q[m] - ab) <= 1e-12 * scale
+    assert 0.05 * f.B < locked < 0.95 * f.B
+
+
+def test_margin_indicator_from_positions(oracle_lib, dyads):
+    """On general candidates: q of dyad (k; i, j) at a solved step equals
+    cross(p_i - p_k, p_j - p_k)^2 / (r1^2 r2^2), with the positions of the (separately
+    pinned) trajectories and the link lengths taken from the initial positions.  At the
+    locking step the failing dyad's q comes from the law of cosines on its parents'
+    distance.  min_disc and min_abs_q must be these minima: over the dyads of the steps
+    before the lock, and for min_abs_q also the dyads of the locking step up to and
+    including the failing one."""
+    batch, r = dyads
+    checked = locks = 0
+    for m in range(min(batch.B, 600)):
+        if r.status[m] != 0:
+            continue
+        n = batch.n_joints[m]
+        p0 = batch.pos[m].astype(np.float64)
+        P = oracle_lib.plan(n, batch.adj[m], batch.jtype[m], p0)
+        lk = int(r.lock_step[m])
+        stop = T if lk < 0 else lk
+        tr = r.traj[m]
+        md = ab = np.inf
+        for d in range(P.n_dyads):
+            k, i, j = P.k[d], P.i[d], P.j[d]
+            r1, r2 = ((p0[k] - p0[i]) ** 2).sum(), ((p0[k] - p0[j]) ** 2).sum()
+            if stop:
+                a, b = tr[i, :stop] - tr[k, :stop], tr[j, :stop] - tr[k, :stop]
+                q = (a[:, 0] * b[:, 1] - a[:, 1] * b[:, 0]) ** 2 / (r1 * r2)
+                md = min(md, q.min())
+                ab = min(ab, np.abs(q).min())
+        if lk >= 0:
+            locks += 1
+            out, locked, _, _, q_lock = oracle_lib.solve_at(P, p0, 2 * math.pi * lk / T)
+            assert locked
+            for d in range(P.n_dyads):
+                k, i, j = P.k[d], P.i[d], P.j[d]
+                r1, r2 = math.dist(p0[k], p0[i]), math.dist(p0[k], p0[j])
+                if np.isnan(out[k]).any():  # the failing dyad
+                    dl = math.dist(out[i], out[j])
+                    q = 1 - ((r1 * r1 + r2 * r2 - dl * dl) / (2 * r1 * r2)) ** 2
+                    assert q <= 1e-12 and abs(q - q_lock) <= 1e-12 * (r1 * r1 + r2 * r2 + dl * dl) ** 2 / (r1 * r2) ** 2
+                    ab = min(ab, abs(q))
+                    break
+                a, b = out[i] - out[k], out[j] - out[k]
+                ab = min(ab, (a[0] * b[1] - a[1] * b[0]) ** 2 / (r1 * r1 * r2 * r2))
+        assert r.min_disc[m] == md or abs(r.min_disc[m] - md) <= 1e-9
+        assert r.min_abs_q[m] == ab or abs(r.min_abs_q[m] - ab) <= 1e-9
+        checked += 1
+    assert checked > 300 and locks > 100
+
+
 def solve_branch(p0, i_j_k, signs, theta, pivot, motor, fixed):
     """Positions at crank angle theta for given branch signs, by trigonometry."""
     pos = p0.copy()
