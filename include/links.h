@@ -397,8 +397,10 @@ LINKS_API int links_launch_count(links_ctx ctx, int64_t* out);
  * static device array inside the library sized for B <= 4194304 (4096 x 1024
  * flags); a larger B returns LINKS_EINVAL.  It needs no context and runs on the
  * calling thread's current device and on cuda_stream (a cudaStream_t of that
- * device).  Its first call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * device).  Its first call in a device's context looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it for that context, so make that first
+ * call before any stream capture; after a device reset the new context's first call
+ * looks it up again.
  * Every call on a device shares the array: calls that overlap on the GPU (other
  * streams, other threads) race and must be serialised by the caller.
  * Asynchronous. */

@@ -10,6 +10,9 @@
 // array instead of the context's plan, so it needs no context and allocates nothing.
 // The array is sized for kStaticMaxRows flags; every GPU that loads the library holds
 // it (16 KB) until the process exits.
+#include <cuda.h>  // driver types only: the two driver calls are fetched through the runtime
+
+#include <map>
 #include <mutex>
 
 #include "links_internal.cuh"
@@ -20,14 +23,15 @@ namespace {
 constexpr int kBlockRows = 1024;
 constexpr int kStaticBlocks = 4096;
 constexpr int64_t kStaticMaxRows = (int64_t)kStaticBlocks * kBlockRows;  // 4,194,304 flags
-constexpr int kMaxDevices = 64;
 
 // Block sums of the scan.  Host code must not pass this name to a kernel: it only
 // stands for the symbol; the device address comes from cudaGetSymbolAddress below.
 __device__ __align__(256) int32_t g_block_sums[kStaticBlocks];
 
 std::mutex g_mu;
-int32_t* g_sums_addr[kMaxDevices] = {};
+// Device address of g_block_sums per CUDA context, keyed by the context's unique id (a
+// device reset makes a new context with a new id, so its address is looked up again).
+std::map<unsigned long long, int32_t*> g_sums_addr;
 
 __device__ int static_block_scan(int v, int* total) {
   __shared__ int ws[32];
@@ -89,19 +93,49 @@ __global__ void __launch_bounds__(kBlockRows) static_scan_write(int64_t B, const
   if (v && ex < cap && out_index) out_index[ex] = (int32_t)b;
 }
 
-// Device address of g_block_sums on the current device, looked up once per device.
+// Unique id of the calling thread's current CUDA context (cuCtxGetCurrent + cuCtxGetId,
+// fetched through the runtime so the library needs no driver link); false if either
+// call is unavailable or fails.
+bool current_ctx_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  CUcontext c = nullptr;
+  return get_current && get_id && get_current(&c) == CUDA_SUCCESS && c && get_id(c, id) == CUDA_SUCCESS;
+}
+
+// Device address of g_block_sums in the current context: looked up once per context
+// (cudaGetSymbolAddress with the device current), then cached.  Where the context id
+// cannot be read (no context current yet on this thread, before the runtime's first
+// call makes the primary context current), it is looked up on that call.
 int static_sums(int32_t** out) {
-  int dev = 0;
-  LINKS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= kMaxDevices) return set_error(LINKS_EINVAL, "links_compact_valid_static: device index >= 64");
+  unsigned long long id = 0;
+  const bool keyed = current_ctx_id(&id);
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_sums_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_block_sums);
-    if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_block_sums)");
-    g_sums_addr[dev] = static_cast<int32_t*>(p);
+  if (keyed) {
+    auto it = g_sums_addr.find(id);
+    if (it != g_sums_addr.end()) {
+      *out = it->second;
+      return LINKS_OK;
+    }
   }
-  *out = g_sums_addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_block_sums);
+  if (e != cudaSuccess) return cuda_status(e, "cudaGetSymbolAddress(g_block_sums)");
+  if (keyed) g_sums_addr[id] = static_cast<int32_t*>(p);
+  *out = static_cast<int32_t*>(p);
   return LINKS_OK;
 }
 

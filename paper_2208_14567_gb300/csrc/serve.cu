@@ -218,10 +218,18 @@ void worker_main(ServeState* s) {
     {
       std::unique_lock<std::mutex> lk(s->mu);
       if (s->stop && s->pending.empty() && s->inflight.empty()) break;
+      // Each pass owns one of kSlots count slots until it retires.  A request may open
+      // a new pass (one per contiguous run of the ring), so it is admitted only while
+      // the passes in flight plus those of this round leave a slot for one more.
+      int64_t run_end = -1;
+      int runs = 0;
       while (!s->pending.empty() && !s->paused) {
         Req* r = s->pending.front();
+        if ((int)s->inflight.size() + runs + 1 > ServeState::kSlots) break;
         int64_t off = ring_alloc(s, r->r.count);
         if (off < 0) break;
+        if (off != run_end) ++runs;
+        run_end = off + r->r.count;
         r->off = off;
         r->t_admit = now_ms();
         admitted.push_back(r);

@@ -418,11 +418,9 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
                   int16_t* lock_step, float* min_disc, const int32_t* order, const int32_t* n_list) {
   PlanDev& p = plan->d;
   size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
-  static bool attr_set = false;
-  if (!attr_set) {
-    LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr_set = true;
-  }
+  // a function attribute of the current device's context: set on every launch (a host
+  // call, no stream work), so other devices and contexts get it too
+  LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G, S>, kBlock, smem));
   if (per_sm < 1) per_sm = 1;

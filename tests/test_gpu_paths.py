@@ -348,6 +348,22 @@ def test_chamfer_first_under_full_size_sampled(L, ctx):
         print(f"[full size] query {a}: hits {hits.tolist()} at positions {pos.tolist()}")
 
 
+def test_chamfer_topk_full_size_sampled(L, ctx):
+    """The top-10 at the retrieval benchmark's size (1024 noisy queries against 1M
+    normalised curves of 200 points, pruning on): at this size the shared k-th distance
+    is tight and the prune and early-exit paths run as in the benchmark.  Sampled queries
+    are checked against the oracle's exhaustive chamfer distances over all 1M curves."""
+    T, M, Q, k = 200, 1_000_000, 1024, 10
+    db = O.normalize(I.fourier_curves(M, T, seed=31).astype(np.float64)).astype(np.float32)
+    held = O.normalize(I.fourier_curves(Q, T, seed=32).astype(np.float64)).astype(np.float32)
+    q = O.normalize(I.perturb_curves(held, 0.02, seed=33).astype(np.float64)).astype(np.float32)
+    q[1] = db[777_777]  # an exact copy ranks first at distance 0
+    idx, dist = gpu_topk(L, ctx, q, db, k)
+    assert idx[1, 0] == 777_777 and dist[1, 0] == 0.0
+    sel = sorted({0, Q - 1} | set(np.random.default_rng(34).choice(Q, 2, replace=False).tolist()))
+    check_topk(q[sel], db, idx[sel], dist[sel], k, "full size 1024 x 1M")
+
+
 @pytest.mark.parametrize("n_lo,n_hi,T,keep", [(6, 8, 200, 0.005), (5, 12, 64, 0.3), (6, 10, 33, 1.0)])
 def test_curation_matches_oracle(L, ctx, n_lo, n_hi, T, keep):
     """The paper's curation of every moving joint's path, on the oracle's trajectories of

@@ -140,6 +140,56 @@ def test_alone_equals_mix_equals_batch_path(L):
           f"max error / (1e-5 L / r) {(err[ok] / (amp[ok] * (1 + 1 / gap[ok]))).max():.2f}")
 
 
+def test_overload_many_small_requests_behind_a_large_one(L):
+    """Offered load above what one pass at a time can absorb: a large request occupies
+    the GPU while 200 small requests arrive one by one, each of which can open a pass of
+    its own.  Every request's flags, valid indices and normalised paths must equal the
+    batch path's on the same candidates (the serving loop must not mix up the results
+    of passes that are in flight together)."""
+    pool = I.dyad_batch(80000, 6, 20, seed=35, nmax=NMAX, permute=True)
+    rng = np.random.default_rng(3)
+    sizes = [60000] + list(rng.integers(1, 40, 200))
+    sizes = np.array(sizes)[np.cumsum(sizes) <= pool.B]
+    reqs = make_requests(pool, sizes)
+    ctx = L.links_create(0, torch.cuda.current_stream())
+    outs, tickets = [], []
+    try:
+        L.links_serve_start(ctx, 1 << 30, 512, NMAX, T)
+        for b in reqs:
+            o = Out(b.B)
+            t, keep = submit(L, ctx, b, o)
+            outs.append(o)
+            tickets.append((t, keep))
+            time.sleep(2e-5)
+        results = [wait(L, ctx, t) for t, _ in tickets]
+        L.links_serve_stop(ctx)
+    finally:
+        L.links_destroy(ctx)
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    allb = pool.slice(0, int(sizes.sum()))
+    with Simulator(allb.B, NMAX) as s:
+        s.build(to_device(allb))
+        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=True)
+        p = o.path[:int(o.n_out[0])].clone()
+        L.links_normalize(s.ctx, p, p)
+        s.sync()
+        valid = o.valid.cpu().numpy()
+        lock = o.lock_step.cpu().numpy()
+        paths = p.cpu().numpy()
+    off = row = 0
+    for b, o, r in zip(reqs, outs, results):
+        assert r.status == 0
+        v = valid[off:off + b.B]
+        assert np.array_equal(o.valid, v) and np.array_equal(o.lock, lock[off:off + b.B])
+        n = int(v.sum())
+        assert r.n_valid == n
+        assert np.array_equal(o.idx[:n], np.nonzero(v)[0])
+        assert np.array_equal(o.paths[:n], paths[row:row + n])
+        off += b.B
+        row += n
+    print(f"overload: {len(reqs)} requests, {off} candidates, {row} valid rows")
+
+
 def test_admission_timeout_and_refusals(L):
     pool = I.dyad_batch(4000, 6, 12, seed=32, nmax=12)
     ctx = L.links_create(0, torch.cuda.current_stream())

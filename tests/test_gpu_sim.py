@@ -267,11 +267,52 @@ def test_emit_census(L):
         s.close()
 
 
+def check_rows_against_oracle(batch, got, T, label):
+    """A LINKS_MIXED result with VALID_ONLY rows (got: numpy outputs) against the FP64
+    oracle on the same inputs: valid flags equal outside the margin; every row within
+    TOL_MIXED of the oracle's trajectory and coupler path where the oracle calls the
+    mechanism valid; every rejected mechanism's lock step a step at which the oracle's
+    solver locks (or whose smallest |q| lies inside the margin), no earlier than the
+    oracle's first lock."""
+    ref = O.simulate(batch, T)
+    margin = ~(ref.min_abs_q > MARGIN)
+    ok = ref.status == 0
+    bad = (got["valid"] != ref.valid) & ~margin
+    assert not bad.any(), f"{int(bad.sum())} flag mismatches outside the margin"
+    n = int(got["n_out"][0])
+    rows = got["out_index"][:n]
+    Ld = bbox_diag(batch.pos, batch.n_joints)
+    worst = 0.0
+    for r, b in enumerate(rows):
+        if ref.valid[b] != 1:
+            continue
+        nj = batch.n_joints[b]
+        e = np.abs(got["traj"][r, :nj].astype(np.float64) - ref.traj[b, :nj]).max() / Ld[b]
+        ep = np.abs(got["path"][r].astype(np.float64) - ref.path[b]).max() / Ld[b]
+        worst = max(worst, e, ep)
+    assert worst <= TOL_MIXED, f"max position error / L {worst:.3e}"
+    rej = np.nonzero(ok & (got["valid"] == 0))[0]
+    checked = 0
+    for b in rej:
+        ls = int(got["lock_step"][b])
+        assert ls >= 0
+        if not margin[b]:
+            assert ls >= ref.lock_step[b] >= 0
+        P = O.plan(batch.n_joints[b], batch.adj[b], batch.jtype[b], batch.pos[b].astype(np.float64))
+        _, locked, _, qabs, _ = O.solve_at(P, batch.pos[b].astype(np.float64), 2 * np.pi * ls / T)
+        assert locked or qabs <= MARGIN, (b, ls)
+        checked += 1
+    print(f"[{label}] oracle: rows {n}, max position error / L {worst:.2e}, rejected lock steps checked {checked}, "
+          f"margin cases {int(margin.sum())}")
+
+
 @pytest.mark.parametrize("case", ["dyad6-8", "dyad6-20"])
 def test_two_stage_screen(L, case):
     """links_simulate_two_stage: the coarse grid's angles are fine-grid angles, so the
     valid flags, the valid rows and their outputs equal the single-stage run; rejected
-    mechanisms carry a fine-grid locking step no earlier than the first one."""
+    mechanisms carry a fine-grid locking step no earlier than the first one.  Then the
+    two-stage result itself against the oracle (flags, rows, and each rejected
+    mechanism's lock step an oracle locking angle)."""
     import torch
     from paper_2208_14567_gb300.api import to_device
     batch = I.dyad_batch(5000, 6, 8, seed=21) if case == "dyad6-8" else I.dyad_batch(4000, 6, 20, seed=22, nmax=20)
@@ -301,10 +342,30 @@ def test_two_stage_screen(L, case):
         nl = int(n_low.item())
         assert nl >= n
         print(f"[{case}] valid {n}, valid on {T_low} positions {nl}: false-valid rate {(nl - n) / max(nl, 1):.4f}")
+        check_rows_against_oracle(batch, got, T, f"two-stage {case}")
         with pytest.raises(L.LinksError):
             s.simulate_two_stage(T, 60)
     finally:
         s.close()
+
+
+@pytest.mark.parametrize("n", [6, 8, 10, 12, 15, 20])
+def test_paper_generator_matches_oracle(L, n):
+    """Candidates of the paper's own generator (topologies by the J operator under the
+    paper's rules; ground pivot at (0.5, 0.5), horizontal actuator arm of 0.05, the other
+    joints uniform in the unit box): eight topologies x 300 position samples of n joints,
+    LINKS_MIXED FULL against the oracle -- flags outside the margin, positions within
+    1e-5 L at every step, min_disc as in the generic tests."""
+    batch = I.paper_batch(8, 300, n, seed=500 + n)
+    T = 200
+    ref = O.simulate(batch, T)
+    res = run(batch, T, L.MIXED, L.OUT_FULL, L)
+    assert np.array_equal(res["status"], ref.status) and (ref.status == 0).all()
+    check_flags(res, ref, f"paper n={n}")
+    check_positions(batch, res["traj"], res["path"], ref, res["lock_step"], TOL_MIXED, f"paper n={n}")
+    ok = (ref.lock_step != 0) & (res["lock_step"] == ref.lock_step)
+    dq = np.abs(res["min_disc"][ok] - ref.min_disc[ok])
+    assert (dq <= 1e-4 + 1e-3 * ref.min_disc[ok]).all()
 
 
 @pytest.mark.parametrize("T", [1, 7, 33, 64])

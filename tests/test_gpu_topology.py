@@ -2,8 +2,8 @@
 
 Its mechanisms get the generic screen's flags, lock steps and minimum discriminants
 bit for bit (the same operations in the same order), the others go to the generic
-screen, so every output of a simulation equals that of links_simulate (MIXED): the
-generic path is itself checked against the FP64 oracle in test_gpu_sim.py.
+screen, so every output of a simulation equals that of links_simulate (MIXED).  The
+specialised path is also checked against the FP64 oracle directly.
 """
 import numpy as np
 import pytest
@@ -68,6 +68,52 @@ def test_one_topology_matches_generic(L, n, T, lanes):
         assert esc == 0
     print(f"[topology n={n} T={T} lanes={lanes}] dyads {info['dyads']} valid {ra['valid'].mean():.3f} escaped {esc} "
           f"compile {info['compile_ms']:.0f} ms")
+
+
+@pytest.mark.parametrize("n,lanes", [(6, 0), (8, 16), (10, 32), (12, 0)])
+def test_topology_screen_matches_oracle(L, n, lanes):
+    """The topology-specialised path against the FP64 oracle directly: 4000 position
+    samples of one paper topology, LINKS_MIXED FULL through links_simulate_topology --
+    flags identical outside the oracle's margin (min |q| <= 1e-9), positions within
+    1e-5 of the bounding-box diagonal at every step both sides simulated, NaN from the
+    lock on, min_disc within 1e-4 + 1e-3 q."""
+    from conftest import bbox_diag
+    from oracle import oracle as O
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.paper_batch(1, 4000, n, seed=40 + n)
+    T = 200
+    ref = O.simulate(batch, T)
+    with Simulator(batch.B, batch.nmax) as s:
+        s.build(to_device(batch))
+        topo = L.links_topo_create(s.ctx, int(batch.n_joints[0]), batch.adj[0], batch.jtype[0], lanes)
+        try:
+            esc = torch.zeros(1, dtype=torch.int32, device="cuda")
+            o = s.simulate_topology(topo, T, L.OUT_FULL, n_escaped=esc)
+            s.sync()
+            g = {k: None if v is None else v.cpu().numpy() for k, v in o.__dict__.items()}
+        finally:
+            L.links_topo_free(topo)
+    assert int(esc.item()) == 0
+    margin = ~(ref.min_abs_q > 1e-9)
+    mism = (g["valid"] != ref.valid) | (g["lock_step"] != ref.lock_step)
+    assert not (mism & ~margin).any()
+    Ld = bbox_diag(batch.pos, batch.n_joints)
+    lr = np.where(ref.lock_step < 0, T, ref.lock_step)
+    lg = np.where(g["lock_step"] < 0, T, g["lock_step"])
+    stop = np.minimum(lr, lg)
+    tm = np.arange(T)[None, :] < stop[:, None]
+    err = np.abs(g["traj"][:, :n].astype(np.float64) - ref.traj[:, :n]).max(-1)  # [B, n, T]
+    e = np.where(tm[:, None, :], err, 0.0).max((1, 2)) / Ld
+    assert (e <= 1e-5).all(), e.max()
+    after = np.arange(T)[None, :] >= lg[:, None]
+    assert np.isnan(g["traj"][:, :n][np.broadcast_to(after[:, None, :], (batch.B, n, T))]).all()
+    pe = np.where(tm, np.abs(g["path"].astype(np.float64) - ref.path).max(-1), 0.0).max(1) / Ld
+    assert (pe <= 1e-5).all()
+    ok = (ref.lock_step != 0) & (g["lock_step"] == ref.lock_step)
+    dq = np.abs(g["min_disc"][ok] - ref.min_disc[ok])
+    assert (dq <= 1e-4 + 1e-3 * ref.min_disc[ok]).all()
+    print(f"[topology vs oracle n={n}] valid {g['valid'].mean():.3f} margin cases {int(margin.sum())} "
+          f"max position error / L {e.max():.2e}")
 
 
 def test_other_topologies_escape(L):
