@@ -1,22 +1,26 @@
 #!/usr/bin/env python
 """Benchmark of the batched linkage-simulation hot path (LINKS, arXiv 2208.14567) on GB300.
 
-Workload: 1,000,000 random 1-DOF candidates of 6-8 joints built by sequential dyad
-addition (2-3 ground joints, one crank), positions uniform in [0,1]^2 (float32),
-T = 200 crank steps.  One step = the whole hot path on one batch: device plan build
-(solve order, branch, lengths, work list) + mixed-precision simulation (certified
-FP32 screen with double-word rescue, valid-row compaction, double-word trajectories
-of the valid candidates) producing valid flags, lock steps, min_disc, and the
-trajectories [rows, 8, 200, 2] and coupler paths of every valid candidate.
+Headline workload (--config 3, the default): 4,194,304 random 1-DOF candidates built by
+sequential dyad addition, joint count uniform in 6..20 (n_max 20, 2-3 ground joints, one
+crank), positions uniform in [0,1]^2 (float32), T = 200 crank steps.  One step = the
+whole hot path on one batch, replayed as one captured CUDA graph: device plan build
+(solve order, branch, lengths, work list) + mixed-precision simulation (persistent
+certified FP32 screen with double-word rescue, lanes per mechanism autotuned; valid-row
+compaction; trajectories of the valid candidates) producing valid flags, lock steps,
+min_disc, and the trajectories and coupler paths of every valid candidate.  The same
+line carries the 1M 6-8-joint configuration (--config 2) and the 4096 four-bars of the
+plain FP64 method under `configs`, each with its accuracy against the FP64 oracle.
 
-Metric: mechanism-steps/s = B x T / wall time of a step (the plain FP64 kernel on the
+Metric: mechanism-steps/s = B x T / device time of a step (the plain FP64 kernel on the
 same inputs is timed beside it).  `value` is device time with inputs resident in HBM
-(140 MB of inputs > 126 MB L2, so no flush is needed); `e2e` adds the pinned
-host->device copy of the inputs and the device->host copy of the flags and of every
-valid trajectory and path.  Multi-GPU runs are independent replicas (weak scaling,
-no collective on the data path).
+(inputs larger than the 126 MB L2, so no flush is needed; the four-bar configuration
+writes a 256 MB buffer between timed steps); `e2e` adds the pinned host->device copy
+of the inputs and the device->host copy of the flags, valid indices and coupler paths
+(`e2e_full`: every valid trajectory too).  Multi-GPU runs are independent replicas
+(weak scaling, no collective on the data path).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config 2|3]
 """
 from __future__ import annotations
 
@@ -33,15 +37,28 @@ sys.path.insert(0, ROOT)
 
 METRIC = "mechanism-steps/s vs plain FP64 kernel (pos err<=1e-5 rel); serve p50/p99 ms"
 UNIT = "mechanism-steps/s"
-WORKLOAD = ("1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U[0,1]^2 float32, T=200, "
-            "mixed precision, valid-only trajectories + paths + flags")
-SM_COUNT = 152
 FP32_LANES_PER_CLK_SM = 128  # FP32 pipe lanes per SM per clock (an FMA is one op)
-# Algorithmic FP32 operation counts of the formulations (an FMA is one op, a MUFU op is one op):
+# FP32 operation counts (an FMA is one op, a MUFU op is one op).  The method's own work:
+METHOD_DYAD_OPS = 18   # one circle-circle intersection: ~16 FMA-pipe ops + 2 MUFU (d, sqrt(D))
+METHOD_STEP_OPS = 4    # crank rotation, per step
+# ... and what this build's precision design executes for it:
 DW_DYAD_OPS = 221      # one double-word dyad (sub, squares, D, sqrt, reciprocal, update)
 DW_STEP_OPS = 72       # double-word crank rotation and pivot offset, per step
 SCREEN_DYAD_OPS = 35   # one certified FP32 dyad (product-form D, bounds, update)
 SCREEN_STEP_OPS = 6    # FP32 crank rotation, per step
+# The bound each hot kernel's ncu counters show (profiles/), and where it is read.
+BINDING = {"mixed_emit": "hbm", "mixed_screen": "alu", "plan_build": "hbm"}
+BINDING_EVIDENCE = {
+    "mixed_emit": "profiles/: emit issue active 71% vs DRAM 30% of peak on 6-8 joints; the HBM view counts "
+                  "only the real joints' bytes, the ALU view beside it",
+    "mixed_screen": "profiles/: screen DRAM 4% of peak, issue active 74%",
+    "plan_build": "profiles/: latency-bound, 12 of 32 lanes active",
+}
+# DRAM bytes per unit (per valid row for the emit, per candidate otherwise) from a committed
+# ncu capture of the same kernel on the same configuration, scaled to the launch; empty
+# where no capture of the current kernels exists for the configuration.
+TRAFFIC_PER_UNIT = {}
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, scaled per unit"
 
 
 def peaks():
@@ -165,20 +182,19 @@ def algorithmic_dyad_steps(batch, lock_step, T):
     return int((nd.astype(np.int64) * steps).sum())
 
 
-def cpu_baseline(T, seconds=12.0, sample=20000):
-    """The FP64 oracle as it stands, on a bounded sample of the same workload."""
+def cpu_baseline(cfg, args, seconds=12.0, sample=20000):
+    """The FP64 oracle as it stands, on a bounded sample of the headline workload."""
     from oracle import oracle as O
-    from paper_2208_14567_gb300 import inputs as I
-    batch = I.dyad_batch(sample, 6, 8, seed=12345)
+    batch = make_batch(cfg, sample, seed=12345)
     O.lib()
     runs, t0 = 0, time.perf_counter()
     while True:
-        O.simulate(batch, T, traj=True, path=True)
+        O.simulate(batch, args.T, traj=True, path=True)
         runs += 1
         el = time.perf_counter() - t0
         if el >= seconds:
             break
-    return {"value": runs * sample * T / el, "unit": UNIT, "cores": O.n_threads(), "kind": "oracle",
+    return {"value": runs * sample * args.T / el, "unit": UNIT, "cores": O.n_threads(), "kind": "oracle",
             "sample": f"{runs} x {sample} candidates of the same recipe (seed 12345), full trajectories, "
                       f"{el:.1f} s on the host cores"}
 
@@ -428,7 +444,7 @@ def curation_stage(args, local, stream):
     ctx = L.links_create(local, stream)
     res = {}
     try:
-        for name, batch in (("dyad_6-8", I.dyad_batch(args.batch, 6, 8, seed=0)),
+        for name, batch in (("dyad_6-8", I.dyad_batch(CONFIGS[2]["B"], 6, 8, seed=0)),
                             ("paper_n6", I.paper_batch(256, 1024, 6, seed=6)),
                             ("paper_n10", I.paper_batch(256, 1024, 10, seed=10)),
                             ("paper_n15", I.paper_batch(256, 1024, 15, seed=15))):
@@ -577,20 +593,6 @@ def serve_stage(args, local, stream):
             "budget_GiB": args.serve_budget}
 
 
-def run_reference(args, world, rank):
-    if rank != 0:
-        return
-    cb = cpu_baseline(args.T, seconds=args.ref_seconds)
-    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": args.batch * args.T / cb["value"] * 1e3,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "batch": args.batch, "T": args.T,
-                       "note": "oracle throughput measured on a bounded sample; ms_per_step extrapolated"},
-            "cpu_baseline": cb,
-            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
-
-
 def profile_kernels(args):
     """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
     (no timing): plan build, screen and emit of args.batch 6-8-joint candidates; max-line
@@ -637,17 +639,460 @@ def profile_kernels(args):
     print(json.dumps({"profile_kernels": "done", "batch": B, "valid_rows": nv}))
 
 
+def make_batch(cfg, B, seed):
+    """The seeded synthetic candidates of a configuration (B of them)."""
+    from paper_2208_14567_gb300 import inputs as I
+    if cfg["kind"] == "fourbar":
+        return I.fourbar_batch(B, seed=seed)
+    return I.dyad_batch(B, cfg["n_lo"], cfg["n_hi"], seed=seed, nmax=cfg["n_max"])
+
+
+def config_dict(cfg, args, world):
+    """The `config` object of a bench line (the same for both arms)."""
+    d = {"workload": cfg["workload"], "batch": cfg["B"], "T": args.T, "joints": cfg["joints"],
+         "n_max": cfg["n_max"], "precision": cfg["precision_name"], "out_mode": cfg["out_name"],
+         "graph": cfg["graph"], "l2": cfg["l2"], "parallelism": f"replicas x{world}"}
+    return d
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on the same
+    configuration's recipe; each step is a bounded seeded sample of that workload (full
+    trajectories), timed with the host clock."""
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    cfg = headline_config(args)
+    sample = min(cfg["B"], args.ref_sample)
+    batch = make_batch(cfg, sample, seed=12345)
+    O.lib()
+    for _ in range(args.warmup):
+        O.simulate(batch, args.T, traj=True, path=True)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.simulate(batch, args.T, traj=True, path=True)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = sample * args.T / (ms * 1e-3)
+    cb = {"value": value, "unit": UNIT, "cores": O.n_threads(), "kind": "oracle",
+          "sample": f"{sample} candidates of the same recipe per step (seed 12345), full trajectories and paths, "
+                    f"{args.steps} timed steps after {args.warmup} warm-up steps on the host cores"}
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_dict(cfg, args, world), "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+CONFIGS = {
+    1: {"name": "config1_fourbars_f64", "kind": "fourbar", "B": 4096, "n_lo": 5, "n_hi": 5, "n_max": 5,
+        "joints": "5", "precision_name": "plain_f64", "out_name": "full", "graph": False,
+        "workload": "4096 random four-bar mechanisms (2 ground pivots, crank about ground 0, rocker, coupler "
+                    "point), positions U[0,1]^2 float64, T=200, plain FP64 kernel, full trajectories + flags",
+        "l2": "inputs 1 MB fit L2; a 256 MB buffer is written between timed steps"},
+    2: {"name": "config2_1M_6-8", "kind": "dyad", "B": 1_000_000, "n_lo": 6, "n_hi": 8, "n_max": 8,
+        "joints": "6-8", "precision_name": "mixed", "out_name": "valid_only", "graph": False,
+        "workload": "1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U[0,1]^2 float32, T=200, "
+                    "mixed precision, valid-only trajectories + paths + flags",
+        "l2": "inputs 140 MB per step exceed the 126 MB L2; no flush"},
+    3: {"name": "config3_4M_6-20", "kind": "dyad", "B": 4 * 1024 * 1024, "n_lo": 6, "n_hi": 20, "n_max": 20,
+        "joints": "6-20", "precision_name": "mixed", "out_name": "valid_only", "graph": True,
+        "workload": "4M (4,194,304) dyad-built 1-DOF candidates, joint count uniform in 6..20 (n_max 20), 2-3 "
+                    "ground, positions U[0,1]^2 float32, T=200, mixed precision; one CUDA-graph step of device "
+                    "plan build + persistent certified screen (lanes per mechanism autotuned) + compaction + "
+                    "emit; valid-only trajectories + paths + flags; the plain FP64 kernel on the same inputs",
+        "l2": "inputs 2.4 GB per step exceed the 126 MB L2; no flush"},
+}
+
+
+def headline_config(args):
+    cfg = dict(CONFIGS[args.config])
+    if args.headline_batch:
+        cfg["B"] = args.headline_batch
+    return cfg
+
+
+def flush_l2(dev, buf=[]):
+    import torch
+    if not buf:
+        buf.append(torch.empty(256 << 20, dtype=torch.uint8, device=dev))
+    buf[0].fill_(1)
+
+
+def accuracy(cfg, batch, out, T, full_mode, seed=99, rows_sample=2000):
+    """The GPU result against the FP64 oracle on the same inputs: flags of every
+    candidate (mismatches inside / outside the margin min |q| <= 1e-9), and the position
+    error / L (L = bounding-box diagonal) over every step of a seeded sample of valid
+    rows, both sides' valid rows."""
+    import numpy as np
+    import torch
+
+    from oracle import oracle as O
+    t0 = time.perf_counter()
+    ref = O.simulate(batch, T, traj=False, path=False)
+    valid = out.valid.cpu().numpy()
+    lock = out.lock_step.cpu().numpy()
+    margin = ~(ref.min_abs_q > 1e-9)
+    mism = (valid != ref.valid) | (lock != ref.lock_step)
+    if full_mode:
+        cand = np.nonzero((valid == 1) & (ref.valid == 1))[0]
+    else:
+        n = int(out.n_out[0])
+        cand = np.nonzero(ref.valid[out.out_index[:n].cpu().numpy()] == 1)[0]  # rows
+    rng = np.random.default_rng(seed)
+    pick = np.sort(rng.choice(len(cand), size=min(rows_sample, len(cand)), replace=False))
+    rows = cand[pick]
+    if full_mode:
+        mech = rows
+    else:
+        mech = out.out_index[torch.from_numpy(rows).to(out.out_index.device)].cpu().numpy()
+    ridx = torch.from_numpy(rows).to(out.valid.device)
+    traj = out.traj[ridx].double().cpu().numpy()
+    sub = batch.take(mech)
+    rs = O.simulate(sub, T)
+    live = (np.arange(batch.nmax)[None, :] < sub.n_joints[:, None])
+    p = np.asarray(sub.pos, np.float64)
+    hi = np.where(live[..., None], p, -np.inf).max(1)
+    lo = np.where(live[..., None], p, np.inf).min(1)
+    Ld = np.sqrt(((hi - lo) ** 2).sum(-1))
+    err = np.abs(traj - rs.traj)
+    err = np.where(live[:, :, None, None], err, 0.0).max(axis=(1, 2, 3)) / Ld
+    return {"flags_checked": int(len(valid)), "margin_cases": int(margin.sum()),
+            "flag_mismatches_in_margin": int((mism & margin).sum()),
+            "flag_mismatches_out_of_margin": int((mism & ~margin).sum()),
+            "valid_rate": float(valid.mean()), "rows_checked": int(len(rows)),
+            "pos_err_max_over_L": float(err.max()) if len(rows) else 0.0,
+            "pos_err_p99_over_L": float(np.percentile(err, 99)) if len(rows) else 0.0,
+            "oracle_seconds": time.perf_counter() - t0}
+
+
+def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
+    """One configuration: inputs resident in HBM, `warmup` untimed steps, `steps` timed
+    steps (CUDA events on the launching stream; clocks sampled in the timed region for
+    the headline), then per-kernel timings, the roofline of the dominant kernel, the
+    plain FP64 kernel on the same inputs and the accuracy against the oracle."""
+    import numpy as np
+    import torch
+
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    T, B, nmax = args.T, cfg["B"], cfg["n_max"]
+    batch = make_batch(cfg, B, seed=rank)
+    db = to_device(batch, dev)
+    sim = Simulator(B, nmax, device=local, stream=stream)
+    status = torch.empty(B, dtype=torch.int32, device=dev)
+    fourbar = cfg["kind"] == "fourbar"
+    prec = L.PLAIN_F64 if fourbar else L.MIXED
+    mode = L.OUT_FULL if fourbar else L.OUT_VALID_ONLY
+    sim.build(db, status)
+    lanes = None
+    if not fourbar:
+        if cfg["graph"]:
+            lanes = L.links_autotune(sim.ctx, sim.plan, T)
+        probe = sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
+        sim.sync()
+        out = sim.alloc(T, prec, mode, out_capacity=int(probe.n_out[0]) + 4096)
+        del probe
+    else:
+        out = sim.alloc(T, prec, mode)
+    graph = None
+    per_step_launches = None
+    if cfg["graph"]:
+        L.links_prepare(sim.ctx, T)
+        c0 = L.links_launch_count(sim.ctx)
+        L.links_capture_begin(sim.ctx)
+        sim.build(db, status)
+        sim.simulate(T, prec, mode, out=out)
+        graph = L.links_capture_end(sim.ctx)
+        per_step_launches = L.links_launch_count(sim.ctx) - c0
+
+    def step():
+        if graph is not None:
+            L.links_graph_launch(sim.ctx, graph)
+        else:
+            sim.build(db, status)
+            sim.simulate(T, prec, mode, out=out)
+
+    for _ in range(warmup):
+        step()
+    sim.sync()
+    launches0 = L.links_launch_count(sim.ctx)
+    flush = fourbar  # a small working set: write a buffer larger than L2 between timed steps
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    clk = Clocks(local) if headline else None
+    if clk:
+        clk.__enter__()
+        clk.wait_ready()
+        clk.mark_start()
+    if flush:
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for a, b in evs:
+            flush_l2(dev)
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    else:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / steps
+    if clk:
+        clk.mark_end()
+        clk.__exit__(None, None, None)
+    barrier(world)
+    if graph is not None:
+        launches = per_step_launches * steps
+    else:
+        launches = L.links_launch_count(sim.ctx) - launches0
+    ms = max_over_ranks(ms, world, dev)
+    sim.sync()
+    res = {"workload": cfg["workload"], "batch": B, "T": T, "ms_per_step": ms,
+           "value": world * B * T / (ms * 1e-3), "unit": UNIT, "gpu_launches": int(launches),
+           "graph": cfg["graph"], "screen_lanes_autotuned": lanes}
+    if clk:
+        res["clocks"] = clk.summary()
+    lock_np = out.lock_step.cpu().numpy()
+    n_valid = int(out.n_out[0]) if out.n_out is not None else int(out.valid.sum().item())
+    res["valid_rows"] = n_valid
+    dyad_steps = algorithmic_dyad_steps(batch, lock_np, T)
+    res["algorithmic_dyad_steps_per_step"] = dyad_steps
+
+    # per-kernel event timing over ungraphed steps (a profile cannot run inside a graph)
+    L.links_profile(sim.ctx, True)
+    prof_steps = 3
+    for _ in range(prof_steps):
+        sim.build(db, status)
+        sim.simulate(T, prec, mode, out=out)
+    prof = L.links_profile_read(sim.ctx)
+    L.links_profile(sim.ctx, False)
+    total = sum(v[0] for v in prof.values())
+    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / prof_steps,
+                   "share": v[0] / total if total else 0.0} for k, v in prof.items()}
+    res["kernels"] = kernels
+    if not fourbar:
+        res["roofline"], res["roofline_views"] = roofline(kernels, batch, out, lock_np, dyad_steps, n_valid, T,
+                                                          nmax, sim, L)
+
+    # the plain FP64 kernel on the same inputs (the comparator the metric names)
+    if not fourbar:
+        f64_out = sim.alloc(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out_capacity=max(n_valid, 1))
+        sim.build(db, status)
+        sim.simulate(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out=f64_out)
+        sim.sync()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        f64_steps = 2
+        for _ in range(f64_steps):
+            sim.build(db, status)
+            sim.simulate(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out=f64_out)
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        f64_ms = max_over_ranks(f0.elapsed_time(f1) / f64_steps, world, dev)
+        res["plain_f64"] = {"value": world * B * T / (f64_ms * 1e-3), "ms_per_step": f64_ms,
+                            "speedup_of_mixed": f64_ms / ms,
+                            "same_valid_flags": bool(torch.equal(f64_out.valid, out.valid))}
+        del f64_out
+        torch.cuda.empty_cache()
+    if rank == 0 and not args.no_accuracy:
+        res["accuracy_vs_oracle"] = accuracy(cfg, batch, out, T, fourbar)
+    return res, {"sim": sim, "db": db, "out": out, "status": status, "batch": batch, "graph": graph,
+                 "prec": prec, "mode": mode, "n_valid": n_valid}
+
+
+def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L):
+    """Roofline views of the hot kernels (algorithmic work of one launch / its event
+    time) and the binding one of the dominant kernel."""
+    import numpy as np
+    import torch
+    pk = peaks()
+    sm = torch.cuda.get_device_properties(out.valid.device).multi_processor_count
+    fp32_peak = FP32_LANES_PER_CLK_SM * sm * pk["sm_max_mhz"] * 1e6  # lane-ops/s, an FMA counts as one
+    nd_all = (batch.n_joints - (batch.jtype == 0).sum(1) - 1).astype(np.int64)
+    steps_alg = np.where(lock_np < 0, T, lock_np.astype(np.int64) + 1)
+    steps_alg = np.where(lock_np == -2, 0, steps_alg)
+    views = {}
+    if "mixed_emit" in kernels:
+        ms_e = kernels["mixed_emit"]["ms_per_launch"]
+        valid_np = out.valid.cpu().numpy().astype(bool)
+        nd_valid = nd_all[valid_np]
+        n_valid_joints = batch.n_joints[valid_np].astype(np.int64)
+        emit_steps, emit_dyads = rows * T, T * int(nd_valid.sum())
+        work = L.links_emit_census(sim.ctx, sim.plan, T, L.OUT_VALID_ONLY, out.lock_step, out.out_index,
+                                   out.traj.shape[0])
+        method_ops = int(METHOD_STEP_OPS * emit_steps + METHOD_DYAD_OPS * emit_dyads)
+        design_ops = int(SCREEN_STEP_OPS * emit_steps + SCREEN_DYAD_OPS * emit_dyads
+                         + DW_STEP_OPS * work["double_word_steps"] + DW_DYAD_OPS * work["double_word_dyads"])
+        real_bytes = int(n_valid_joints.sum()) * T * 8 + rows * T * 8  # the joints of each row + its path
+        written = rows * nmax * T * 8 + rows * T * 8 if out.traj.dim() == 4 else real_bytes
+        s = ms_e * 1e-3
+        views["mixed_emit"] = {
+            "hbm": {"bound": "hbm", "achieved": real_bytes / s / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": real_bytes / s / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": real_bytes,
+                    "bytes_written": written},
+            "alu": {"bound": "alu", "achieved": design_ops / s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": design_ops / s / fp32_peak, "algorithmic_ops": design_ops,
+                    "method_ops": method_ops, "emit_steps": emit_steps,
+                    "double_word_steps": work["double_word_steps"],
+                    "double_word_fraction": work["double_word_steps"] / max(emit_steps, 1)}}
+    if "mixed_screen" in kernels:
+        s = kernels["mixed_screen"]["ms_per_launch"] * 1e-3
+        method = int(dyad_steps * METHOD_DYAD_OPS + steps_alg.sum() * METHOD_STEP_OPS)
+        design = int(dyad_steps * SCREEN_DYAD_OPS + steps_alg.sum() * SCREEN_STEP_OPS)
+        views["mixed_screen"] = {
+            "alu": {"bound": "alu", "achieved": method / s / 1e12, "peak": fp32_peak / 1e12, "unit": "TFLOP/s",
+                    "frac": method / s / fp32_peak, "algorithmic_ops": method, "certified_ops": design,
+                    "certified_frac": design / s / fp32_peak, "dyad_steps_per_s": dyad_steps / s}}
+    if "plan_build" in kernels:
+        s = kernels["plan_build"]["ms_per_launch"] * 1e-3
+        nbytes = len(batch.n_joints) * (nmax * nmax + nmax + nmax * 8 + 4)
+        views["plan_build"] = {"hbm": {"bound": "hbm", "achieved": nbytes / s / 1e9, "peak": pk["hbm_gbs"],
+                                       "unit": "GB/s", "frac": nbytes / s / 1e9 / pk["hbm_gbs"],
+                                       "algorithmic_bytes": nbytes}}
+    top = max((k for k in kernels if k in views), key=lambda k: kernels[k]["share"], default=None)
+    if top is None:
+        return None, views
+    bind = BINDING.get(top, next(iter(views[top])))
+    roof = dict(views[top][bind])
+    roof.update({"kernel": top, "share_of_step": kernels[top]["share"], "peak_source": pk["src"],
+                 "binding_evidence": BINDING_EVIDENCE.get(top, ""),
+                 "traffic": TRAFFIC_PER_UNIT[top][0] * (rows if TRAFFIC_PER_UNIT[top][1] == "row" else len(lock_np))
+                 if top in TRAFFIC_PER_UNIT else None,
+                 "traffic_source": TRAFFIC_SOURCE})
+    return roof, views
+
+
+def e2e_run(state, args, world, local, full):
+    """The headline metric end to end through the public API: every step copies its
+    inputs from pinned host memory and its results (flags, lock steps, min_disc, valid
+    indices, coupler paths; with `full` every valid trajectory too) back to pinned host
+    memory.  Two input and two output buffers: step i computes while step i+1 uploads
+    and step i-1 drains."""
+    import numpy as np
+    import torch
+
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import to_device
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sim, batch, T = state["sim"], state["batch"], args.T
+    B = batch.B
+    prec, mode = state["prec"], state["mode"]
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (batch.n_joints, batch.adj, batch.jtype, batch.pos)]
+    if "dbs" not in state:
+        state["dbs"] = [state["db"], to_device(batch, dev)]
+        rows_cap = state["out"].traj.shape[0]
+        state["outs"] = [state["out"], sim.alloc(T, prec, mode, out_capacity=rows_cap)]
+        graphs = [state["graph"], None]
+        if state["graph"] is not None:
+            L.links_capture_begin(sim.ctx)
+            sim.build(state["dbs"][1], state["status"])
+            sim.simulate(T, prec, mode, out=state["outs"][1])
+            graphs[1] = L.links_capture_end(sim.ctx)
+        state["graphs"] = graphs
+    dbs, outs, graphs = state["dbs"], state["outs"], state["graphs"]
+    dev_in = [[d.n_joints, d.adj, d.jtype, d.pos] for d in dbs]
+    h2d_stream, copy_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    uploaded = [torch.cuda.Event() for _ in range(2)]
+    computed = [torch.cuda.Event() for _ in range(2)]
+    drained = [torch.cuda.Event() for _ in range(2)]
+    rows_cap = outs[0].traj.shape[0]
+    hb_rows = min(rows_cap, state["n_valid"] + 4096)
+    hbuf = [dict(valid=torch.empty(B, dtype=torch.uint8).pin_memory(),
+                 lock=torch.empty(B, dtype=torch.int16).pin_memory(),
+                 md=torch.empty(B, dtype=torch.float32).pin_memory(),
+                 n=torch.empty(1, dtype=torch.int32).pin_memory(),
+                 traj=torch.empty((hb_rows,) + tuple(outs[0].traj.shape[1:]), dtype=torch.float32).pin_memory()
+                 if full else None,
+                 path=torch.empty((hb_rows,) + tuple(outs[0].path.shape[1:]), dtype=torch.float32).pin_memory(),
+                 idx=torch.empty(hb_rows, dtype=torch.int32).pin_memory()) for _ in range(2)]
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    nmax = batch.nmax
+
+    def drain(j):
+        o, hb = outs[j], hbuf[j]
+        with torch.cuda.stream(copy_stream):
+            copy_stream.wait_event(computed[j])
+            hb["valid"].copy_(o.valid[:B], non_blocking=True)
+            hb["lock"].copy_(o.lock_step[:B], non_blocking=True)
+            hb["md"].copy_(o.min_disc[:B], non_blocking=True)
+            hb["n"].copy_(o.n_out, non_blocking=True)
+        copy_stream.synchronize()
+        n = min(int(hb["n"][0]), hb_rows)
+        with torch.cuda.stream(copy_stream):
+            if full:
+                hb["traj"][:n].copy_(o.traj[:n], non_blocking=True)
+            hb["path"][:n].copy_(o.path[:n], non_blocking=True)
+            hb["idx"][:n].copy_(o.out_index[:n], non_blocking=True)
+            drained[j].record(copy_stream)
+        return B * 7 + 4 + n * (T * 8 + 4) + (n * nmax * T * 8 if full else 0)
+
+    def upload(i):
+        j = i % 2
+        with torch.cuda.stream(h2d_stream):
+            if i >= 2:
+                h2d_stream.wait_event(computed[j])  # step i-2 has read input buffer j
+            for d, h in zip(dev_in[j], host_in):
+                d.copy_(h, non_blocking=True)
+            uploaded[j].record(h2d_stream)
+
+    total = 0
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    upload(0)
+    for i in range(args.e2e_steps):
+        j = i % 2
+        if i >= 2:
+            stream.wait_event(drained[j])  # output buffer j is free again
+        stream.wait_event(uploaded[j])
+        if graphs[j] is not None:
+            L.links_graph_launch(sim.ctx, graphs[j])
+        else:
+            sim.build(dbs[j], state["status"])
+            sim.simulate(T, prec, mode, out=outs[j])
+        computed[j].record(stream)
+        if i + 1 < args.e2e_steps:
+            upload(i + 1)
+        if i >= 1:
+            total += drain(1 - j)
+    total += drain((args.e2e_steps - 1) % 2)
+    copy_stream.synchronize()
+    torch.cuda.synchronize(dev)
+    el = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world, dev)
+    barrier(world)
+    del hbuf
+    return {"value": world * B * T / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": total // args.e2e_steps, "ms_per_step": el * 1e3}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=1_000_000)
+    ap.add_argument("--config", type=int, default=3, choices=[2, 3],
+                    help="the headline configuration (3: 4M candidates of 6-20 joints; 2: 1M of 6-8)")
     ap.add_argument("--T", type=int, default=200)
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--headline-batch", type=int, default=0,
+                    help="candidates of the headline configuration (0: the configuration's own, for small test runs)")
+    ap.add_argument("--e2e-steps", type=int, default=12)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-seconds", type=float, default=12.0)
+    ap.add_argument("--ref-sample", type=int, default=65536, help="candidates per step of the reference arm")
+    ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true")
+    ap.add_argument("--no-e2e-full", action="store_true")
     ap.add_argument("--path-db", type=int, default=1_000_000)
     ap.add_argument("--path-queries", type=int, default=1024)
     ap.add_argument("--no-path-stage", action="store_true")
@@ -655,11 +1100,13 @@ def main():
     ap.add_argument("--no-paper-generator", action="store_true")
     ap.add_argument("--no-curation", action="store_true")
     ap.add_argument("--no-topology", action="store_true")
+    ap.add_argument("--no-two-stage", action="store_true")
     ap.add_argument("--topology-samples", type=int, default=1_000_000)
     ap.add_argument("--serve-requests", type=int, default=4000)
     ap.add_argument("--serve-rate", type=float, default=2000.0)
     ap.add_argument("--serve-pool", type=int, default=600_000)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB of device arena")
+    ap.add_argument("--batch", type=int, default=300_000, help="candidates of --profile-kernels")
     ap.add_argument("--profile-kernels", action="store_true",
                     help="launch each hot kernel once on a mid-size case (for a profiler) and exit")
     args = ap.parse_args()
@@ -671,273 +1118,59 @@ def main():
         run_reference(args, world, rank)
         return
 
-    import numpy as np
     import torch
-
-    from paper_2208_14567_gb300 import inputs as I
-    from paper_2208_14567_gb300 import links as L
-    from paper_2208_14567_gb300.api import Simulator, to_device
-
     torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    T, B = args.T, args.batch
-    batch = I.dyad_batch(B, 6, 8, seed=rank)
-    nmax = batch.nmax
-    db = to_device(batch, dev)
-    stream = torch.cuda.current_stream(dev)
-    sim = Simulator(B, nmax, device=local, stream=stream)
-    status = torch.empty(B, dtype=torch.int32, device=dev)
-    # size the valid rows from a flags-only pass (the same inputs are reused every step)
-    sim.build(db, status)
-    probe = sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
-    sim.sync()
-    out = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=int(probe.n_out[0]) + 1024)
-    del probe
-
-    def step():
-        sim.build(db, status)
-        sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=out)
-
-    for _ in range(args.warmup):
-        step()
-    sim.sync()
-    launches0 = L.links_launch_count(sim.ctx)
-
-    # ---- timed region: device time, inputs resident
-    barrier(world)
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local) as clk:
-        clk.wait_ready()
-        clk.mark_start()
-        e0.record(stream)
-        for _ in range(args.steps):
-            step()
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        clk.mark_end()
-    barrier(world)
-    ms = e0.elapsed_time(e1) / args.steps
-    launches = (L.links_launch_count(sim.ctx) - launches0) // args.steps
-    ms = max_over_ranks(ms, world, dev)
-    sim.sync()
-    n_valid = int(out.n_out[0])
-    lock_np = out.lock_step.cpu().numpy()
-    dyad_steps = algorithmic_dyad_steps(batch, lock_np, T)
-    value = world * B * T / (ms * 1e-3)
-
-    # ---- per-kernel event timing over the same steps (second pass)
-    L.links_profile(sim.ctx, True)
-    prof_steps = max(1, min(args.steps, 5))
-    for _ in range(prof_steps):
-        step()
-    prof = L.links_profile_read(sim.ctx)
-    L.links_profile(sim.ctx, False)
-    total = sum(v[0] for v in prof.values())
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches_per_step": v[1] / prof_steps,
-                   "share": v[0] / total if total else 0.0} for k, v in prof.items()}
-    top = max(kernels, key=lambda k: kernels[k]["share"])
-    pk = peaks()
-    rows = n_valid
-    fp32_peak = FP32_LANES_PER_CLK_SM * SM_COUNT * pk["sm_max_mhz"] * 1e6  # ops/s, an FMA counts as one
-    steps_alg = np.where(lock_np < 0, T, lock_np.astype(np.int64) + 1)
-    steps_alg = np.where(lock_np == -2, 0, steps_alg)
-    views = {}
-    if "mixed_emit" in kernels:
-        ms_e = kernels["mixed_emit"]["ms_per_launch"]
-        # the work the emit's precision design does: the certified FP32 chain for every
-        # emitted step (valid rows x T), the double-word chain again where the bound
-        # exceeded the tolerance (counted by the census, outside the timed steps)
-        valid_np = out.valid.cpu().numpy().astype(bool)
-        nd_valid = (batch.n_joints - (batch.jtype == 0).sum(1) - 1)[valid_np].astype(np.int64)
-        emit_steps, emit_dyads = rows * T, T * int(nd_valid.sum())
-        work = L.links_emit_census(sim.ctx, sim.plan, T, L.OUT_VALID_ONLY, out.lock_step, out.out_index,
-                                   out.traj.shape[0])
-        ops = int(SCREEN_STEP_OPS * emit_steps + SCREEN_DYAD_OPS * emit_dyads
-                  + DW_STEP_OPS * work["double_word_steps"] + DW_DYAD_OPS * work["double_word_dyads"])
-        nbytes = rows * nmax * T * 8 + rows * T * 8
-        views["mixed_emit"] = {
-            "alu": {"bound": "alu", "achieved": ops / (ms_e * 1e-3) / 1e12, "peak": fp32_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": ops / (ms_e * 1e-3) / fp32_peak, "algorithmic_ops": ops,
-                    "emit_steps": emit_steps, "double_word_steps": work["double_word_steps"],
-                    "double_word_fraction": work["double_word_steps"] / max(emit_steps, 1)},
-            "hbm": {"bound": "hbm", "achieved": nbytes / (ms_e * 1e-3) / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": nbytes / (ms_e * 1e-3) / 1e9 / pk["hbm_gbs"], "algorithmic_bytes": nbytes}}
-    if "mixed_screen" in kernels:
-        ms_s = kernels["mixed_screen"]["ms_per_launch"]
-        ops = int(dyad_steps * SCREEN_DYAD_OPS + steps_alg.sum() * SCREEN_STEP_OPS)
-        views["mixed_screen"] = {
-            "alu": {"bound": "alu", "achieved": ops / (ms_s * 1e-3) / 1e12, "peak": fp32_peak / 1e12,
-                    "unit": "TFLOP/s", "frac": ops / (ms_s * 1e-3) / fp32_peak, "algorithmic_ops": ops,
-                    "dyad_steps_per_s": dyad_steps / (ms_s * 1e-3)}}
-    if "plan_build" in kernels:
-        ms_b = kernels["plan_build"]["ms_per_launch"]
-        nbytes = B * (nmax * nmax + nmax + nmax * 8 + 4)
-        views["plan_build"] = {"hbm": {"bound": "hbm", "achieved": nbytes / (ms_b * 1e-3) / 1e9, "peak": pk["hbm_gbs"],
-                                       "unit": "GB/s", "frac": nbytes / (ms_b * 1e-3) / 1e9 / pk["hbm_gbs"],
-                                       "algorithmic_bytes": nbytes}}
-    # the binding roofline of the dominant kernel: of its views (ALU issue, HBM bytes),
-    # the one it runs closest to
-    tv = views.get(top, {})
-    bind = max(tv, key=lambda k: tv[k]["frac"]) if tv else None
-    roof = dict(tv.get(bind, {}))
-    # DRAM bytes per launch from the committed ncu capture of the same kernels
-    # (300,000 candidates; 74,163 valid rows), scaled by the units this launch processed
-    per_unit = {"mixed_emit": (1053.7e6 / 74163, rows), "mixed_screen": (141.7e6 / 300000, B),
-                "plan_build": (158.2e6 / 300000, B)}
-    traffic = per_unit[top][0] * per_unit[top][1] if top in per_unit else None
-    roof.update({"traffic": traffic, "traffic_source": "ncu dram bytes of a 300k-candidate capture, scaled",
-                 "kernel": top, "peak_source": pk["src"]})
-
-    # ---- the paper's two-stage screen on the same inputs: T/4 positions, then T for the
-    # mechanisms valid on the coarse grid (same valid flags and rows)
-    two = None
-    if T % 4 == 0:
-        n_low = torch.zeros(1, dtype=torch.int32, device=dev)
-        out2 = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=out.traj.shape[0])
-        sim.build(db, status)
-        sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
-        sim.sync()
-        t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        t0e.record(stream)
-        for _ in range(args.steps):
-            sim.build(db, status)
-            sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
-        t1e.record(stream)
-        torch.cuda.synchronize(dev)
-        ms2 = t0e.elapsed_time(t1e) / args.steps
-        nl, n2 = int(n_low.item()), int(out2.n_out[0])
-        two = {"T_low": T // 4, "ms_per_step": ms2, "mechanism_steps_per_s": B * T / (ms2 * 1e-3),
-               "valid_on_coarse_grid": nl, "valid": n2, "false_valid_rate": (nl - n2) / max(nl, 1),
-               "same_valid_flags": bool(torch.equal(out2.valid, out.valid))}
-        del out2
-        torch.cuda.empty_cache()
-
-    # ---- plain FP64 kernel on the same inputs (the comparator named by the metric)
-    f64_out = sim.alloc(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out_capacity=max(n_valid, 1))
-    sim.build(db, status)
-    sim.simulate(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out=f64_out)
-    sim.sync()
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    f64_steps = 2
-    for _ in range(f64_steps):
-        sim.build(db, status)
-        sim.simulate(T, L.PLAIN_F64, L.OUT_VALID_ONLY, out=f64_out)
-    f1.record(stream)
-    torch.cuda.synchronize(dev)
-    f64_ms = max_over_ranks(f0.elapsed_time(f1) / f64_steps, world, dev)
-    same_flags = bool(torch.equal(f64_out.valid, out.valid))
-    del f64_out
-    torch.cuda.empty_cache()
-
-    # ---- end to end through the public API: pinned host inputs in, flags + valid rows out.
-    # Two input and two output buffers: while step i computes, the inputs of step i+1
-    # go up on one copy stream and the rows of step i-1 drain on another (the host
-    # link, ~190-210 GB/s each way, runs beside the compute).
-    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-               for a in (batch.n_joints, batch.adj, batch.jtype, batch.pos)]
-    dbs = [db, to_device(batch, dev)]
-    dev_in = [[d.n_joints, d.adj, d.jtype, d.pos] for d in dbs]
-    h2d_stream = torch.cuda.Stream(dev)
-    uploaded = [torch.cuda.Event() for _ in range(2)]
-    rows_cap = max(n_valid, 1) + 1024
-    outs = [out, sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=rows_cap)]
-    hbuf = [dict(valid=torch.empty(B, dtype=torch.uint8).pin_memory(),
-                 lock=torch.empty(B, dtype=torch.int16).pin_memory(),
-                 md=torch.empty(B, dtype=torch.float32).pin_memory(),
-                 n=torch.empty(1, dtype=torch.int32).pin_memory(),
-                 traj=torch.empty((rows_cap,) + tuple(out.traj.shape[1:]), dtype=torch.float32).pin_memory(),
-                 path=torch.empty((rows_cap,) + tuple(out.path.shape[1:]), dtype=torch.float32).pin_memory(),
-                 idx=torch.empty(rows_cap, dtype=torch.int32).pin_memory()) for _ in range(2)]
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    copy_stream = torch.cuda.Stream(dev)
-    computed = [torch.cuda.Event() for _ in range(2)]
-    drained = [torch.cuda.Event() for _ in range(2)]
-
-    def drain(j, full):
-        """Copy the results of the step held in buffer j: flags, count, valid indices and
-        coupler paths; with `full` also every valid trajectory."""
-        o, hb = outs[j], hbuf[j]
-        with torch.cuda.stream(copy_stream):
-            copy_stream.wait_event(computed[j])
-            hb["valid"].copy_(o.valid[:B], non_blocking=True)
-            hb["lock"].copy_(o.lock_step[:B], non_blocking=True)
-            hb["md"].copy_(o.min_disc[:B], non_blocking=True)
-            hb["n"].copy_(o.n_out, non_blocking=True)
-        copy_stream.synchronize()
-        n = min(int(hb["n"][0]), rows_cap)
-        with torch.cuda.stream(copy_stream):
-            if full:
-                hb["traj"][:n].copy_(o.traj[:n], non_blocking=True)
-            hb["path"][:n].copy_(o.path[:n], non_blocking=True)
-            hb["idx"][:n].copy_(o.out_index[:n], non_blocking=True)
-            drained[j].record(copy_stream)
-        return B * 7 + 4 + n * (T * 8 + 4) + (n * nmax * T * 8 if full else 0)
-
-    def e2e_run(full):
-        nonlocal_total = 0
-        barrier(world)
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        def upload(i):
-            j = i % 2
-            with torch.cuda.stream(h2d_stream):
-                if i >= 2:
-                    h2d_stream.wait_event(computed[j])  # step i-2 has read input buffer j
-                for d, h in zip(dev_in[j], host_in):
-                    d.copy_(h, non_blocking=True)
-                uploaded[j].record(h2d_stream)
-
-        upload(0)
-        for i in range(args.e2e_steps):
-            j = i % 2
-            if i >= 2:
-                stream.wait_event(drained[j])  # output buffer j is free again
-            stream.wait_event(uploaded[j])
-            sim.build(dbs[j], status)
-            sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, out=outs[j])
-            computed[j].record(stream)
-            if i + 1 < args.e2e_steps:
-                upload(i + 1)
-            if i >= 1:
-                nonlocal_total += drain(1 - j, full)
-        nonlocal_total += drain((args.e2e_steps - 1) % 2, full)
-        copy_stream.synchronize()
-        torch.cuda.synchronize(dev)
-        el = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world, dev)
-        barrier(world)
-        return {"value": world * B * T / el, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": nonlocal_total // args.e2e_steps, "ms_per_step": el * 1e3}
-
-    e2e = e2e_run(False)
+    # all work on one created stream (the legacy default stream cannot be captured in a graph)
+    torch.cuda.set_stream(torch.cuda.Stream(torch.device("cuda", local)))
+    head = headline_config(args)
+    res, state = run_config(head, args, world, rank, local, args.steps, args.warmup, headline=True)
+    e2e = e2e_run(state, args, world, local, full=False)
     e2e["result"] = "flags, lock steps, min_disc, valid indices and valid coupler paths to pinned host memory"
     e2e["pipelined"] = "two input and two output buffers; step i computes while step i+1 uploads and step i-1 drains"
-    e2e_full = e2e_run(True)
-    e2e_full["result"] = "as e2e plus every valid trajectory [rows, 8, 200, 2] (host-link bound, ~193 GB/s)"
-
+    e2e_full = None
+    if not args.no_e2e_full:
+        e2e_full = e2e_run(state, args, world, local, full=True)
+        e2e_full["result"] = "as e2e plus every valid trajectory (host-link bound)"
+    two = None
+    if not args.no_two_stage and args.T % 4 == 0 and world == 1:
+        two = two_stage(state, args, local)
+    state["sim"].close()
+    del state
+    torch.cuda.empty_cache()
     if rank != 0:
         return
-    ps = None if args.no_path_stage or world > 1 else path_stage(args, local, stream)
-    sv = None if args.no_serve or world > 1 else serve_stage(args, local, stream)
-    pg = None if args.no_paper_generator or world > 1 else paper_generator_stage(args, local, stream)
-    cu = None if args.no_curation or world > 1 else curation_stage(args, local, stream)
-    tp = None if args.no_topology or world > 1 else topology_stage(args, local, stream)
-    cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(T)
+    configs = {}
+    if not args.no_other_configs and world == 1:
+        for c in (1, 2, 3):
+            if c == args.config:
+                continue
+            r, st = run_config(CONFIGS[c], args, world, rank, local, min(args.steps, 20), 3)
+            st["sim"].close()
+            del st
+            torch.cuda.empty_cache()
+            configs[CONFIGS[c]["name"]] = r
+    ps = None if args.no_path_stage or world > 1 else path_stage(args, local, torch.cuda.current_stream())
+    sv = None if args.no_serve or world > 1 else serve_stage(args, local, torch.cuda.current_stream())
+    pg = None if args.no_paper_generator or world > 1 else paper_generator_stage(args, local,
+                                                                                  torch.cuda.current_stream())
+    cu = None if args.no_curation or world > 1 else curation_stage(args, local, torch.cuda.current_stream())
+    tp = None if args.no_topology or world > 1 else topology_stage(args, local, torch.cuda.current_stream())
+    cb = None if args.no_cpu_baseline or world > 1 else cpu_baseline(head, args)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch": B, "T": T, "joints": "6-8", "precision": "mixed",
-                   "out_mode": "valid_only", "valid_rows": n_valid,
-                   "l2": "inputs 140 MB per step exceed the 126 MB L2; no flush", "parallelism": f"replicas x{world}"},
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": config_dict(head, args, world),
+        "valid_rows": res["valid_rows"],
+        "screen_lanes_autotuned": res["screen_lanes_autotuned"],
+        "plain_f64": res.get("plain_f64"),
+        "accuracy_vs_oracle": res.get("accuracy_vs_oracle"),
+        "algorithmic_dyad_steps_per_step": res["algorithmic_dyad_steps_per_step"],
+        "kernels": res["kernels"],
+        "roofline": res.get("roofline"),
+        "roofline_views": res.get("roofline_views"),
+        "configs": configs,
         "two_stage_screen": two,
-        "plain_f64": {"value": world * B * T / (f64_ms * 1e-3), "ms_per_step": f64_ms,
-                      "speedup_of_mixed": f64_ms / ms, "same_valid_flags": same_flags},
-        "algorithmic_dyad_steps_per_step": dyad_steps,
-        "kernels": kernels,
-        "roofline": roof,
-        "roofline_views": views,
         "cpu_baseline": cb,
         "path_stage": ps,
         "serve": sv,
@@ -951,14 +1184,47 @@ def main():
                               "CPU node, 10,000 mechanisms",
             "v100_seconds_per_10k": 0.1823,
             "v100_mech_steps_per_s_if_T200": 10000 * 200 / 0.1823,
-            "this_run_over_that": value / (10000 * 200 / 0.1823),
+            "this_run_over_that": res["value"] / (10000 * 200 / 0.1823),
         },
         "e2e": e2e,
         "e2e_full": e2e_full,
-        "gpu_launches": int(launches * args.steps),
-        "clocks": clk.summary(),
+        "gpu_launches": res["gpu_launches"],
+        "clocks": res.get("clocks"),
     }
     print(json.dumps(line), flush=True)
+
+
+def two_stage(state, args, local):
+    """The paper's two-stage screen on the headline inputs: T/4 positions, then T for the
+    mechanisms valid on the coarse grid (same valid flags and rows)."""
+    import torch
+
+    from paper_2208_14567_gb300 import links as L
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    sim, db, out, T = state["sim"], state["db"], state["out"], args.T
+    n_low = torch.zeros(1, dtype=torch.int32, device=dev)
+    out2 = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=out.traj.shape[0])
+    sim.build(db, state["status"])
+    sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
+    sim.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record(stream)
+    for _ in range(reps):
+        sim.build(db, state["status"])
+        sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms2 = e0.elapsed_time(e1) / reps
+    B = db.B
+    nl, n2 = int(n_low.item()), int(out2.n_out[0])
+    r = {"T_low": T // 4, "ms_per_step": ms2, "mechanism_steps_per_s": B * T / (ms2 * 1e-3),
+         "valid_on_coarse_grid": nl, "valid": n2, "false_valid_rate": (nl - n2) / max(nl, 1),
+         "same_valid_flags": bool(torch.equal(out2.valid, out.valid))}
+    del out2
+    torch.cuda.empty_cache()
+    return r
 
 
 if __name__ == "__main__":

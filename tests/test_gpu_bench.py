@@ -15,9 +15,9 @@ def test_bench_line_contract():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--batch", "100000", "--steps", "3", "--warmup", "3",
-           "--e2e-steps", "3", "--no-path-stage", "--no-serve", "--no-paper-generator", "--no-curation",
-           "--no-topology", "--no-cpu-baseline"]
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--headline-batch", "100000", "--steps", "3",
+           "--warmup", "3", "--e2e-steps", "3", "--no-path-stage", "--no-serve", "--no-paper-generator",
+           "--no-curation", "--no-topology", "--no-cpu-baseline", "--no-other-configs", "--no-two-stage"]
     r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]

@@ -63,7 +63,7 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     env = dict(os.environ, BENCH_BACKEND="gloo", OMP_NUM_THREADS="1")
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(free_port()), os.path.join(ROOT, "bench.py"),
-           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3", "--ref-seconds", "0.5"]
+           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "3", "--ref-sample", "2000"]
     r = subprocess.run(cmd, cwd=str(tmp_path), env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
     lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
@@ -71,3 +71,9 @@ def test_reference_arm_under_torchrun_prints_once(tmp_path):
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+    # the reference arm describes the same configuration as the GPU arm's line
+    sys.path.insert(0, ROOT)
+    import bench
+    args = type("A", (), {"T": 200, "config": 3, "headline_batch": 0})()
+    assert d["config"] == bench.config_dict(bench.headline_config(args), args, 2)
+    assert d["steps"] == 2 and d["ms_per_step"] > 0
