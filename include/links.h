@@ -407,14 +407,42 @@ LINKS_API int links_launch_count(links_ctx ctx, int64_t* out);
 LINKS_API int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_t* out_index,
                                          int64_t out_capacity, int32_t* n_out, void* cuda_stream);
 
-/* Autotuner of the mixed-precision screen: times it with 8, 16 and 32 lanes per
- * mechanism (consecutive steps of one mechanism per lane group) on the plan as last
- * built, over T steps, and keeps the fastest for plans of this n_max on this
- * context (*lanes receives it; may be NULL).  Allocates scratch and synchronizes:
- * call it before capturing a graph.  Without it the screen uses 8 lanes. */
+/* ---- Kernel shapes (no counterpart in the paper; how the batched kernels are laid out
+ * on the GPU).  Each context keeps a table of shapes per n_max; the keys: */
+#define LINKS_TUNE_BUILDER 0      /* device plan builder: 0 default (warp-flat), 1 a thread
+                                     per mechanism (n_max <= 8 only), 2 warp-flat: a lane
+                                     per mechanism for the solve order, a lane per dyad for
+                                     the geometry */
+#define LINKS_TUNE_SCREEN_LANES 1 /* lanes per mechanism of the screen: 8 (default), 16, 32 */
+#define LINKS_TUNE_SCREEN_STEPS 2 /* steps per lane of the screen: 0 by size (2 when
+                                     n_max <= 9), 1, 2 (n_max <= 16 only) */
+#define LINKS_TUNE_SCREEN_CTAS 3  /* CTAs per SM of the persistent screen, 0 = as many as fit */
+#define LINKS_TUNE_EMIT_DWS 4     /* double-word slots of the emit: -1 by size (shared
+                                     memory when n_max <= 12), 0 thread-local, 1 shared */
+#define LINKS_TUNE_EMIT_CTAS 5    /* CTAs per SM of the emit, 0 = as many as fit */
+
+/* Autotuner: on the plan as last built, over T steps, times the screen with every shape
+ * (lanes 8/16/32 x steps per lane 1/2 x CTAs per SM all/2/1), then the emit (shared or
+ * thread-local double-word slots x CTAs per SM all/2/1) on up to 16384 valid rows of
+ * that screen's result, and keeps the fastest of each in the context's table for this
+ * n_max (*lanes receives the screen's lanes; may be NULL).  Each shape gives the same
+ * outputs; only the time differs.  Allocates scratch and synchronizes: call it before
+ * capturing a graph.  Without it the defaults above apply. */
 LINKS_API int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes);
 
-/* Sets the screen's lanes per mechanism (8, 16 or 32) for plans of this n_max. */
+/* Sets (or reads) one key of the shape table for plans of n_max joints (2..32).
+ * LINKS_EINVAL for an unknown key or a value outside the key's range for that n_max. */
+LINKS_API int links_set_tuning(links_ctx ctx, int n_max, int key, int value);
+LINKS_API int links_get_tuning(links_ctx ctx, int n_max, int key, int* value);
+/* Writes the context's shape table to a text file (a header naming the device and its SM
+ * count, then one line per n_max: n_max and the six keys in key order), or reads one
+ * back (LINKS_ESTATE if it was written on another kind of device, LINKS_EINVAL if
+ * malformed or out of range; nothing is loaded then). */
+LINKS_API int links_tuning_save(links_ctx ctx, const char* path);
+LINKS_API int links_tuning_load(links_ctx ctx, const char* path);
+
+/* Sets the screen's lanes per mechanism (8, 16 or 32) for plans of this n_max
+ * (links_set_tuning with LINKS_TUNE_SCREEN_LANES). */
 LINKS_API int links_set_screen_lanes(links_ctx ctx, int n_max, int lanes);
 
 /* Begin / end capturing the context's stream into a reusable graph. */

@@ -505,7 +505,7 @@ int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes) {
   int st = LINKS_OK;
   const TTable* tab = get_table(ctx, T, &st);
   if (!tab) return st;
-  return autotune_screen(ctx, plan, tab, lanes);
+  return autotune(ctx, plan, tab, lanes);
 }
 
 int links_chamfer_first_under(links_ctx ctx, int Q, int64_t M, int T, const float* queries, const float* db,
@@ -548,9 +548,110 @@ int links_set_chamfer_prune(links_ctx ctx, int on) {
 }
 
 int links_set_screen_lanes(links_ctx ctx, int n_max, int lanes) {
-  if (!ctx) return set_error(LINKS_EINVAL, "links_set_screen_lanes: NULL ctx");
-  if (lanes != 8 && lanes != 16 && lanes != 32) return set_error(LINKS_EINVAL, "links_set_screen_lanes: lanes must be 8, 16 or 32");
-  ctx->screen_lanes[n_max] = lanes;
+  return links_set_tuning(ctx, n_max, LINKS_TUNE_SCREEN_LANES, lanes);
+}
+
+static int* tuning_field(links::Tuning& t, int key) {
+  switch (key) {
+    case LINKS_TUNE_BUILDER: return &t.builder;
+    case LINKS_TUNE_SCREEN_LANES: return &t.screen_lanes;
+    case LINKS_TUNE_SCREEN_STEPS: return &t.screen_steps;
+    case LINKS_TUNE_SCREEN_CTAS: return &t.screen_ctas;
+    case LINKS_TUNE_EMIT_DWS: return &t.emit_dws;
+    case LINKS_TUNE_EMIT_CTAS: return &t.emit_ctas;
+    default: return nullptr;
+  }
+}
+
+static bool tuning_value_ok(int n_max, int key, int v) {
+  switch (key) {
+    case LINKS_TUNE_BUILDER: return v == 0 || v == 2 || (v == 1 && n_max <= 8);
+    case LINKS_TUNE_SCREEN_LANES: return v == 8 || v == 16 || v == 32;
+    case LINKS_TUNE_SCREEN_STEPS: return v == 0 || v == 1 || (v == 2 && n_max <= 16);
+    case LINKS_TUNE_SCREEN_CTAS: return v >= 0 && v <= 32;
+    case LINKS_TUNE_EMIT_DWS: return v >= -1 && v <= 1;
+    case LINKS_TUNE_EMIT_CTAS: return v >= 0 && v <= 32;
+    default: return false;
+  }
+}
+
+int links_set_tuning(links_ctx ctx, int n_max, int key, int value) {
+  if (!ctx) return set_error(LINKS_EINVAL, "links_set_tuning: NULL ctx");
+  if (n_max < 2 || n_max > LINKS_MAX_JOINTS) return set_error(LINKS_EINVAL, "links_set_tuning: n_max out of [2, 32]");
+  links::Tuning t = links::tuning_of(ctx, n_max);
+  int* f = tuning_field(t, key);
+  if (!f) return set_error(LINKS_EINVAL, "links_set_tuning: unknown key");
+  if (!tuning_value_ok(n_max, key, value)) return set_error(LINKS_EINVAL, "links_set_tuning: value out of range for this key and n_max");
+  *f = value;
+  ctx->tuning[n_max] = t;
+  return LINKS_OK;
+}
+
+int links_get_tuning(links_ctx ctx, int n_max, int key, int* value) {
+  if (!ctx || !value) return set_error(LINKS_EINVAL, "links_get_tuning: NULL argument");
+  links::Tuning t = links::tuning_of(ctx, n_max);
+  int* f = tuning_field(t, key);
+  if (!f) return set_error(LINKS_EINVAL, "links_get_tuning: unknown key");
+  *value = *f;
+  return LINKS_OK;
+}
+
+// Text file: a header naming the device, then one line per n_max with the six keys.
+int links_tuning_save(links_ctx ctx, const char* path) {
+  if (!ctx || !path) return set_error(LINKS_EINVAL, "links_tuning_save: NULL argument");
+  cudaDeviceProp prop;
+  LINKS_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
+  FILE* f = fopen(path, "w");
+  if (!f) return set_error(LINKS_EINVAL, std::string("links_tuning_save: cannot open ") + path);
+  fprintf(f, "links-tuning 1 sms %d device %s\n", prop.multiProcessorCount, prop.name);
+  for (const auto& kv : ctx->tuning) {
+    const links::Tuning& t = kv.second;
+    fprintf(f, "%d %d %d %d %d %d %d\n", kv.first, t.builder, t.screen_lanes, t.screen_steps, t.screen_ctas,
+            t.emit_dws, t.emit_ctas);
+  }
+  const bool ok = fclose(f) == 0;
+  return ok ? LINKS_OK : set_error(LINKS_EINVAL, std::string("links_tuning_save: write failed: ") + path);
+}
+
+int links_tuning_load(links_ctx ctx, const char* path) {
+  if (!ctx || !path) return set_error(LINKS_EINVAL, "links_tuning_load: NULL argument");
+  cudaDeviceProp prop;
+  LINKS_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
+  FILE* f = fopen(path, "r");
+  if (!f) return set_error(LINKS_EINVAL, std::string("links_tuning_load: cannot open ") + path);
+  char name[256] = {0};
+  int version = 0, sms = 0;
+  if (fscanf(f, "links-tuning %d sms %d device %255[^\n]", &version, &sms, name) != 3 || version != 1) {
+    fclose(f);
+    return set_error(LINKS_EINVAL, "links_tuning_load: not a tuning file");
+  }
+  if (sms != prop.multiProcessorCount || std::string(name) != prop.name) {
+    fclose(f);
+    return set_error(LINKS_ESTATE, "links_tuning_load: the file was tuned on another device");
+  }
+  std::map<int, links::Tuning> table;
+  int n, v[6];
+  int st = LINKS_OK;
+  while (fscanf(f, "%d %d %d %d %d %d %d", &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 7) {
+    links::Tuning t;
+    const int keys[6] = {LINKS_TUNE_BUILDER, LINKS_TUNE_SCREEN_LANES, LINKS_TUNE_SCREEN_STEPS,
+                         LINKS_TUNE_SCREEN_CTAS, LINKS_TUNE_EMIT_DWS, LINKS_TUNE_EMIT_CTAS};
+    bool ok = n >= 2 && n <= LINKS_MAX_JOINTS;
+    for (int k = 0; k < 6 && ok; ++k) {
+      ok = tuning_value_ok(n, keys[k], v[k]);
+      if (ok) *tuning_field(t, keys[k]) = v[k];
+    }
+    if (!ok) {
+      st = set_error(LINKS_EINVAL, "links_tuning_load: an entry is out of range");
+      break;
+    }
+    table[n] = t;
+  }
+  const bool at_end = feof(f) != 0;
+  fclose(f);
+  if (st) return st;
+  if (!at_end) return set_error(LINKS_EINVAL, "links_tuning_load: malformed entry");
+  for (const auto& kv : table) ctx->tuning[kv.first] = kv.second;
   return LINKS_OK;
 }
 

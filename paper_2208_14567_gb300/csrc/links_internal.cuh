@@ -65,6 +65,16 @@ struct TTable {
 
 struct ServeState;
 void serve_free(ServeState* s);
+
+// Kernel shapes for plans of one n_max (links_set_tuning; the autotuner's table).
+struct Tuning {
+  int builder = 0;       // 0 default (warp-flat), 1 thread per mechanism (n_max <= 8), 2 warp-flat
+  int screen_lanes = 8;  // lanes per mechanism: 8, 16, 32
+  int screen_steps = 0;  // steps per lane: 0 by size (2 when n_max <= 9), 1, 2
+  int screen_ctas = 0;   // CTAs per SM of the persistent screen; 0 = as many as fit
+  int emit_dws = -1;     // double-word slots of the emit in shared memory: -1 by size, 0, 1
+  int emit_ctas = 0;     // CTAs per SM of the emit; 0 = as many as fit
+};
 }  // namespace links
 
 struct links_ctx_s {
@@ -88,8 +98,8 @@ struct links_ctx_s {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   links::ServeState* serve = nullptr;
-  std::map<int, int> screen_lanes;  // autotuned lanes per mechanism, by n_max
-  int chamfer_prune = 1;             // lower-bound pruning in links_chamfer_topk
+  std::map<int, links::Tuning> tuning;  // kernel shapes by n_max (set or autotuned)
+  int chamfer_prune = 1;                // lower-bound pruning in links_chamfer_topk
 };
 
 struct links_plan_s {
@@ -166,9 +176,11 @@ int emit_census(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode,
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
-// Times the screen with 8, 16 and 32 lanes per mechanism on the built plan and keeps
-// the fastest for this n_max (allocates scratch; not inside a capture).
-int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes);
+// The kernel shapes for plans of n_max joints (defaults where none were set).
+Tuning tuning_of(links_ctx ctx, int n_max);
+// Times the screen's and the emit's shapes on the built plan and keeps the fastest for
+// this n_max (allocates scratch; not inside a capture).
+int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes);
 // Shared by both precisions: rows of the valid mechanisms in index order.
 // A first screen of the OK mechanisms (see simulate_prescreened).
 using Prescreen = std::function<int(links_ctx, links_plan, const TTable*, uint8_t*, int16_t*, float*)>;

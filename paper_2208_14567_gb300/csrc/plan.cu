@@ -9,9 +9,10 @@
 // (Sec. "1-DOF Operator"): apart from ground-ground links and the crank, every simple
 // joint owns exactly two links.
 //
-// The builder runs on host threads and in CUDA kernels: one thread per mechanism
-// (build_one) for n_max <= 8, a group of 16 or 32 lanes per mechanism (build_group)
-// for larger mechanisms.  All produce bit-identical plans.
+// The builder runs on host threads (build_one) and in CUDA kernels: the warp-flat
+// builder (a lane per mechanism for the search, a lane per dyad for the geometry) and,
+// for n_max <= 8 on request, a thread per mechanism (build_one).  All produce
+// bit-identical plans.
 #include <algorithm>
 #include <thread>
 #include <vector>
@@ -121,6 +122,57 @@ LINKS_HD float u2f(uint32_t u) {
 // |(x, y)| rounded up a little (a bound, identical on host and device).
 LINKS_HD float hyp_up(float x, float y) {
   return fmul(fsqrt_rn(fadd(fmul(x, x), fmul(y, y))), 1.0f + 4.0f * kU);
+}
+
+// Geometry of dyad (k; i, j) from the initial positions: the parents ordered so that the
+// initial branch is the "+" one, (p_j - p_i) x (p_k - p_i) >= 0, and the double-word
+// link lengths.  Every builder computes a dyad through these helpers, so their plans
+// agree to the bit.
+struct DyadGeo {
+  int i, j;
+  dw r1sq, r1, r2, R12, Rm, c;
+};
+
+template <typename PT>
+LINKS_HD DyadGeo dyad_geo(const PT* pos, int k, int i, int j) {
+  dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
+  dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
+  if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
+    int t = i; i = j; j = t;
+    dw2 tv = vi; vi = vj; vj = tv;
+  }
+  DyadGeo g;
+  g.i = i;
+  g.j = j;
+  g.r1sq = norm2(vi);
+  const dw r2sq = norm2(vj);
+  g.r1 = dw_sqrt_exact(g.r1sq);
+  g.r2 = dw_sqrt_exact(r2sq);
+  g.R12 = dw_add(g.r1, g.r2);
+  dw Rm = dw_sub(g.r1, g.r2);
+  if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
+  g.Rm = Rm;
+  g.c = dw_sub(g.r1sq, r2sq);
+  return g;
+}
+
+// The dyad's record for slots si, sj (parents), sk (the joint k solved).  Byte offsets
+// into a lane's slot arrays of the screen: positions 256 B per slot, bounds 128 B.
+LINKS_HD DyadRec dyad_record(const DyadGeo& g, int si, int sj, int k, int sk) {
+  const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
+  const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
+  const uint32_t offK = ((uint32_t)sk * 256u) | (((uint32_t)sk * 128u) << 16);
+  const uint32_t offEij = ((uint32_t)si * 128u) | (((uint32_t)sj * 128u) << 16);
+  DyadRec rec;
+  rec.r0 = make_float4(u2f(offPij), g.R12.h, g.Rm.h, g.c.h);
+  rec.r1 = make_float4(fmul(fadd(g.r1.h, g.r1.h), g.r2.h), fmul(kAmpErr * kU, g.R12.h), u2f(offK), u2f(offEij));
+  rec.r2 = make_float4(g.r1sq.h, g.r1sq.l, g.c.l, u2f(slots));
+  return rec;
+}
+
+// Bound of |p_k - pivot| during the turn from the parents' bounds and the link lengths.
+LINKS_HD float dyad_bound(float bi, float bj, float r1h, float r2h) {
+  return fmul(fminf(fadd(bi, r1h), fadd(bj, r2h)), 1.0f + 4.0f * kU);
 }
 
 template <typename PT, int NJ>
@@ -233,35 +285,13 @@ LINKS_HD int build_one(int n, int n_max, const uint8_t* adj, const int8_t* type,
   bmax = fmaxf(bmax, crank);
 
   for (int d = 0; d < nd; ++d) {
-    int k = S.dk(d), i = S.di(d), j = S.dj(d);
-    dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
-    dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
-    if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
-      int t = i; i = j; j = t;
-      dw2 tv = vi; vi = vj; vj = tv;
-    }
-    dw r1sq = norm2(vi), r2sq = norm2(vj);
-    dw r1 = dw_sqrt_exact(r1sq), r2 = dw_sqrt_exact(r2sq);
-    dw R12 = dw_add(r1, r2);
-    dw Rm = dw_sub(r1, r2);
-    if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
-    dw c = dw_sub(r1sq, r2sq);
-    int si = S.slot(i), sj = S.slot(j), sk = nf + 1 + d;
-    float bi = S.bound(si), bj = S.bound(sj);
-    const float bk = fmul(fminf(fadd(bi, r1.h), fadd(bj, r2.h)), 1.0f + 4.0f * kU);
+    const int k = S.dk(d);
+    const DyadGeo g = dyad_geo(pos, k, S.di(d), S.dj(d));
+    const int si = S.slot(g.i), sj = S.slot(g.j), sk = nf + 1 + d;
+    const float bk = dyad_bound(S.bound(si), S.bound(sj), g.r1.h, g.r2.h);
     S.set_bound(sk, bk);
     bmax = fmaxf(bmax, bk);
-    float locc = fmul(kAmpErr * kU, R12.h);
-    const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)k << 16) | ((uint32_t)sk << 24);
-    // byte offsets into a lane's slot arrays: positions 256 B per slot, bounds 128 B
-    const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
-    const uint32_t offK = ((uint32_t)sk * 256u) | (((uint32_t)sk * 128u) << 16);
-    const uint32_t offEij = ((uint32_t)si * 128u) | (((uint32_t)sj * 128u) << 16);
-    DyadRec rec;
-    rec.r0 = make_float4(u2f(offPij), R12.h, Rm.h, c.h);
-    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), locc, u2f(offK), u2f(offEij));
-    rec.r2 = make_float4(r1sq.h, r1sq.l, c.l, u2f(slots));
-    o.dyad[d] = rec;
+    o.dyad[d] = dyad_record(g, si, sj, k, sk);
   }
 
   h.nd = (uint8_t)nd;
@@ -302,203 +332,7 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
   return o;
 }
 
-// The same builder on a group of G lanes per mechanism (G >= n_max): lane a holds
-// joint a's neighbour mask and slot, lane s the bound of slot s, lane d the dyad d
-// found d-th.  The checks and the solve-order search are group votes, the dyads'
-// geometry is computed by their lanes in parallel, and the bound chain (each dyad's
-// bound from its parents') runs over the dyads in solve order through shuffles.  Each
-// value is the same expression on the same operands as in build_one, and the maxima
-// and minima do not depend on the order they are taken in, so the plan is the same
-// to the bit.
 constexpr unsigned kFull = 0xffffffffu;
-
-template <int G>
-struct Group {
-  unsigned mask;
-  int base;
-  __device__ unsigned ballot(bool v) const { return (__ballot_sync(mask, v) & mask) >> base; }
-  __device__ bool any(bool v) const { return ballot(v) != 0; }
-  template <class V>
-  __device__ V bc(V v, int src) const { return __shfl_sync(mask, v, src, G); }
-  __device__ int sum(int v) const {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(mask, v, o, G);
-    return v;
-  }
-  __device__ float max(float v) const {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v = fmaxf(v, __shfl_xor_sync(mask, v, o, G));
-    return v;
-  }
-  __device__ float min(float v) const {
-#pragma unroll
-    for (int o = 1; o < G; o <<= 1) v = fminf(v, __shfl_xor_sync(mask, v, o, G));
-    return v;
-  }
-};
-
-template <typename PT, int G>
-__device__ int build_group(int n, int n_max, const uint8_t* __restrict__ adj, const int8_t* __restrict__ type,
-                           const PT* __restrict__ pos, BuildOut o, int gl, const Group<G>& grp, int* nd_out) {
-  MechHdr h{};
-  h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
-  int status = LINKS_MECH_OK;
-  if (n < 2 || n > n_max || n_max > G) status = LINKS_MECH_BAD_SIZE;
-  const bool joint = status == LINKS_MECH_OK && gl < n;
-  const int t = joint ? type[gl] : -1;
-  const uint32_t fixm = grp.ballot(joint && t == 0), simm = grp.ballot(joint && t == 1);
-  const uint32_t motm = grp.ballot(joint && t == 2);
-  if (grp.any(joint && (t < 0 || t > 2))) status = LINKS_MECH_BAD_TYPE;
-  uint32_t nb = 0;  // lane a: neighbours of joint a
-  if (status == LINKS_MECH_OK) {
-    if (gl < n) {
-      const uint8_t* row = adj + (size_t)gl * n_max;
-      for (int c = 0; c < n; ++c) nb |= (row[c] != 0 ? 1u : 0u) << c;
-    }
-    bool bad = gl < n && ((nb >> gl) & 1u);
-    for (int c = 0; c < n; ++c) {
-      const uint32_t nbc = grp.bc(nb, c);
-      if (gl < n && ((nb >> c) & 1u) && !((nbc >> gl) & 1u)) bad = true;
-    }
-    if (grp.any(bad)) status = LINKS_MECH_BAD_ADJ;
-  }
-  if (status == LINKS_MECH_OK && popc32(motm) != 1) status = LINKS_MECH_NO_MOTOR;
-  int motor = -1, pivot = -1, nd = 0;
-  if (status == LINKS_MECH_OK) {
-    motor = ffs32(motm);
-    const uint32_t pm = grp.bc(nb, motor) & fixm;
-    if (!pm) status = LINKS_MECH_NO_PIVOT;
-    else pivot = ffs32(pm);
-  }
-  int dk = 0, di = 0, dj = 0, my_d = -1;  // lane d: dyad d; lane a: the dyad solving joint a
-  if (status == LINKS_MECH_OK) {
-    uint32_t known = fixm | motm, unknown = simm;
-    while (unknown) {
-      const int c = popc32(nb & known);
-      const uint32_t cand = grp.ballot(gl < n && ((unknown >> gl) & 1u) && c >= 2);
-      if (!cand) {
-        status = LINKS_MECH_NOT_DYAD_SOLVABLE;
-        break;
-      }
-      const int pick = ffs32(cand);
-      if (grp.bc(c, pick) > 2) {
-        status = LINKS_MECH_OVERCONSTRAINED;
-        break;
-      }
-      const uint32_t par = grp.bc(nb, pick) & known;
-      if (gl == nd) {
-        dk = pick;
-        di = ffs32(par);
-        dj = ffs32(par & (par - 1));
-      }
-      if (gl == pick) my_d = nd;
-      ++nd;
-      known |= 1u << pick;
-      unknown &= ~(1u << pick);
-    }
-  }
-  if (status == LINKS_MECH_OK) {
-    const int e2 = grp.sum(gl < n ? popc32(nb) : 0);
-    const int ff2 = grp.sum(gl < n && ((fixm >> gl) & 1u) ? popc32(nb & fixm) : 0);
-    if ((e2 - ff2) / 2 - 1 != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
-  }
-  h.status = status;
-  if (status != LINKS_MECH_OK) {
-    h.nd = 0;
-    if (gl == 0) *o.hdr = h;
-    return status;
-  }
-
-  // Slots: fixed joints by index, then the actuated joint, then dyads in solve order.
-  const int nf = popc32(fixm);
-  int slot = 0;  // lane a: slot of joint a
-  if ((fixm >> gl) & 1u) slot = popc32(fixm & ((1u << gl) - 1u));
-  else if (gl == motor) slot = nf;
-  else if (my_d >= 0) slot = nf + 1 + my_d;
-  if (gl < n) {
-    o.slot_joint[slot] = (uint8_t)gl;
-    o.pos64[slot] = make_double2((double)pos[2 * gl], (double)pos[2 * gl + 1]);
-  }
-  float bound = 0.0f, bmax = 0.0f;  // lane s: bound of slot s
-  if (gl < nf) {
-    uint32_t m = fixm;
-    for (int q = 0; q < gl; ++q) m &= m - 1;
-    const dw2 r = rel(pos, ffs32(m), pivot);
-    o.fixpos[gl] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
-    bound = hyp_up(r.x.h, r.y.h);
-    bmax = bound;
-  }
-  const dw2 u = rel(pos, motor, pivot);
-  const float crank = hyp_up(u.x.h, u.y.h);
-  if (gl == nf) bound = crank;
-  bmax = fmaxf(bmax, crank);
-
-  int i = di, j = dj;
-  float r1h = 0.0f, r2h = 0.0f;
-  DyadRec rec;
-  if (gl < nd) {
-    const int k = dk;
-    dw2 a = rel(pos, j, i), vi = rel(pos, k, i), vj = rel(pos, k, j);
-    dw cross = dw_sub(dw_mul(a.x, vi.y), dw_mul(a.y, vi.x));
-    if (dw_sign(cross) < 0.0f) {  // keep the initial branch as the "+" one
-      int tt = i; i = j; j = tt;
-      dw2 tv = vi; vi = vj; vj = tv;
-    }
-    dw r1sq = norm2(vi), r2sq = norm2(vj);
-    dw r1 = dw_sqrt_exact(r1sq), r2 = dw_sqrt_exact(r2sq);
-    dw R12 = dw_add(r1, r2);
-    dw Rm = dw_sub(r1, r2);
-    if (dw_sign(Rm) < 0.0f) Rm = dw_neg(Rm);
-    dw c = dw_sub(r1sq, r2sq);
-    r1h = r1.h;
-    r2h = r2.h;
-    rec.r0 = make_float4(0.0f, R12.h, Rm.h, c.h);
-    rec.r1 = make_float4(fmul(fadd(r1.h, r1.h), r2.h), fmul(kAmpErr * kU, R12.h), 0.0f, 0.0f);
-    rec.r2 = make_float4(r1sq.h, r1sq.l, c.l, 0.0f);
-  }
-  const int si = grp.bc(slot, i), sj = grp.bc(slot, j);  // slots of the lane's dyad's parents
-  if (gl < nd) {
-    const int sk = nf + 1 + gl;
-    const uint32_t slots = (uint32_t)si | ((uint32_t)sj << 8) | ((uint32_t)dk << 16) | ((uint32_t)sk << 24);
-    const uint32_t offPij = ((uint32_t)si * 256u) | (((uint32_t)sj * 256u) << 16);
-    const uint32_t offK = ((uint32_t)sk * 256u) | (((uint32_t)sk * 128u) << 16);
-    const uint32_t offEij = ((uint32_t)si * 128u) | (((uint32_t)sj * 128u) << 16);
-    rec.r0.x = u2f(offPij);
-    rec.r1.z = u2f(offK);
-    rec.r1.w = u2f(offEij);
-    rec.r2.w = u2f(slots);
-    o.dyad[gl] = rec;
-  }
-  for (int d = 0; d < nd; ++d) {  // the bound chain, in solve order
-    const float bi = grp.bc(bound, grp.bc(si, d)), bj = grp.bc(bound, grp.bc(sj, d));
-    const float bk = fmul(fminf(fadd(bi, grp.bc(r1h, d)), fadd(bj, grp.bc(r2h, d))), 1.0f + 4.0f * kU);
-    if (gl == nf + 1 + d) bound = bk;
-    bmax = fmaxf(bmax, bk);
-  }
-  bmax = grp.max(bmax);
-  const float x = gl < n ? (float)pos[2 * gl] : INFINITY, y = gl < n ? (float)pos[2 * gl + 1] : INFINITY;
-  const float lo_x = grp.min(x), lo_y = grp.min(y);
-  const float hi_x = grp.max(gl < n ? x : -INFINITY), hi_y = grp.max(gl < n ? y : -INFINITY);
-  const int pivot_slot = grp.bc(slot, pivot);
-  if (gl == 0) {
-    h.nd = (uint8_t)nd;
-    h.nf = (uint8_t)nf;
-    h.motor_joint = (uint8_t)motor;
-    h.pivot_joint = (uint8_t)pivot;
-    h.pad0 = (uint8_t)pivot_slot;
-    h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
-    h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
-    dw px = abs_dw(pos, 2 * pivot), py = abs_dw(pos, 2 * pivot + 1);
-    h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
-    h.bmax = bmax;
-    h.lbox = hyp_up(fsub(hi_x, lo_x), fsub(hi_y, lo_y));
-    h.e_motor = fmul(4.0f * kU, crank);
-    h.e_fixed = fmul(kU, bmax);
-    *o.hdr = h;
-  }
-  if (nd_out) *nd_out = nd;
-  return status;
-}
 
 // Inputs of the block's 256 mechanisms (n_max <= 8) staged in shared memory with
 // coalesced loads: each mechanism's adjacency, type and position rows padded to an odd
@@ -561,30 +395,363 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
 }
 
-// G lanes per mechanism (build_group); 256 / G mechanisms per block.
-template <typename PT, int G>
-__global__ void __launch_bounds__(256) build_group_kernel(int64_t B, const int32_t* __restrict__ n_joints,
-                                                          const uint8_t* __restrict__ adj,
-                                                          const int8_t* __restrict__ type,
-                                                          const PT* __restrict__ pos, PlanDev p,
-                                                          int32_t* __restrict__ status_out) {
+// ---------------------------------------------------------------------------------------
+// Warp-flat builder: each warp builds 32 mechanisms.  The lanes first stage the warp's
+// neighbour masks (a lane per adjacency row, word loads issued in batches), joint types
+// and initial positions (vector loads) in shared memory; then lane m runs mechanism m's
+// checks, solve-order search and slot assignment (the decisions of build_one, on bit
+// masks); then the warp computes the geometry of all its mechanisms' dyads as one flat
+// list, a dyad per lane, so that mechanisms of different sizes keep every lane busy;
+// finally lane m runs its mechanism's bound chain and writes the header and the FP64
+// positions.  Each value is the same expression on the same operands as in build_one.
+// ---------------------------------------------------------------------------------------
+constexpr int kFlatWarps = 4;  // warps per block
+
+// One warp's shared memory, per-mechanism arrays column-major ([e * 32 + m]) unless noted.
+template <typename PT>
+struct FlatSmem {
+  PT* pos;        // [32][2 NM + 1]  initial positions, odd row stride (row-major)
+  uint32_t* nb;   // [NM]            neighbour masks; after the search, the slot bounds (float)
+  int* pfx;       // [33]            exclusive prefix of the dyad counts
+  uint8_t* type;  // [32][NM]        joint types as stored in global memory (row-major)
+  uint8_t* slot;  // [NM]            slot of each joint
+  uint8_t* dk;    // [MD]            dyad d: the joint solved ...
+  uint8_t* di;    // [MD]            ... and its parents; after the geometry pass, the
+  uint8_t* dj;    // [MD]                parents' slots in branch order
+  uint8_t* nfv;   // [32]            fixed joints of each mechanism
+  __host__ __device__ static size_t pos_bytes(int NM) {
+    return (sizeof(PT) * 32 * (2 * NM + 1) + 15) & ~size_t(15);
+  }
+  __host__ __device__ static size_t type_bytes(int NM) { return (32 * (size_t)NM + 15) & ~size_t(15); }
+  __host__ __device__ static size_t bytes(int NM, int MD) {
+    const size_t b = pos_bytes(NM) + type_bytes(NM) + 4 * 32 * NM + 4 * 36 + 32 * NM + 3 * 32 * MD + 32;
+    return (b + 15) & ~size_t(15);
+  }
+  __device__ FlatSmem(char* base, int NM, int MD) {
+    size_t o = 0;
+    pos = reinterpret_cast<PT*>(base);
+    o += pos_bytes(NM);
+    type = reinterpret_cast<uint8_t*>(base + o);
+    o += type_bytes(NM);
+    nb = reinterpret_cast<uint32_t*>(base + o);
+    o += 4 * 32 * NM;
+    pfx = reinterpret_cast<int*>(base + o);
+    o += 4 * 36;
+    slot = reinterpret_cast<uint8_t*>(base + o);
+    o += 32 * NM;
+    dk = reinterpret_cast<uint8_t*>(base + o);
+    o += 32 * MD;
+    di = reinterpret_cast<uint8_t*>(base + o);
+    o += 32 * MD;
+    dj = reinterpret_cast<uint8_t*>(base + o);
+    o += 32 * MD;
+    nfv = reinterpret_cast<uint8_t*>(base + o);
+  }
+};
+
+template <typename PT>
+struct Vec16;  // 16-byte vector of positions
+template <>
+struct Vec16<float> {
+  using T = float4;
+  static constexpr int kN = 4;
+  __device__ static void put(float* d, const float4& v) { d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w; }
+};
+template <>
+struct Vec16<double> {
+  using T = double2;
+  static constexpr int kN = 2;
+  __device__ static void put(double* d, const double2& v) { d[0] = v.x; d[1] = v.y; }
+};
+
+// flags: bit 0 the adjacency rows are 4-byte aligned whole words (n_max % 4 == 0 and an
+// aligned base); bit 1 positions and types are read as 16-byte vectors (aligned bases, and
+// position rows of whole vectors).
+template <typename PT>
+__global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, const int32_t* __restrict__ n_joints,
+                                                                      const uint8_t* __restrict__ adj,
+                                                                      const int8_t* __restrict__ type,
+                                                                      const PT* __restrict__ pos, PlanDev p,
+                                                                      int32_t* __restrict__ status_out, int flags) {
+  extern __shared__ __align__(16) char flat_smem[];
   __shared__ int hist[32];
+  const int NM = p.n_max, MD = p.max_dyads;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
   __syncthreads();
-  const int nm = p.n_max;
-  const int lane = threadIdx.x & 31, gl = lane % G;
-  Group<G> grp;
-  grp.base = lane - gl;
-  grp.mask = G == 32 ? kFull : (((1u << G) - 1u) << grp.base);
-  const int64_t b = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / G;
-  if (b < B) {  // uniform in the group
-    int nd = 0;
-    const int st = build_group<PT, G>(n_joints[b], nm, adj + b * nm * nm, type + b * nm, pos + b * nm * 2,
-                                      out_of(p, b), gl, grp, &nd);
-    if (gl == 0) {
-      if (status_out) status_out[b] = st;
-      if (st == LINKS_MECH_OK) atomicAdd(&hist[nd], 1);
+  FlatSmem<PT> S(flat_smem + warp * FlatSmem<PT>::bytes(NM, MD), NM, MD);
+  const int64_t b0 = ((int64_t)blockIdx.x * kFlatWarps + warp) * 32;
+  const int mc = b0 < B ? (int)min((int64_t)32, B - b0) : 0;
+  const int prow = 2 * NM + 1;
+  const int m = lane;
+  const int64_t b = b0 + m;
+  const int n = m < mc ? __ldg(n_joints + b) : 0;
+
+  // 1. staging
+  const int nrows = mc * NM;
+  if (flags & 1) {  // neighbour masks from whole words, two rows per lane in flight
+    const int W = NM >> 2;
+    const uint8_t* blk = adj + b0 * NM * NM;
+    for (int r0 = 0; r0 < nrows; r0 += 64) {
+      uint32_t wv[2][8];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + h * 32 + lane;
+        const uint32_t* w = reinterpret_cast<const uint32_t*>(blk + (int64_t)r * NM);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) wv[h][q] = (r < nrows && q < W) ? __ldg(w + q) : 0u;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = r0 + h * 32 + lane;
+        if (r < nrows) {
+          uint32_t mask = 0;
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            // one bit per nonzero byte: the four bits land on bits 21..24 of the product
+            const uint32_t v = __vcmpne4(wv[h][q], 0u) & 0x01010101u;
+            mask |= ((v * 0x00204081u) >> 21 & 0xfu) << (4 * q);
+          }
+          const int mm = r / NM;
+          S.nb[(r - mm * NM) * 32 + mm] = mask;
+        }
+      }
     }
+  } else {
+    for (int r = lane; r < nrows; r += 32) {
+      const uint8_t* row = adj + (b0 * NM + r) * NM;
+      uint32_t mask = 0;
+      for (int c = 0; c < NM; ++c) mask |= (__ldg(row + c) != 0 ? 1u : 0u) << c;
+      const int mm = r / NM;
+      S.nb[(r - mm * NM) * 32 + mm] = mask;
+    }
+  }
+  {
+    const int per = 2 * NM, ne = mc * per;
+    const PT* src = pos + b0 * per;
+    if (flags & 2) {  // positions as 16-byte vectors, eight per lane in flight
+      using V = typename Vec16<PT>::T;
+      constexpr int kN = Vec16<PT>::kN;
+      const V* vs = reinterpret_cast<const V*>(src);
+      const int nv = ne / kN;
+      for (int x0 = 0; x0 < nv; x0 += 256) {
+        V v[8];
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const int x = x0 + h * 32 + lane;
+          if (x < nv) v[h] = __ldg(vs + x);
+        }
+#pragma unroll
+        for (int h = 0; h < 8; ++h) {
+          const int x = x0 + h * 32 + lane;
+          if (x < nv) {
+            const int e = x * kN, mm = e / per;
+            Vec16<PT>::put(S.pos + mm * prow + (e - mm * per), v[h]);
+          }
+        }
+      }
+    } else {
+      for (int x = lane; x < ne; x += 32) {
+        const int mm = x / per;
+        S.pos[mm * prow + (x - mm * per)] = __ldg(src + x);
+      }
+    }
+    const int nt = mc * NM;  // types: 16-byte vectors over whole chunks, then bytes
+    const int8_t* ts = type + b0 * NM;
+    int done = 0;
+    if (flags & 2) {
+      const int n16 = nt >> 4;
+      for (int x = lane; x < n16; x += 32)
+        reinterpret_cast<uint4*>(S.type)[x] = __ldg(reinterpret_cast<const uint4*>(ts) + x);
+      done = n16 << 4;
+    }
+    for (int x = done + lane; x < nt; x += 32) S.type[x] = (uint8_t)__ldg(ts + x);
+  }
+  __syncwarp();
+
+  // 2. lane m: checks, solve order and slots of mechanism m (build_one's decisions)
+  const PT* P = S.pos + m * prow;
+  int status = LINKS_MECH_OK, nd = 0, nf = 0, motor = -1, pivot = -1;
+  uint32_t fixm = 0, simm = 0, motm = 0;
+  if (m < mc) {
+    if (n < 2 || n > NM) status = LINKS_MECH_BAD_SIZE;
+    const int8_t* ty = reinterpret_cast<const int8_t*>(S.type) + m * NM;
+    for (int a = 0; a < n && status == LINKS_MECH_OK; ++a) {
+      const int t = ty[a];
+      if (t == 0) fixm |= 1u << a;
+      else if (t == 1) simm |= 1u << a;
+      else if (t == 2) motm |= 1u << a;
+      else status = LINKS_MECH_BAD_TYPE;
+    }
+  } else {
+    status = -1;  // no mechanism
+  }
+  const uint32_t live = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
+  auto nbm = [&](int a) { return S.nb[a * 32 + m] & live; };
+  if (status == LINKS_MECH_OK) {  // no self-loop, and every link listed both ways
+    uint32_t asym = 0;
+    for (int a = 0; a < n; ++a) {
+      const uint32_t na = nbm(a);
+      asym |= na & (1u << a);
+      for (uint32_t q = na; q; q &= q - 1) asym |= ~nbm(ffs32(q)) & (1u << a);
+    }
+    if (asym) status = LINKS_MECH_BAD_ADJ;
+  }
+  if (status == LINKS_MECH_OK && popc32(motm) != 1) status = LINKS_MECH_NO_MOTOR;
+  if (status == LINKS_MECH_OK) {
+    motor = ffs32(motm);
+    const uint32_t pm = nbm(motor) & fixm;
+    if (!pm) status = LINKS_MECH_NO_PIVOT;
+    else pivot = ffs32(pm);
+  }
+  if (status == LINKS_MECH_OK) {
+    // The search of build_one (the lowest-index unknown joint with >= 2 known neighbours;
+    // > 2 is over-constraint) on running counts: has1 / has2 / has3 mark the joints with
+    // at least 1 / 2 / 3 known neighbours, updated from each newly known joint's mask.
+    uint32_t known = fixm | motm, unknown = simm, has1 = 0, has2 = 0, has3 = 0;
+    for (uint32_t q = known; q; q &= q - 1) {
+      const uint32_t nbq = nbm(ffs32(q));
+      has3 |= has2 & nbq;
+      has2 |= has1 & nbq;
+      has1 |= nbq;
+    }
+    while (unknown) {
+      const uint32_t ready = has2 & unknown;
+      if (!ready) { status = LINKS_MECH_NOT_DYAD_SOLVABLE; break; }
+      const int pick = ffs32(ready);
+      if ((has3 >> pick) & 1u) { status = LINKS_MECH_OVERCONSTRAINED; break; }
+      const uint32_t nbp = nbm(pick);
+      const uint32_t par = nbp & known;
+      S.dk[nd * 32 + m] = (uint8_t)pick;
+      S.di[nd * 32 + m] = (uint8_t)ffs32(par);
+      S.dj[nd * 32 + m] = (uint8_t)ffs32(par & (par - 1));
+      ++nd;
+      known |= 1u << pick;
+      unknown &= ~(1u << pick);
+      has3 |= has2 & nbp;
+      has2 |= has1 & nbp;
+      has1 |= nbp;
+    }
+  }
+  if (status == LINKS_MECH_OK) {
+    int e2 = 0, ff2 = 0;
+    for (int a = 0; a < n; ++a) {
+      e2 += popc32(nbm(a));
+      if ((fixm >> a) & 1u) ff2 += popc32(nbm(a) & fixm);
+    }
+    if ((e2 - ff2) / 2 - 1 != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
+  }
+  // every lane reads only its own column of the masks, whose words now hold slot bounds
+  float* const bnd = reinterpret_cast<float*>(S.nb);
+  const BuildOut o = out_of(p, b);
+  float bmax = 0.0f, crank = 0.0f;
+  dw2 u{};
+  if (status == LINKS_MECH_OK) {
+    // slots: fixed joints by index, then the actuated joint, then dyads in solve order
+    for (uint32_t q = fixm; q; q &= q - 1) {
+      const int a = ffs32(q);
+      S.slot[a * 32 + m] = (uint8_t)nf;
+      o.slot_joint[nf] = (uint8_t)a;
+      const dw2 r = rel(P, a, pivot);
+      o.fixpos[nf] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
+      const float bs = hyp_up(r.x.h, r.y.h);
+      bnd[nf * 32 + m] = bs;
+      bmax = fmaxf(bmax, bs);
+      ++nf;
+    }
+    S.slot[motor * 32 + m] = (uint8_t)nf;
+    o.slot_joint[nf] = (uint8_t)motor;
+    for (int d = 0; d < nd; ++d) {
+      const int k = S.dk[d * 32 + m];
+      S.slot[k * 32 + m] = (uint8_t)(nf + 1 + d);
+      o.slot_joint[nf + 1 + d] = (uint8_t)k;
+    }
+    u = rel(P, motor, pivot);
+    crank = hyp_up(u.x.h, u.y.h);
+    bnd[nf * 32 + m] = crank;
+    bmax = fmaxf(bmax, crank);
+  } else if (status > 0) {
+    MechHdr h{};
+    h.n = (uint8_t)(n > 0 && n <= 255 ? n : 0);
+    h.status = status;
+    *o.hdr = h;
+    nd = 0;
+  } else {
+    nd = 0;
+  }
+  S.nfv[m] = (uint8_t)nf;
+  // exclusive prefix of the dyad counts
+  int incl = nd;
+#pragma unroll
+  for (int q = 1; q < 32; q <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, q);
+    if (lane >= q) incl += y;
+  }
+  S.pfx[m] = incl - nd;
+  if (lane == 31) S.pfx[32] = incl;
+  __syncwarp();
+
+  // 3. the warp's dyads as one flat list, a dyad per lane.  Each dyad's link lengths
+  // (r1, r2 high words) go to its joint's FP64 position slot, which lane m reads back
+  // for the bound chain and then overwrites with the position.
+  const int total = S.pfx[32];
+  for (int f = lane; f < total; f += 32) {
+    int lo = 0, hi = 31;  // the mechanism mm with pfx[mm] <= f < pfx[mm + 1]
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (S.pfx[mid] <= f) lo = mid;
+      else hi = mid - 1;
+    }
+    const int mm = lo, d = f - S.pfx[mm];
+    const int k = S.dk[d * 32 + mm], sk = S.nfv[mm] + 1 + d;
+    const DyadGeo g = dyad_geo(S.pos + mm * prow, k, (int)S.di[d * 32 + mm], (int)S.dj[d * 32 + mm]);
+    const int si = S.slot[g.i * 32 + mm], sj = S.slot[g.j * 32 + mm];
+    p.dyad[(b0 + mm) * MD + d] = dyad_record(g, si, sj, k, sk);
+    S.di[d * 32 + mm] = (uint8_t)si;
+    S.dj[d * 32 + mm] = (uint8_t)sj;
+    *reinterpret_cast<float2*>(p.pos64 + (b0 + mm) * NM + sk) = make_float2(g.r1.h, g.r2.h);
+  }
+  __syncwarp();  // also orders the lanes' global writes above before the reads below
+
+  // 4. lane m: the bound chain in solve order, the FP64 positions, the header
+  if (status == LINKS_MECH_OK) {
+    for (int d = 0; d < nd; ++d) {
+      const float2 rr = *reinterpret_cast<const float2*>(o.pos64 + nf + 1 + d);
+      const float bk = dyad_bound(bnd[S.di[d * 32 + m] * 32 + m], bnd[S.dj[d * 32 + m] * 32 + m], rr.x, rr.y);
+      bnd[(nf + 1 + d) * 32 + m] = bk;
+      bmax = fmaxf(bmax, bk);
+    }
+    for (int a = 0; a < n; ++a)
+      o.pos64[S.slot[a * 32 + m]] = make_double2((double)P[2 * a], (double)P[2 * a + 1]);
+    MechHdr h{};
+    h.n = (uint8_t)n;
+    h.status = status;
+    h.nd = (uint8_t)nd;
+    h.nf = (uint8_t)nf;
+    h.motor_joint = (uint8_t)motor;
+    h.pivot_joint = (uint8_t)pivot;
+    h.pad0 = S.slot[pivot * 32 + m];  // pivot slot
+    h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
+    h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
+    const dw px = abs_dw(P, 2 * pivot), py = abs_dw(P, 2 * pivot + 1);
+    h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
+    h.bmax = bmax;
+    float lo_x = (float)P[0], hi_x = lo_x, lo_y = (float)P[1], hi_y = lo_y;
+    for (int a = 1; a < n; ++a) {
+      const float x = (float)P[2 * a], y = (float)P[2 * a + 1];
+      lo_x = fminf(lo_x, x);
+      hi_x = fmaxf(hi_x, x);
+      lo_y = fminf(lo_y, y);
+      hi_y = fmaxf(hi_y, y);
+    }
+    h.lbox = hyp_up(fsub(hi_x, lo_x), fsub(hi_y, lo_y));
+    h.e_motor = fmul(4.0f * kU, crank);
+    h.e_fixed = fmul(kU, bmax);
+    *o.hdr = h;
+  }
+  if (status >= 0) {
+    if (status_out) status_out[b] = status;
+    if (status == LINKS_MECH_OK) atomicAdd(&hist[nd], 1);
   }
   __syncthreads();
   if (threadIdx.x < 32 && hist[threadIdx.x]) atomicAdd(&p.ctrs[kHist + threadIdx.x], hist[threadIdx.x]);
@@ -638,21 +805,35 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
   unsigned grid = (unsigned)((B + 255) / 256);
   {
     KernelScope ks(ctx, "plan_build");
-    // n_max <= 8: a thread per mechanism, scratch in registers (measured faster than a
-    // lane group at this size); larger: a group of 16 or 32 lanes per mechanism
-    const int G = p.n_max <= 16 ? 16 : 32;
-    const unsigned ggrid = (unsigned)((B * G + 255) / 256);
-    const bool small = p.n_max <= 8;
+    // the warp-flat builder (a lane per mechanism for the search, a lane per dyad for the
+    // geometry; measured faster at every n_max), or on request for n_max <= 8 a thread
+    // per mechanism with its scratch in registers
+    const int builder = tuning_of(ctx, p.n_max).builder;
+    const bool small = p.n_max <= 8 && builder == 1;
+    const bool vec = ((uintptr_t)pos0 & 15u) == 0 && ((uintptr_t)type & 15u) == 0 &&
+                     (pos_dtype == LINKS_F64 || p.n_max % 2 == 0);
+    const int flags = ((p.n_max % 4 == 0 && ((uintptr_t)adj & 3u) == 0) ? 1 : 0) | (vec ? 2 : 0);
+    const unsigned fgrid = (unsigned)((B + 32 * kFlatWarps - 1) / (32 * kFlatWarps));
     if (pos_dtype == LINKS_F32) {
       const float* ps = (const float*)pos0;
-      if (small) build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-      else if (G == 16) build_group_kernel<float, 16><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-      else build_group_kernel<float, 32><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      if (small) {
+        build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      } else {
+        const size_t sm = kFlatWarps * FlatSmem<float>::bytes(p.n_max, p.max_dyads);
+        LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        build_flat_kernel<float><<<fgrid, 32 * kFlatWarps, sm, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+                                                                            status_out, flags);
+      }
     } else {
       const double* ps = (const double*)pos0;
-      if (small) build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-      else if (G == 16) build_group_kernel<double, 16><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
-      else build_group_kernel<double, 32><<<ggrid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      if (small) {
+        build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
+      } else {
+        const size_t sm = kFlatWarps * FlatSmem<double>::bytes(p.n_max, p.max_dyads);
+        LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        build_flat_kernel<double><<<fgrid, 32 * kFlatWarps, sm, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+                                                                             status_out, flags);
+      }
     }
   }
   LINKS_CUDA(cudaGetLastError());

@@ -413,9 +413,15 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   }
 }
 
+// Shapes of the screen: lanes per mechanism G, steps per lane S, CTAs per SM (0 = as many
+// as fit).
+struct ScreenShape {
+  int G = 8, S = 1, ctas = 0;
+};
+
 template <int G, int S>
-int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
-                  int16_t* lock_step, float* min_disc, const int32_t* order, const int32_t* n_list) {
+int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid, int16_t* lock_step,
+                  float* min_disc, const int32_t* order, const int32_t* n_list, int ctas) {
   PlanDev& p = plan->d;
   size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
   // a function attribute of the current device's context: set on every launch (a host
@@ -423,6 +429,7 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G, S>, kBlock, smem));
+  if (ctas > 0 && ctas < per_sm) per_sm = ctas;
   if (per_sm < 1) per_sm = 1;
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
   {
@@ -434,17 +441,38 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   return LINKS_OK;
 }
 
-int launch_screen_lanes(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
-                        int16_t* lock_step, float* min_disc, int lanes, const int32_t* order = nullptr,
-                        const int32_t* n_list = nullptr) {
-  if (plan->d.n_max <= kScreenTwoStepMaxSlots) {
-    if (lanes == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
-    if (lanes == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
-    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+// Two steps per lane need the doubled slot arrays in shared memory (at most 16 slots).
+constexpr int kScreenTwoStepLimit = 16;
+
+ScreenShape screen_shape(links_ctx ctx, int n_max) {
+  const Tuning t = tuning_of(ctx, n_max);
+  ScreenShape sh;
+  sh.G = t.screen_lanes;
+  sh.S = t.screen_steps ? t.screen_steps : (n_max <= kScreenTwoStepMaxSlots ? 2 : 1);
+  if (n_max > kScreenTwoStepLimit) sh.S = 1;
+  sh.ctas = t.screen_ctas;
+  return sh;
+}
+
+int launch_screen_shape(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
+                        int16_t* lock_step, float* min_disc, const ScreenShape& sh,
+                        const int32_t* order = nullptr, const int32_t* n_list = nullptr) {
+  const int c = sh.ctas;
+  if (sh.S == 2) {
+    if (sh.G == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+    if (sh.G == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
   }
-  if (lanes == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
-  if (lanes == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
-  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list);
+  if (sh.G == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+  if (sh.G == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+}
+
+int launch_screen_tuned(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
+                        int16_t* lock_step, float* min_disc, const int32_t* order = nullptr,
+                        const int32_t* n_list = nullptr) {
+  return launch_screen_shape(ctx, plan, T, tab, valid, lock_step, min_disc, screen_shape(ctx, plan->d.n_max), order,
+                             n_list);
 }
 
 // After the low-fidelity pass: the mechanisms it found valid go, in work-list order
@@ -483,60 +511,28 @@ __global__ void __launch_bounds__(256) confirm_list_kernel(PlanDev p, const uint
   if (keep) p.order2[base + wcount[warp] + __popc(m & ((1u << lane) - 1u))] = b;
 }
 
-int screen_lanes(links_ctx ctx, links_plan plan) {
-  auto it = ctx->screen_lanes.find(plan->d.n_max);
-  return it == ctx->screen_lanes.end() ? 8 : it->second;
-}
-
 }  // namespace
 
-int autotune_screen(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) {
-  const int64_t B = plan->B;
-  uint8_t* v = nullptr;
-  int16_t* l = nullptr;
-  float* q = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  int best = 8, st = LINKS_OK;
-  float best_ms = 1e30f;
-  cudaError_t e = cudaMalloc(&v, std::max<int64_t>(B, 1));
-  if (e == cudaSuccess) e = cudaMalloc(&l, 2 * std::max<int64_t>(B, 1));
-  if (e == cudaSuccess) e = cudaMalloc(&q, 4 * std::max<int64_t>(B, 1));
-  if (e == cudaSuccess) e = cudaEventCreate(&e0);
-  if (e == cudaSuccess) e = cudaEventCreate(&e1);
-  if (e != cudaSuccess) st = cuda_status(e, "autotune_screen");
-  for (int lanes : {8, 16, 32}) {
-    if (st) break;
-    float total = 0.f;
-    for (int rep = 0; rep < 3 && !st; ++rep) {
-      cudaEventRecord(e0, ctx->stream);
-      st = launch_screen_lanes(ctx, plan, tab->T, tab, v, l, q, lanes);
-      cudaEventRecord(e1, ctx->stream);
-      if (cudaEventSynchronize(e1) != cudaSuccess) st = set_error(LINKS_ECUDA, "autotune_screen: run failed");
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rep > 0) total += ms;  // the first run warms up
-    }
-    if (!st && total < best_ms) {
-      best_ms = total;
-      best = lanes;
-    }
-  }
-  if (!st) {
-    ctx->screen_lanes[plan->d.n_max] = best;
-    if (lanes_out) *lanes_out = best;
-  }
-  cudaFree(v);
-  cudaFree(l);
-  cudaFree(q);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  return st;
+// Shapes of the emit: double-word slots in shared memory or thread-local, CTAs per SM.
+struct EmitShape {
+  bool dws = true;
+  int ctas = 0;
+};
+
+EmitShape emit_shape(links_ctx ctx, int n_max) {
+  const Tuning t = tuning_of(ctx, n_max);
+  EmitShape e;
+  e.dws = t.emit_dws < 0 ? n_max <= kEmitSharedDWMaxSlots : t.emit_dws != 0;
+  e.ctas = t.emit_ctas;
+  return e;
 }
 
 template <bool CENSUS>
 int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, const int16_t* lock_step,
-                const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name) {
-  const bool dws = plan->d.n_max <= kEmitSharedDWMaxSlots;
+                const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name,
+                const EmitShape* shape = nullptr) {
+  const EmitShape sh = shape ? *shape : emit_shape(ctx, plan->d.n_max);
+  const bool dws = sh.dws;
   auto kern = dws ? emit_kernel<CENSUS, true> : emit_kernel<CENSUS, false>;
   const size_t smem = (size_t)kWarps * (plan->d.n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes) +
                                         plan->d.max_dyads * 48);
@@ -544,6 +540,7 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
     LINKS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem));
+  if (sh.ctas > 0 && sh.ctas < per_sm) per_sm = sh.ctas;
   if (per_sm < 1) per_sm = 1;
   KernelScope ks(ctx, name);
   kern<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, plan->B, tab->T, tab->cs, full ? 1 : 0,
@@ -553,13 +550,120 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
   return LINKS_OK;
 }
 
+// Autotuner: times the screen over its shapes (lanes per mechanism 8/16/32, one or two
+// steps per lane, CTAs per SM) on the built plan, then the emit over its shapes
+// (double-word slots in shared memory or thread-local, CTAs per SM) on up to
+// kTuneRows valid rows of that screen's result, and keeps the fastest of each in the
+// context's table for this n_max.  Each shape runs once to warm up and twice timed.
+constexpr int64_t kTuneRows = 16384;
+
+int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) {
+  const int64_t B = std::max<int64_t>(plan->B, 1);
+  const int n_max = plan->d.n_max, T = tab->T;
+  uint8_t* v = nullptr;
+  int16_t* l = nullptr;
+  float *q = nullptr, *traj = nullptr, *path = nullptr;
+  int32_t *idx = nullptr, *nout = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int st = LINKS_OK;
+  cudaError_t e = cudaMalloc(&v, B);
+  if (e == cudaSuccess) e = cudaMalloc(&l, 2 * B);
+  if (e == cudaSuccess) e = cudaMalloc(&q, 4 * B);
+  if (e == cudaSuccess) e = cudaMalloc(&idx, 4 * B);
+  if (e == cudaSuccess) e = cudaMalloc(&nout, 4);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) st = cuda_status(e, "links_autotune");
+  auto timed = [&](auto&& run) -> float {  // warm-up + 2 timed runs, ms (huge on failure)
+    float total = 0.f;
+    for (int rep = 0; rep < 3 && !st; ++rep) {
+      cudaEventRecord(e0, ctx->stream);
+      st = run();
+      cudaEventRecord(e1, ctx->stream);
+      if (!st && cudaEventSynchronize(e1) != cudaSuccess) st = set_error(LINKS_ECUDA, "links_autotune: run failed");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) total += ms;
+    }
+    return st ? 1e30f : total;
+  };
+  Tuning best = tuning_of(ctx, n_max);
+  float best_ms = 1e30f;
+  ScreenShape best_sh = screen_shape(ctx, n_max);
+  for (int S : {1, 2}) {
+    if (S == 2 && n_max > kScreenTwoStepLimit) continue;
+    for (int G : {8, 16, 32})
+      for (int ctas : {0, 2, 1}) {
+        if (st) break;
+        ScreenShape sh{G, S, ctas};
+        const float ms = timed([&] { return launch_screen_shape(ctx, plan, T, tab, v, l, q, sh); });
+        if (ms < best_ms) {
+          best_ms = ms;
+          best_sh = sh;
+        }
+      }
+  }
+  if (!st) {
+    best.screen_lanes = best_sh.G;
+    best.screen_steps = best_sh.S;
+    best.screen_ctas = best_sh.ctas;
+    // the emit on up to kTuneRows valid rows of the chosen screen's result
+    st = launch_screen_shape(ctx, plan, T, tab, v, l, q, best_sh);
+    if (!st) st = compact_valid(ctx, plan, v, idx, B, nout);
+    int32_t nv = 0;
+    if (!st && cudaMemcpyAsync(&nv, nout, 4, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+      st = set_error(LINKS_ECUDA, "links_autotune: copy failed");
+    if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+      st = set_error(LINKS_ECUDA, "links_autotune: screen failed");
+    const int64_t R = std::min<int64_t>(nv, kTuneRows);
+    if (!st && R > 0) {
+      e = cudaMalloc(&traj, sizeof(float) * 2 * R * n_max * T);
+      if (e == cudaSuccess) e = cudaMalloc(&path, sizeof(float) * 2 * R * T);
+      if (e != cudaSuccess) st = cuda_status(e, "links_autotune");
+      float emit_best = 1e30f;
+      for (int dws : {1, 0})
+        for (int ctas : {0, 2, 1}) {
+          if (st) break;
+          EmitShape es{dws != 0, ctas};
+          const float ms = timed([&] {
+            return launch_emit<false>(ctx, plan, tab, false, l, idx, R, traj, path, "mixed_emit", &es);
+          });
+          if (ms < emit_best) {
+            emit_best = ms;
+            best.emit_dws = dws;
+            best.emit_ctas = ctas;
+          }
+        }
+    }
+  }
+  if (!st) {
+    ctx->tuning[n_max] = best;
+    if (lanes_out) *lanes_out = best.screen_lanes;
+  }
+  cudaFree(v);
+  cudaFree(l);
+  cudaFree(q);
+  cudaFree(idx);
+  cudaFree(nout);
+  cudaFree(traj);
+  cudaFree(path);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return st;
+}
+
+Tuning tuning_of(links_ctx ctx, int n_max) {
+  auto it = ctx->tuning.find(n_max);
+  return it == ctx->tuning.end() ? Tuning{} : it->second;
+}
+
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
   const int T = tab->T;
   int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
   if (st) return st;
-  st = launch_screen_lanes(ctx, plan, T, tab, valid, lock_step, min_disc, screen_lanes(ctx, plan));
+  st = launch_screen_tuned(ctx, plan, T, tab, valid, lock_step, min_disc);
   if (st) return st;
   const bool full = out_mode == LINKS_OUT_FULL;
   if (!full) {
@@ -586,8 +690,7 @@ int simulate_prescreened(links_ctx ctx, links_plan plan, const TTable* tab, int 
   if (n_escaped)
     LINKS_CUDA(cudaMemcpyAsync(n_escaped, p.ctrs + kNConfirm, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                ctx->stream));
-  st = launch_screen_lanes(ctx, plan, tab->T, tab, valid, lock_step, min_disc, screen_lanes(ctx, plan), p.order2,
-                           p.ctrs + kNConfirm);
+  st = launch_screen_tuned(ctx, plan, tab->T, tab, valid, lock_step, min_disc, p.order2, p.ctrs + kNConfirm);
   if (st) return st;
   const bool full = out_mode == LINKS_OUT_FULL;
   if (!full) {
@@ -607,8 +710,7 @@ int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, con
   PlanDev& p = plan->d;
   int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
   if (st) return st;
-  const int lanes = screen_lanes(ctx, plan);
-  st = launch_screen_lanes(ctx, plan, tab_lo->T, tab_lo, valid, lock_step, min_disc, lanes);
+  st = launch_screen_tuned(ctx, plan, tab_lo->T, tab_lo, valid, lock_step, min_disc);
   if (st) return st;
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kNConfirm, 0, sizeof(int32_t), ctx->stream));
   if (plan->B > 0) {
@@ -620,7 +722,7 @@ int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, con
   if (n_low_valid)
     LINKS_CUDA(cudaMemcpyAsync(n_low_valid, p.ctrs + kNConfirm, sizeof(int32_t), cudaMemcpyDeviceToDevice,
                                ctx->stream));
-  st = launch_screen_lanes(ctx, plan, tab->T, tab, valid, lock_step, min_disc, lanes, p.order2, p.ctrs + kNConfirm);
+  st = launch_screen_tuned(ctx, plan, tab->T, tab, valid, lock_step, min_disc, p.order2, p.ctrs + kNConfirm);
   if (st) return st;
   st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
   if (st) return st;

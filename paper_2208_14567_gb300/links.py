@@ -93,6 +93,10 @@ def lib():
             "links_compact_valid_static": ([P, i64, P, i64, P, P], i32),
             "links_autotune": ([P, P, i32, P], i32),
             "links_set_screen_lanes": ([P, i32, i32], i32),
+            "links_set_tuning": ([P, i32, i32, i32], i32),
+            "links_get_tuning": ([P, i32, i32, P], i32),
+            "links_tuning_save": ([P, ctypes.c_char_p], i32),
+            "links_tuning_load": ([P, ctypes.c_char_p], i32),
             "links_set_chamfer_prune": ([P, i32], i32),
             "links_capture_begin": ([P], i32),
             "links_capture_end": ([P, P], i32),
@@ -464,6 +468,34 @@ def links_autotune(ctx, plan, T: int) -> int:
 
 def links_set_chamfer_prune(ctx, on: bool):
     _check(lib().links_set_chamfer_prune(ctx, 1 if on else 0), "links_set_chamfer_prune")
+
+
+TUNE_BUILDER, TUNE_SCREEN_LANES, TUNE_SCREEN_STEPS, TUNE_SCREEN_CTAS, TUNE_EMIT_DWS, TUNE_EMIT_CTAS = range(6)
+TUNE_KEYS = {"builder": TUNE_BUILDER, "screen_lanes": TUNE_SCREEN_LANES, "screen_steps": TUNE_SCREEN_STEPS,
+             "screen_ctas": TUNE_SCREEN_CTAS, "emit_dws": TUNE_EMIT_DWS, "emit_ctas": TUNE_EMIT_CTAS}
+
+
+def links_set_tuning(ctx, n_max: int, key: int, value: int):
+    _check(lib().links_set_tuning(ctx, int(n_max), int(key), int(value)), "links_set_tuning")
+
+
+def links_get_tuning(ctx, n_max: int, key: int) -> int:
+    v = ctypes.c_int()
+    _check(lib().links_get_tuning(ctx, int(n_max), int(key), ctypes.byref(v)), "links_get_tuning")
+    return v.value
+
+
+def tuning_table(ctx, n_max: int) -> dict:
+    """The context's kernel shapes for plans of n_max joints, by key name."""
+    return {name: links_get_tuning(ctx, n_max, k) for name, k in TUNE_KEYS.items()}
+
+
+def links_tuning_save(ctx, path: str):
+    _check(lib().links_tuning_save(ctx, os.fsencode(path)), "links_tuning_save")
+
+
+def links_tuning_load(ctx, path: str):
+    _check(lib().links_tuning_load(ctx, os.fsencode(path)), "links_tuning_load")
 
 
 def links_set_screen_lanes(ctx, n_max: int, lanes: int):

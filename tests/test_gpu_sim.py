@@ -38,10 +38,12 @@ def sim_for(batch, L):
     return Simulator(max(batch.B, 1), batch.nmax)
 
 
-def run(batch, T, precision, out_mode, L, host_build=False, out_capacity=None):
+def run(batch, T, precision, out_mode, L, host_build=False, out_capacity=None, builder=0):
     from paper_2208_14567_gb300.api import to_device
     s = sim_for(batch, L)
     try:
+        if builder:
+            L.links_set_tuning(s.ctx, batch.nmax, L.TUNE_BUILDER, builder)
         if host_build:
             st = s.build_host(batch)
         else:
@@ -130,15 +132,19 @@ def planted_bad(batch):
     return b
 
 
-@pytest.mark.parametrize("n_lo,n_hi,nmax,f64", [(6, 8, 8, False), (5, 8, 8, True), (6, 16, 16, False),
-                                                 (6, 20, 20, True), (3, 6, 32, False)])
-def test_device_and_host_plans_simulate_identically(L, n_lo, n_hi, nmax, f64):
-    """The device builder (a lane group per mechanism: 8, 16 or 32 lanes by n_max) and the
-    host builder give the same plans: every output of a mixed simulation on them is
-    the same to the bit, the planted ill-formed mechanisms included."""
+@pytest.mark.parametrize("n_lo,n_hi,nmax,f64,builder", [(6, 8, 8, False, 0), (5, 8, 8, True, 0), (6, 8, 8, False, 2),
+                                                         (5, 8, 8, True, 2), (6, 16, 16, False, 0),
+                                                         (6, 20, 20, True, 0), (6, 20, 20, False, 0),
+                                                         (3, 6, 32, False, 0), (5, 15, 15, False, 0)])
+def test_device_and_host_plans_simulate_identically(L, n_lo, n_hi, nmax, f64, builder):
+    """The device builders (a thread per mechanism for n_max <= 8; the warp-flat builder,
+    a lane per mechanism for the search and a lane per dyad for the geometry, for larger
+    n_max or when chosen) and the host builder give the same plans: every output of a
+    mixed simulation on them is the same to the bit, the planted ill-formed mechanisms
+    included.  n_max 15 reads the adjacency bytewise (rows not whole words)."""
     batch = planted_bad(I.dyad_batch(4000, n_lo, n_hi, seed=n_hi + nmax, permute=True, nmax=nmax,
                                      pos_dtype=np.float64 if f64 else np.float32))
-    a = run(batch, 64, L.MIXED, L.OUT_FULL, L, host_build=False)
+    a = run(batch, 64, L.MIXED, L.OUT_FULL, L, host_build=False, builder=builder)
     b = run(batch, 64, L.MIXED, L.OUT_FULL, L, host_build=True)
     for k in ("status", "valid", "lock_step", "min_disc", "traj", "path"):
         assert np.array_equal(a[k], b[k], equal_nan=True), k
@@ -470,6 +476,61 @@ def test_full_size_one_million_candidates(L):
                     TOL_MIXED, "1M sampled rows")
     f64 = run(batch, 200, L.PLAIN_F64, L.OUT_VALID_ONLY, L)
     check_flags(f64, ref, "1M f64")
+
+
+@pytest.mark.parametrize("nmax", [8, 12, 20])
+def test_every_kernel_shape_gives_the_same_outputs(L, nmax, tmp_path):
+    """The shape table (links_set_tuning): every screen shape (lanes, steps per lane, CTAs
+    per SM) and emit shape (shared or thread-local double-word slots, CTAs per SM) gives
+    the same flags, lock steps, minimum discriminants, rows and trajectories to the bit;
+    the autotuner's table survives a save and a load into another context; out-of-range
+    values and files tuned on another device are refused."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.dyad_batch(6000, 6, nmax, seed=70 + nmax, permute=True, nmax=nmax)
+    T = 96
+    db = to_device(batch)
+    shapes = [dict(screen_lanes=8), dict(screen_lanes=16, screen_steps=1), dict(screen_lanes=32, screen_ctas=1),
+              dict(screen_lanes=8, screen_steps=2 if nmax <= 16 else 1, screen_ctas=2),
+              dict(emit_dws=0), dict(emit_dws=1, emit_ctas=1), dict(emit_dws=0, emit_ctas=2)]
+    ref = None
+    with Simulator(batch.B, nmax) as s:
+        for sh in shapes:
+            for k in L.TUNE_KEYS:
+                L.links_set_tuning(s.ctx, nmax, L.TUNE_KEYS[k], -1 if k == "emit_dws" else (8 if k == "screen_lanes" else 0))
+            for k, v in sh.items():
+                L.links_set_tuning(s.ctx, nmax, L.TUNE_KEYS[k], v)
+            s.build(db)
+            o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY)
+            s.sync()
+            n = int(o.n_out[0])
+            got = [o.valid.cpu().numpy(), o.lock_step.cpu().numpy(), o.min_disc.cpu().numpy(),
+                   o.out_index[:n].cpu().numpy(), o.traj[:n].cpu().numpy(), o.path[:n].cpu().numpy()]
+            if ref is None:
+                ref = got
+            else:
+                for a, b in zip(ref, got):
+                    assert np.array_equal(a, b, equal_nan=True), sh
+        lanes = L.links_autotune(s.ctx, s.plan, T)
+        table = L.tuning_table(s.ctx, nmax)
+        assert table["screen_lanes"] == lanes
+        path = str(tmp_path / "tuning.txt")
+        L.links_tuning_save(s.ctx, path)
+        with pytest.raises(L.LinksError):
+            L.links_set_tuning(s.ctx, nmax, L.TUNE_SCREEN_LANES, 12)
+        with pytest.raises(L.LinksError):
+            L.links_set_tuning(s.ctx, 20, L.TUNE_SCREEN_STEPS, 2)
+        with pytest.raises(L.LinksError):
+            L.links_set_tuning(s.ctx, nmax, 17, 0)
+    with Simulator(batch.B, nmax) as s2:
+        L.links_tuning_load(s2.ctx, path)
+        assert L.tuning_table(s2.ctx, nmax) == table
+        text = open(path).read().splitlines()
+        other = str(tmp_path / "other.txt")
+        with open(other, "w") as f:
+            f.write("links-tuning 1 sms 7 device some other GPU\n" + "\n".join(text[1:]) + "\n")
+        with pytest.raises(L.LinksError):
+            L.links_tuning_load(s2.ctx, other)
+    print(f"[shapes n_max={nmax}] autotuned {table}")
 
 
 @pytest.mark.parametrize("lanes", [8, 16, 32])
