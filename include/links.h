@@ -420,9 +420,13 @@ LINKS_API int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_
 #define LINKS_TUNE_EMIT_DWS 4     /* double-word slots of the emit: -1 by size (shared
                                      memory when n_max <= 12), 0 thread-local, 1 shared */
 #define LINKS_TUNE_EMIT_CTAS 5    /* CTAs per SM of the emit, 0 = as many as fit */
+#define LINKS_TUNE_SCREEN_DEFER 6 /* steps the screen's FP32 bounds leave uncertain: 0
+                                     recomputed in double-word at once by their lane, 1
+                                     their mechanisms left to a second, rescuing launch */
 
 /* Autotuner: on the plan as last built, over T steps, times the screen with every shape
- * (lanes 8/16/32 x steps per lane 1/2 x CTAs per SM all/2/1), then the emit (shared or
+ * (lanes 8/16/32 x steps per lane 1/2 x CTAs per SM all/2/1 x inline or deferred
+ * rescue), then the emit (shared or
  * thread-local double-word slots x CTAs per SM all/2/1) on up to 16384 valid rows of
  * that screen's result, and keeps the fastest of each in the context's table for this
  * n_max (*lanes receives the screen's lanes; may be NULL).  Each shape gives the same
@@ -435,7 +439,7 @@ LINKS_API int links_autotune(links_ctx ctx, links_plan plan, int T, int* lanes);
 LINKS_API int links_set_tuning(links_ctx ctx, int n_max, int key, int value);
 LINKS_API int links_get_tuning(links_ctx ctx, int n_max, int key, int* value);
 /* Writes the context's shape table to a text file (a header naming the device and its SM
- * count, then one line per n_max: n_max and the six keys in key order), or reads one
+ * count, then one line per n_max: n_max and the seven keys in key order), or reads one
  * back (LINKS_ESTATE if it was written on another kind of device, LINKS_EINVAL if
  * malformed or out of range; nothing is loaded then). */
 LINKS_API int links_tuning_save(links_ctx ctx, const char* path);

@@ -231,6 +231,7 @@ int links_plan_create(links_ctx ctx, int64_t capacity, int n_max, links_plan* ou
   alloc((void**)&d.dyad, sizeof(DyadRec) * d.max_dyads * c);
   alloc((void**)&d.order, sizeof(int32_t) * c);
   alloc((void**)&d.order2, sizeof(int32_t) * c);
+  alloc((void**)&d.rescue, sizeof(int32_t) * c);
   alloc((void**)&d.ctrs, sizeof(int32_t) * kCtrs);
   alloc((void**)&d.scan, sizeof(int32_t) * (c / 1024 + 2));
   if (e == cudaSuccess) e = cudaMemset(d.ctrs, 0, sizeof(int32_t) * kCtrs);
@@ -252,6 +253,7 @@ int links_plan_free(links_plan plan) {
   cudaFree(d.dyad);
   cudaFree(d.order);
   cudaFree(d.order2);
+  cudaFree(d.rescue);
   cudaFree(d.ctrs);
   cudaFree(d.scan);
   delete plan;
@@ -559,6 +561,7 @@ static int* tuning_field(links::Tuning& t, int key) {
     case LINKS_TUNE_SCREEN_CTAS: return &t.screen_ctas;
     case LINKS_TUNE_EMIT_DWS: return &t.emit_dws;
     case LINKS_TUNE_EMIT_CTAS: return &t.emit_ctas;
+    case LINKS_TUNE_SCREEN_DEFER: return &t.screen_defer;
     default: return nullptr;
   }
 }
@@ -571,6 +574,7 @@ static bool tuning_value_ok(int n_max, int key, int v) {
     case LINKS_TUNE_SCREEN_CTAS: return v >= 0 && v <= 32;
     case LINKS_TUNE_EMIT_DWS: return v >= -1 && v <= 1;
     case LINKS_TUNE_EMIT_CTAS: return v >= 0 && v <= 32;
+    case LINKS_TUNE_SCREEN_DEFER: return v == 0 || v == 1;
     default: return false;
   }
 }
@@ -603,11 +607,11 @@ int links_tuning_save(links_ctx ctx, const char* path) {
   LINKS_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
   FILE* f = fopen(path, "w");
   if (!f) return set_error(LINKS_EINVAL, std::string("links_tuning_save: cannot open ") + path);
-  fprintf(f, "links-tuning 1 sms %d device %s\n", prop.multiProcessorCount, prop.name);
+  fprintf(f, "links-tuning 2 sms %d device %s\n", prop.multiProcessorCount, prop.name);
   for (const auto& kv : ctx->tuning) {
     const links::Tuning& t = kv.second;
-    fprintf(f, "%d %d %d %d %d %d %d\n", kv.first, t.builder, t.screen_lanes, t.screen_steps, t.screen_ctas,
-            t.emit_dws, t.emit_ctas);
+    fprintf(f, "%d %d %d %d %d %d %d %d\n", kv.first, t.builder, t.screen_lanes, t.screen_steps, t.screen_ctas,
+            t.emit_dws, t.emit_ctas, t.screen_defer);
   }
   const bool ok = fclose(f) == 0;
   return ok ? LINKS_OK : set_error(LINKS_EINVAL, std::string("links_tuning_save: write failed: ") + path);
@@ -621,7 +625,7 @@ int links_tuning_load(links_ctx ctx, const char* path) {
   if (!f) return set_error(LINKS_EINVAL, std::string("links_tuning_load: cannot open ") + path);
   char name[256] = {0};
   int version = 0, sms = 0;
-  if (fscanf(f, "links-tuning %d sms %d device %255[^\n]", &version, &sms, name) != 3 || version != 1) {
+  if (fscanf(f, "links-tuning %d sms %d device %255[^\n]", &version, &sms, name) != 3 || version != 2) {
     fclose(f);
     return set_error(LINKS_EINVAL, "links_tuning_load: not a tuning file");
   }
@@ -630,14 +634,15 @@ int links_tuning_load(links_ctx ctx, const char* path) {
     return set_error(LINKS_ESTATE, "links_tuning_load: the file was tuned on another device");
   }
   std::map<int, links::Tuning> table;
-  int n, v[6];
+  int n, v[7];
   int st = LINKS_OK;
-  while (fscanf(f, "%d %d %d %d %d %d %d", &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5]) == 7) {
+  while (fscanf(f, "%d %d %d %d %d %d %d %d", &n, &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6]) == 8) {
     links::Tuning t;
-    const int keys[6] = {LINKS_TUNE_BUILDER, LINKS_TUNE_SCREEN_LANES, LINKS_TUNE_SCREEN_STEPS,
-                         LINKS_TUNE_SCREEN_CTAS, LINKS_TUNE_EMIT_DWS, LINKS_TUNE_EMIT_CTAS};
+    const int keys[7] = {LINKS_TUNE_BUILDER, LINKS_TUNE_SCREEN_LANES, LINKS_TUNE_SCREEN_STEPS,
+                         LINKS_TUNE_SCREEN_CTAS, LINKS_TUNE_EMIT_DWS, LINKS_TUNE_EMIT_CTAS,
+                         LINKS_TUNE_SCREEN_DEFER};
     bool ok = n >= 2 && n <= LINKS_MAX_JOINTS;
-    for (int k = 0; k < 6 && ok; ++k) {
+    for (int k = 0; k < 7 && ok; ++k) {
       ok = tuning_value_ok(n, keys[k], v[k]);
       if (ok) *tuning_field(t, keys[k]) = v[k];
     }

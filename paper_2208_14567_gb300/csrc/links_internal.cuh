@@ -36,6 +36,7 @@ struct PlanDev {
   DyadRec* dyad;         // [cap][n_max - 2]
   int32_t* order;        // [cap]          OK mechanisms sorted by dyad count
   int32_t* order2;       // [cap]          confirmation work list of the two-stage screen
+  int32_t* rescue;       // [cap]          mechanisms the screen left to its double-word pass
   int32_t* ctrs;         // [kCtrs]        histogram / cursors / work counters
   int32_t* scan;         // [cap/1024 + 2] block sums of the valid-row scan
   int32_t* row_of;       // [cap]          output row of each mechanism (VALID_ONLY), or -1
@@ -55,6 +56,7 @@ constexpr int kNConfirm = 67;     // length of the two-stage screen's confirmati
 constexpr int kStatEmitSteps = 68;     // steps the emit computes
 constexpr int kStatEmitDW = 70;        // ... that its FP32 bound sends to double-word
 constexpr int kStatEmitDWDyads = 72;   // ... in dyad-steps
+constexpr int kNRescue = 74;      // length of the screen's rescue list
 constexpr int kCtrs = 80;
 
 struct TTable {
@@ -72,6 +74,7 @@ struct Tuning {
   int screen_lanes = 8;  // lanes per mechanism: 8, 16, 32
   int screen_steps = 0;  // steps per lane: 0 by size (2 when n_max <= 9), 1, 2
   int screen_ctas = 0;   // CTAs per SM of the persistent screen; 0 = as many as fit
+  int screen_defer = 0;  // uncertain steps: 0 rescued inline, 1 deferred to a second launch
   int emit_dws = -1;     // double-word slots of the emit in shared memory: -1 by size, 0, 1
   int emit_ctas = 0;     // CTAs per SM of the emit; 0 = as many as fit
 };

@@ -111,6 +111,7 @@ PlanDev view(const PlanDev& p, int64_t a) {
   v.pos64 += a * p.n_max;
   v.dyad += a * p.max_dyads;
   v.order += a;
+  v.rescue += a;
   return v;
 }
 
@@ -343,6 +344,7 @@ void serve_free(ServeState* s) {
   cudaFree(d.pos64);
   cudaFree(d.dyad);
   cudaFree(d.order);
+  cudaFree(d.rescue);
   cudaFree(d.ctrs);
   cudaFree(d.scan);
   cudaFreeHost(s->h_nout);
@@ -415,6 +417,7 @@ int links_serve_start(links_ctx ctx, size_t mem_budget_bytes, int max_pending, i
   al((void**)&d.pos64, sizeof(double2) * n_max * cap);
   al((void**)&d.dyad, sizeof(DyadRec) * d.max_dyads * cap);
   al((void**)&d.order, sizeof(int32_t) * cap);
+  al((void**)&d.rescue, sizeof(int32_t) * cap);
   al((void**)&d.ctrs, sizeof(int32_t) * kCtrs);
   al((void**)&d.scan, sizeof(int32_t) * (cap / 1024 + 2));
   if (e == cudaSuccess) e = cudaMemset(s->priv.d_err, 0, 4);

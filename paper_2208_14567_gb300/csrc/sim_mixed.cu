@@ -113,7 +113,13 @@ __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char*
 // load of a dyad record serves S steps.  The slot arrays hold S columns per lane.
 // The work list is order[0, n) with n = *n_list, or p.order and the number of OK
 // mechanisms when n_list is null.
-template <int G, int S>
+// With RESCUE a step that the FP32 bounds leave uncertain is recomputed at once in
+// double-word arithmetic by its lane (the others of the warp wait).  Without it, a
+// mechanism whose first uncertain step of a chunk comes before the chunk's first
+// certain lock (the only case where the uncertain step can decide anything) is put on
+// the rescue list p.rescue and left; a second launch with RESCUE screens that list.
+// Every other mechanism gets the same outputs either way.
+template <int G, int S, bool RESCUE>
 __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, const float4* __restrict__ cs,
                                                         uint8_t* __restrict__ valid,
                                                         int16_t* __restrict__ lock_step,
@@ -237,7 +243,8 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
         else fp32_dyad_rec(r0, r1, Pb, Eb, lockw[0], zmin[0], isgmax[0]);
       }
     // per step: certain lock, certain freedom, or a double-word rescue that decides
-    int first = CH;  // first locking step of the chunk (group-uniform)
+    int first = CH;      // first locking step of the chunk (group-uniform)
+    int first_amb = CH;  // first uncertain step of the chunk (deferring launch)
     float qstep[S];
 #pragma unroll
     for (int u = 0; u < S; ++u) {
@@ -247,7 +254,7 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       const bool amb = act && !certain_lock && !(zmin[u] >= 0.0f);
       qstep[u] = __fdividef(1.0f, isgmax[u] * isgmax[u]);
       bool locked = act && certain_lock;
-      if (amb) {
+      if (RESCUE && amb) {
         dwp loc[kMaxJ];
         float qd;
         locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), LocLocal{loc}, &qd);
@@ -255,21 +262,30 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
       }
       const unsigned lb = __ballot_sync(kFull, locked) & gmask;
       if (lb && first == CH) first = u * G + (__ffs(lb) - 1 - g * G);
+      if (!RESCUE) {
+        const unsigned ab = __ballot_sync(kFull, amb) & gmask;
+        if (ab && first_amb == CH) first_amb = u * G + (__ffs(ab) - 1 - g * G);
+      }
     }
+    // an uncertain step that decides (group-uniform): leave the mechanism to the rescue
+    const bool defer = !RESCUE && has && first_amb < first;
+    if (defer && gl == 0) p.rescue[atomicAdd(&p.ctrs[kNRescue], 1)] = (int32_t)b;
 #pragma unroll
     for (int u = 0; u < S; ++u) {
       const int t = chunk * CH + u * G + gl;
-      if (has && t < T && u * G + gl < first) qacc = fminf(qacc, qstep[u]);
+      if (has && !defer && t < T && u * G + gl < first) qacc = fminf(qacc, qstep[u]);
     }
-    const bool done = has && (first < CH || (chunk + 1) * CH >= T);
+    const bool done = has && (defer || first < CH || (chunk + 1) * CH >= T);
     if (done) {
-      float qr = qacc;
+      if (!defer) {
+        float qr = qacc;
 #pragma unroll
-      for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(gmask, qr, o));
-      if (gl == 0) {
-        valid[b] = first == CH;
-        lock_step[b] = (int16_t)(first < CH ? chunk * CH + first : -1);
-        min_disc[b] = qr;
+        for (int o = 1; o < G; o <<= 1) qr = fminf(qr, __shfl_xor_sync(gmask, qr, o));
+        if (gl == 0) {
+          valid[b] = first == CH;
+          lock_step[b] = (int16_t)(first < CH ? chunk * CH + first : -1);
+          min_disc[b] = qr;
+        }
       }
       item = -1;
     } else {
@@ -417,25 +433,45 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
 // as fit).
 struct ScreenShape {
   int G = 8, S = 1, ctas = 0;
+  bool defer = false;
 };
 
+// The screen in two launches: the deferring screen over the work list, then the
+// rescuing screen over the mechanisms it left (p.rescue, a list usually a few percent
+// long; the persistent grid's idle CTAs exit at once).
 template <int G, int S>
 int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid, int16_t* lock_step,
-                  float* min_disc, const int32_t* order, const int32_t* n_list, int ctas) {
+                  float* min_disc, const int32_t* order, const int32_t* n_list, int ctas, bool defer) {
   PlanDev& p = plan->d;
   size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
   // a function attribute of the current device's context: set on every launch (a host
   // call, no stream work), so other devices and contexts get it too
-  LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int per_sm = 0;
-  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G, S>, kBlock, smem));
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, screen_kernel<G, S, false>, kBlock, smem));
   if (ctas > 0 && ctas < per_sm) per_sm = ctas;
   if (per_sm < 1) per_sm = 1;
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
+  if (!defer) {
+    KernelScope ks(ctx, "mixed_screen");
+    screen_kernel<G, S, true><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
+        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list);
+    LINKS_CUDA(cudaGetLastError());
+    return LINKS_OK;
+  }
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kNRescue, 0, sizeof(int32_t), ctx->stream));
   {
     KernelScope ks(ctx, "mixed_screen");
-    screen_kernel<G, S><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
+    screen_kernel<G, S, false><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
         p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
+  {
+    KernelScope ks(ctx, "mixed_screen_rescue");
+    screen_kernel<G, S, true><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
+        p, T, tab->cs, valid, lock_step, min_disc, p.rescue, p.ctrs + kNRescue);
   }
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
@@ -451,6 +487,7 @@ ScreenShape screen_shape(links_ctx ctx, int n_max) {
   sh.S = t.screen_steps ? t.screen_steps : (n_max <= kScreenTwoStepMaxSlots ? 2 : 1);
   if (n_max > kScreenTwoStepLimit) sh.S = 1;
   sh.ctas = t.screen_ctas;
+  sh.defer = t.screen_defer != 0;
   return sh;
 }
 
@@ -459,13 +496,13 @@ int launch_screen_shape(links_ctx ctx, links_plan plan, int T, const TTable* tab
                         const int32_t* order = nullptr, const int32_t* n_list = nullptr) {
   const int c = sh.ctas;
   if (sh.S == 2) {
-    if (sh.G == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
-    if (sh.G == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
-    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+    if (sh.G == 32) return launch_screen<32, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
+    if (sh.G == 16) return launch_screen<16, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
+    return launch_screen<8, 2>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
   }
-  if (sh.G == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
-  if (sh.G == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
-  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c);
+  if (sh.G == 32) return launch_screen<32, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
+  if (sh.G == 16) return launch_screen<16, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
+  return launch_screen<8, 1>(ctx, plan, T, tab, valid, lock_step, min_disc, order, n_list, c, sh.defer);
 }
 
 int launch_screen_tuned(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid,
@@ -593,20 +630,22 @@ int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) 
   for (int S : {1, 2}) {
     if (S == 2 && n_max > kScreenTwoStepLimit) continue;
     for (int G : {8, 16, 32})
-      for (int ctas : {0, 2, 1}) {
-        if (st) break;
-        ScreenShape sh{G, S, ctas};
-        const float ms = timed([&] { return launch_screen_shape(ctx, plan, T, tab, v, l, q, sh); });
-        if (ms < best_ms) {
-          best_ms = ms;
-          best_sh = sh;
+      for (int ctas : {0, 2, 1})
+        for (int defer : {0, 1}) {
+          if (st) break;
+          ScreenShape sh{G, S, ctas, defer != 0};
+          const float ms = timed([&] { return launch_screen_shape(ctx, plan, T, tab, v, l, q, sh); });
+          if (ms < best_ms) {
+            best_ms = ms;
+            best_sh = sh;
+          }
         }
-      }
   }
   if (!st) {
     best.screen_lanes = best_sh.G;
     best.screen_steps = best_sh.S;
     best.screen_ctas = best_sh.ctas;
+    best.screen_defer = best_sh.defer ? 1 : 0;
     // the emit on up to kTuneRows valid rows of the chosen screen's result
     st = launch_screen_shape(ctx, plan, T, tab, v, l, q, best_sh);
     if (!st) st = compact_valid(ctx, plan, v, idx, B, nout);

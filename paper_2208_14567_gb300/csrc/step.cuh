@@ -14,8 +14,10 @@ __device__ __forceinline__ float min3(float a, float b, float c) {
   return r;
 }
 __device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-propagating
+  // two two-input minima: the three-input NaN-propagating form is not one instruction
   float r;
-  asm("min.NaN.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(r), "f"(c));
   return r;
 }
 

@@ -470,9 +470,11 @@ def links_set_chamfer_prune(ctx, on: bool):
     _check(lib().links_set_chamfer_prune(ctx, 1 if on else 0), "links_set_chamfer_prune")
 
 
-TUNE_BUILDER, TUNE_SCREEN_LANES, TUNE_SCREEN_STEPS, TUNE_SCREEN_CTAS, TUNE_EMIT_DWS, TUNE_EMIT_CTAS = range(6)
+(TUNE_BUILDER, TUNE_SCREEN_LANES, TUNE_SCREEN_STEPS, TUNE_SCREEN_CTAS, TUNE_EMIT_DWS, TUNE_EMIT_CTAS,
+ TUNE_SCREEN_DEFER) = range(7)
 TUNE_KEYS = {"builder": TUNE_BUILDER, "screen_lanes": TUNE_SCREEN_LANES, "screen_steps": TUNE_SCREEN_STEPS,
-             "screen_ctas": TUNE_SCREEN_CTAS, "emit_dws": TUNE_EMIT_DWS, "emit_ctas": TUNE_EMIT_CTAS}
+             "screen_ctas": TUNE_SCREEN_CTAS, "emit_dws": TUNE_EMIT_DWS, "emit_ctas": TUNE_EMIT_CTAS,
+             "screen_defer": TUNE_SCREEN_DEFER}
 
 
 def links_set_tuning(ctx, n_max: int, key: int, value: int):

@@ -491,6 +491,7 @@ def test_every_kernel_shape_gives_the_same_outputs(L, nmax, tmp_path):
     db = to_device(batch)
     shapes = [dict(screen_lanes=8), dict(screen_lanes=16, screen_steps=1), dict(screen_lanes=32, screen_ctas=1),
               dict(screen_lanes=8, screen_steps=2 if nmax <= 16 else 1, screen_ctas=2),
+              dict(screen_lanes=16, screen_defer=1), dict(screen_lanes=8, screen_defer=1, screen_steps=1),
               dict(emit_dws=0), dict(emit_dws=1, emit_ctas=1), dict(emit_dws=0, emit_ctas=2)]
     ref = None
     with Simulator(batch.B, nmax) as s:
@@ -527,7 +528,7 @@ def test_every_kernel_shape_gives_the_same_outputs(L, nmax, tmp_path):
         text = open(path).read().splitlines()
         other = str(tmp_path / "other.txt")
         with open(other, "w") as f:
-            f.write("links-tuning 1 sms 7 device some other GPU\n" + "\n".join(text[1:]) + "\n")
+            f.write("links-tuning 2 sms 7 device some other GPU\n" + "\n".join(text[1:]) + "\n")
         with pytest.raises(L.LinksError):
             L.links_tuning_load(s2.ctx, other)
     print(f"[shapes n_max={nmax}] autotuned {table}")
