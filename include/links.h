@@ -323,7 +323,13 @@ LINKS_API int links_set_chamfer_prune(links_ctx ctx, int on);
 LINKS_API int links_workspace_reserve(links_ctx ctx, size_t bytes);
 
 /* ---- Serving: continuous batching of candidate batches (no counterpart in the paper;
- * the form in which the simulation path is offered as a service).
+ * the form in which the simulation path is offered as a service).  The request loop
+ * runs on the GPU: a persistent cooperative kernel takes the admitted batches ("passes")
+ * from a descriptor ring in device memory and runs each pass's plan build, screen,
+ * valid-row compaction, emit and path normalisation between grid barriers; a host
+ * thread only admits requests, copies their inputs and results, and relaunches the
+ * kernel when it has exited after 2 ms without work.  While requests are in flight the
+ * kernel occupies every SM. 
  * A request is a batch of `count` candidates in the layout of links_plan_build,
  * padded to the serving n_max, positions float32, all in HOST memory (pinned for
  * full overlap) that stays valid until the ticket completes.  Its outputs are
@@ -356,11 +362,13 @@ typedef struct {
   double done_ms;
 } links_result;
 
-/* Starts the scheduler thread.  The device arena holds the candidates of every
- * admitted request (inputs, plans, flags, paths): mem_budget_bytes bounds it, and a
- * request is admitted only when its candidates fit (memory-bounded admission).  Up
- * to max_pending requests may wait for admission; T <= 1024 steps; with_traj != 0
- * also returns trajectories.  Work runs on the library's own streams. */
+/* Starts serving.  The device arena holds the candidates of every admitted request
+ * (inputs, plans, flags, paths): mem_budget_bytes bounds it, and a request is admitted
+ * only when its candidates fit (memory-bounded admission).  Up to max_pending requests
+ * may wait for admission; T <= 256 steps; with_traj != 0 also returns trajectories.
+ * The screen's lanes per mechanism and the emit's slot storage come from ctx's shape
+ * table for n_max (links_set_tuning / links_autotune before this call).  Work runs on
+ * the library's own streams.  LINKS_ESTATE on a device without cooperative launch. */
 LINKS_API int links_serve_start(links_ctx ctx, size_t mem_budget_bytes, int max_pending, int n_max, int T,
                                 int with_traj);
 /* Enqueues a request (non-blocking): LINKS_EBUSY when max_pending requests already
@@ -372,7 +380,18 @@ LINKS_API int links_serve_poll(links_ctx ctx, uint64_t ticket, int timeout_us, l
 /* Holds (paused = 1) or resumes (0) admission of new requests; admitted work
  * continues.  For host-side fault-injection tests. */
 LINKS_API int links_serve_pause(links_ctx ctx, int paused);
-/* Finishes all submitted requests, stops the scheduler and frees the arena. */
+/* Fault injection (a host-side trigger; nothing faults the GPU): one grid barrier of the
+ * next pass waits for a block that does not exist and gives up after wait_ms (1 to
+ * 10000); the serving kernel then returns, and that pass's requests, with any published
+ * behind it, complete with LINKS_EDEVICE (the kernel's bounded wait ran out).  Later
+ * requests are served normally. */
+LINKS_API int links_serve_inject_stall(links_ctx ctx, int wait_ms);
+/* out[6] (host): passes published so far, launches of the serving kernel, its blocks,
+ * the arena's capacity in candidates, the kernel's error word when it last returned
+ * with one (1: a barrier's wait ran out, 2: the emit met a lock the screen had not
+ * found, 4: a pass descriptor out of sequence), and passes finished. */
+LINKS_API int links_serve_stats(links_ctx ctx, int64_t* out);
+/* Finishes all submitted requests, stops the request loop and frees the arena. */
 LINKS_API int links_serve_stop(links_ctx ctx);
 
 /* Per-kernel timing for benchmarks: with enable = 1 (collection cleared), every

@@ -17,7 +17,17 @@
 
 namespace links {
 
+// Loads of data that a kernel only reads: through the non-coherent read-only path (NC,
+// for data no one writes while the kernel runs), or L2-coherent (for a persistent
+// kernel that reads what other blocks or copies wrote during its lifetime).
+template <bool NC, class T>
+__device__ __forceinline__ T ldro(const T* p) {
+  if constexpr (NC) return __ldg(p);
+  else return __ldcg(p);
+}
+
 constexpr int kMaxJ = LINKS_MAX_JOINTS;  // joints per mechanism (bit masks are uint32)
+constexpr unsigned kFull = 0xffffffffu;  // every lane of a warp
 constexpr float kEmitBudget = 9.5e-6f;
 
 // ---------------------------------------------------------------------------------------

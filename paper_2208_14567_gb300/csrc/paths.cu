@@ -26,19 +26,11 @@
 
 #include <algorithm>
 
-#include "links_internal.cuh"
+#include "path_core.cuh"
 #include "packed.cuh"
 
 namespace links {
 namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
 
 template <int PL>
 __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const float2* __restrict__ in,
@@ -47,78 +39,7 @@ __global__ void __launch_bounds__(256) normalize_kernel(int64_t M, int T, const 
   if (M_dev) M = min(M, (int64_t)*M_dev);
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float invT = 1.0f / (float)T;
-  for (int64_t m = w0; m < M; m += nw) {
-    const float2* src = in + m * T;
-    float2 p[PL];
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      int t = lane + 32 * i;
-      p[i] = t < T ? __ldcs(src + t) : make_float2(0.f, 0.f);
-    }
-    // work relative to the first point: smaller magnitudes, and a curve of equal
-    // points becomes exactly zero (so it is recognised below)
-    const float ox = __shfl_sync(kFull, p[0].x, 0), oy = __shfl_sync(kFull, p[0].y, 0);
-    float sx = 0.f, sy = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      if (lane + 32 * i < T) {
-        p[i].x -= ox;
-        p[i].y -= oy;
-        sx += p[i].x;
-        sy += p[i].y;
-      }
-    }
-    const float cx = warp_sum(sx) * invT, cy = warp_sum(sy) * invT;
-    float r2 = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      if (lane + 32 * i < T) {
-        p[i].x -= cx;
-        p[i].y -= cy;
-        r2 = fmaf(p[i].x, p[i].x, fmaf(p[i].y, p[i].y, r2));
-      }
-    }
-    const float ms = warp_sum(r2) * invT;
-    float2* dst = out + m * T;
-    if (!(ms > 0.f)) {
-#pragma unroll
-      for (int i = 0; i < PL; ++i)
-        if (lane + 32 * i < T) __stcs(dst + lane + 32 * i, make_float2(0.f, 0.f));
-      continue;
-    }
-    const float inv = rsqrtf(ms);
-    float a = 0.f, bxy = 0.f, c = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      if (lane + 32 * i < T) {
-        p[i].x *= inv;
-        p[i].y *= inv;
-        a = fmaf(p[i].x, p[i].x, a);
-        bxy = fmaf(p[i].x, p[i].y, bxy);
-        c = fmaf(p[i].y, p[i].y, c);
-      }
-    }
-    const float sxx = warp_sum(a) * invT, sxy = warp_sum(bxy) * invT, syy = warp_sum(c) * invT;
-    const float dxy = sxx - syy;
-    const float gap = sqrtf(fmaf(dxy, dxy, 4.f * sxy * sxy));
-    float cs = 1.f, sn = 0.f;
-    if (gap > 1e-9f * (sxx + syy)) sincosf(0.5f * atan2f(2.f * sxy, dxy), &sn, &cs);
-    float s3 = 0.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i) {
-      if (lane + 32 * i < T) {
-        float xr = fmaf(cs, p[i].x, sn * p[i].y);
-        float yr = fmaf(-sn, p[i].x, cs * p[i].y);
-        p[i] = make_float2(xr, yr);
-        s3 = fmaf(xr * xr, xr, s3);
-      }
-    }
-    const float sg = warp_sum(s3) < 0.f ? -1.f : 1.f;
-#pragma unroll
-    for (int i = 0; i < PL; ++i)
-      if (lane + 32 * i < T) __stcs(dst + lane + 32 * i, make_float2(sg * p[i].x, sg * p[i].y));
-  }
+  for (int64_t m = w0; m < M; m += nw) normalize_warp<PL>(m, T, in, out, lane);
 }
 
 // The paper's path normalisation (Sec. "Dataset Curation & Processing"): the farthest

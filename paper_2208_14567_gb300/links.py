@@ -87,6 +87,8 @@ def lib():
             "links_serve_poll": ([P, ctypes.c_uint64, i32, ctypes.POINTER(Result)], i32),
             "links_serve_pause": ([P, i32], i32),
             "links_serve_stop": ([P], i32),
+            "links_serve_inject_stall": ([P, i32], i32),
+            "links_serve_stats": ([P, P], i32),
             "links_profile": ([P, i32], i32),
             "links_profile_read": ([P, i32, P, P, P, P], i32),
             "links_launch_count": ([P, P], i32),
@@ -409,6 +411,17 @@ def links_serve_poll(ctx, ticket: int, timeout_us: int):
 
 def links_serve_pause(ctx, paused: bool):
     _check(lib().links_serve_pause(ctx, 1 if paused else 0), "links_serve_pause")
+
+
+def links_serve_inject_stall(ctx, wait_ms: int):
+    _check(lib().links_serve_inject_stall(ctx, int(wait_ms)), "links_serve_inject_stall")
+
+
+def links_serve_stats(ctx) -> dict:
+    out = (ctypes.c_int64 * 6)()
+    _check(lib().links_serve_stats(ctx, out), "links_serve_stats")
+    return dict(zip(("passes", "kernel_launches", "blocks", "capacity", "last_error_word", "passes_done"),
+                    (int(v) for v in out)))
 
 
 def links_serve_stop(ctx):

@@ -1,6 +1,7 @@
-"""Continuous-batching serving: results are the same alone and in the mix, match the
-batch path and the oracle, and admission / timeouts behave (host-side fault injection:
-paused admission, a full queue, an oversized request, a poll that times out)."""
+"""Continuous-batching serving (the request loop runs on the device): results are the
+same alone and in the mix, match the batch path and the oracle, and admission /
+timeouts behave (host-side fault injection: paused admission, a full queue, an
+oversized request, a poll that times out, a device barrier whose wait runs out)."""
 import time
 
 import numpy as np
@@ -162,9 +163,13 @@ def test_overload_many_small_requests_behind_a_large_one(L):
             tickets.append((t, keep))
             time.sleep(2e-5)
         results = [wait(L, ctx, t) for t, _ in tickets]
+        stats = L.links_serve_stats(ctx)
         L.links_serve_stop(ctx)
     finally:
         L.links_destroy(ctx)
+    # the request loop ran on the device: many passes per launch of its kernel
+    assert stats["kernel_launches"] < stats["passes"]
+    print(f"overload: {stats}")
     from paper_2208_14567_gb300.api import Simulator, to_device
     allb = pool.slice(0, int(sizes.sum()))
     with Simulator(allb.B, NMAX) as s:
@@ -223,6 +228,43 @@ def test_admission_timeout_and_refusals(L):
     margin = ~(ref.min_abs_q > 1e-9)
     got = np.concatenate([outs[0].valid, outs[1].valid])
     assert not ((got != ref.valid) & ~margin).any()
+
+
+def test_device_loop_barrier_timeout_is_reported_and_recovered(L):
+    """Fault injection on the host side: one grid barrier of the next pass waits for a
+    block that does not exist.  The wait gives up after 200 ms, the serving kernel returns,
+    the request completes with LINKS_EDEVICE, and the next request is served normally
+    (same flags and paths as the batch path)."""
+    pool = I.dyad_batch(3000, 6, 12, seed=36, nmax=NMAX)
+    a, b = pool.slice(0, 1500), pool.slice(1500, 3000)
+    ctx = L.links_create(0, torch.cuda.current_stream())
+    try:
+        L.links_serve_start(ctx, 64 << 20, 8, NMAX, T)
+        L.links_serve_inject_stall(ctx, 200)
+        oa = Out(a.B)
+        t, keep = submit(L, ctx, a, oa)
+        with pytest.raises(L.LinksError) as e:
+            wait(L, ctx, t)
+        assert e.value.status == L.EDEVICE
+        ob = Out(b.B)
+        t, keep = submit(L, ctx, b, ob)
+        rb = wait(L, ctx, t)
+        assert rb.status == 0
+        with pytest.raises(L.LinksError):
+            L.links_serve_inject_stall(ctx, 0)
+        L.links_serve_stop(ctx)
+    finally:
+        L.links_destroy(ctx)
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    with Simulator(b.B, NMAX) as s:
+        s.build(to_device(b))
+        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=True)
+        n = int(o.n_out[0])
+        p = o.path[:n].clone()
+        L.links_normalize(s.ctx, p, p)
+        s.sync()
+        assert np.array_equal(o.valid.cpu().numpy(), ob.valid) and rb.n_valid == n
+        assert np.array_equal(p.cpu().numpy(), ob.paths[:n])
 
 
 def req_arrays(b):
