@@ -495,10 +495,11 @@ def curation_stage(args, local, stream):
 
 
 def serve_stage(args, local, stream):
-    """Poisson arrivals of requests of log-uniform size on [1, 65536] candidates of
-    6-20 joints, served by the continuous-batching loop; p50/p99 latency (submit to
-    results in host memory) and throughput, beside the plain FP64 batch path on the
-    same candidate mix."""
+    """Requests of log-uniform size on [1, 65536] candidates of 6-20 joints served by the
+    device-side request loop: Poisson arrivals at the configured rate (2k req/s), then the
+    same requests offered back to back (load above capacity: sustained throughput).
+    p50/p99 latency (submit to results in host memory) and mechanism-steps/s of each,
+    beside the plain FP64 and the mixed batch paths on the same candidate mix."""
     import threading
 
     import numpy as np
@@ -521,54 +522,69 @@ def serve_stage(args, local, stream):
                   idx=torch.empty(cap_rows, dtype=torch.int32).pin_memory().numpy(),
                   paths=torch.empty((cap_rows, T, 2), dtype=torch.float32).pin_memory().numpy())
              for _ in range(nslot)]
-    free = threading.Semaphore(nslot)
-    tickets = [None] * len(counts)
-    lat, res_all = [], []
     ctx = L.links_create(local, stream)
-    L.links_serve_start(ctx, args.serve_budget << 30, 256, NM, T)
-    done_evt = threading.Event()
 
-    def poller():
-        for i in range(len(counts)):
-            while tickets[i] is None:
-                time.sleep(2e-5)
+    def run(paced):
+        free = threading.Semaphore(nslot)
+        tickets = [None] * len(counts)
+        lat, res_all = [], []
+        done_evt = threading.Event()
+
+        def poller():
+            for i in range(len(counts)):
+                while tickets[i] is None:
+                    time.sleep(2e-5)
+                while True:
+                    r = L.links_serve_poll(ctx, tickets[i], 100000)
+                    if r is not None:
+                        break
+                res_all.append(r)
+                lat.append(r.done_ms - r.submit_ms)
+                free.release()
+            done_evt.set()
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        for i, (t, c, s0) in enumerate(zip(times, counts, starts)):
+            free.acquire()
+            sl = slots[i % nslot]
+            req = L.Request(int(c), host["n_joints"][s0:].ctypes.data, host["adj"][s0:].ctypes.data,
+                            host["jtype"][s0:].ctypes.data, host["pos"][s0:].ctypes.data, sl["valid"].ctypes.data,
+                            sl["lock"].ctypes.data, sl["md"].ctypes.data, cap_rows, sl["idx"].ctypes.data,
+                            sl["paths"].ctypes.data, None)
+            while paced and time.perf_counter() - t0 < t:
+                pass
             while True:
-                r = L.links_serve_poll(ctx, tickets[i], 100000)
-                if r is not None:
+                try:
+                    tickets[i] = L.links_serve_submit(ctx, req)
                     break
-            res_all.append(r)
-            lat.append(r.done_ms - r.submit_ms)
-            free.release()
-        done_evt.set()
+                except L.LinksError as e:
+                    if e.status != L.EBUSY:
+                        raise
+                    time.sleep(5e-5)
+        done_evt.wait(300)
+        th.join()
+        first = min(r.submit_ms for r in res_all)
+        last = max(r.done_ms for r in res_all)
+        wall = (last - first) * 1e-3
+        cand = int(counts.sum())
+        lat = np.array(lat)
+        return {"requests": len(counts), "candidates": cand, "wall_s": wall,
+                "offered_req_per_s": args.serve_rate if paced else None,
+                "served_req_per_s": len(counts) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "max_ms": float(lat.max()), "mechanism_steps_per_s": cand * T / wall,
+                "failed": int(sum(1 for r in res_all if r.status != 0))}
 
-    th = threading.Thread(target=poller)
-    th.start()
-    t0 = time.perf_counter()
-    for i, (t, c, s0) in enumerate(zip(times, counts, starts)):
-        free.acquire()
-        sl = slots[i % nslot]
-        req = L.Request(int(c), host["n_joints"][s0:].ctypes.data, host["adj"][s0:].ctypes.data,
-                        host["jtype"][s0:].ctypes.data, host["pos"][s0:].ctypes.data, sl["valid"].ctypes.data,
-                        sl["lock"].ctypes.data, sl["md"].ctypes.data, cap_rows, sl["idx"].ctypes.data,
-                        sl["paths"].ctypes.data, None)
-        while time.perf_counter() - t0 < t:
-            pass
-        while True:
-            try:
-                tickets[i] = L.links_serve_submit(ctx, req)
-                break
-            except L.LinksError as e:
-                if e.status != L.EBUSY:
-                    raise
-                time.sleep(5e-5)
-    done_evt.wait(300)
-    th.join()
-    L.links_serve_stop(ctx)
-    L.links_destroy(ctx)
-    first = min(r.submit_ms for r in res_all)
-    last = max(r.done_ms for r in res_all)
-    cand = int(counts.sum())
-    lat = np.array(lat)
+    try:
+        L.links_serve_start(ctx, args.serve_budget << 30, 256, NM, T)
+        poisson = run(True)
+        saturation = run(False)
+        stats = L.links_serve_stats(ctx)
+        L.links_serve_stop(ctx)
+    finally:
+        L.links_destroy(ctx)
     # plain FP64 batch path (and the mixed batch path) on a slice of the same pool
     nb = min(200_000, pool.B)
     sub = pool.slice(0, nb)
@@ -580,63 +596,21 @@ def serve_stage(args, local, stream):
             sim.sync()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            sim.build(to_device(sub, torch.device("cuda", local)))
             sim.simulate(T, prec, L.OUT_VALID_ONLY, out=o)
             e1.record(stream)
             sim.sync()
             batch_rates[name] = nb * T / (e0.elapsed_time(e1) * 1e-3)
             del o
-    return {"requests": len(counts), "candidates": cand, "offered_req_per_s": args.serve_rate,
-            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "max_ms": float(lat.max()), "mechanism_steps_per_s": cand * T / ((last - first) * 1e-3),
-            "wall_s": (last - first) * 1e-3, "batch_plain_f64_mech_steps_per_s": batch_rates["plain_f64"],
+    return {"loop": "device-side persistent kernel (descriptor ring, bounded grid barriers)",
+            "poisson": poisson, "saturation": saturation,
+            "p50_ms": poisson["p50_ms"], "p99_ms": poisson["p99_ms"],
+            "mechanism_steps_per_s": poisson["mechanism_steps_per_s"],
+            "saturation_over_batch_mixed": saturation["mechanism_steps_per_s"] / batch_rates["mixed"],
+            "saturation_over_batch_plain_f64": saturation["mechanism_steps_per_s"] / batch_rates["plain_f64"],
+            "batch_plain_f64_mech_steps_per_s": batch_rates["plain_f64"],
             "batch_mixed_mech_steps_per_s": batch_rates["mixed"], "joints": "6-20", "T": T,
-            "budget_GiB": args.serve_budget}
-
-
-def profile_kernels(args):
-    """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
-    (no timing): plan build, screen and emit of args.batch 6-8-joint candidates; max-line
-    normalisation of their valid coupler paths; curation of their trajectories; a first-3
-    scan of 16 queries over those paths; the generic screen and the screen compiled for
-    one topology of the paper's generator on the same args.batch samples."""
-    import torch
-
-    from paper_2208_14567_gb300 import inputs as I
-    from paper_2208_14567_gb300 import links as L
-    from paper_2208_14567_gb300.api import Simulator, to_device
-    T, B = args.T, args.batch
-    dev = torch.device("cuda", 0)
-    batch = I.dyad_batch(B, 6, 8, seed=0)
-    db = to_device(batch, dev)
-    with Simulator(B, 8) as s:
-        s.build(db)
-        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=True, path=True, out_capacity=B // 3)
-        s.sync()
-        nv = min(int(o.n_out[0]), B // 3)
-        paths, traj, rows = o.path[:nv], o.traj[:nv], o.out_index[:nv]
-        ml = torch.empty_like(paths)
-        L.links_normalize_maxline(s.ctx, paths, ml)
-        flags = torch.empty((nv, 8), dtype=torch.uint8, device=dev)
-        nk = torch.empty(1, dtype=torch.int32, device=dev)
-        L.links_curate_paths(s.ctx, traj, rows, db.n_joints, db.adj, db.jtype, flags, nk)
-        q = ml[:16].clone()
-        order = torch.randperm(nv, generator=torch.Generator().manual_seed(5)).to(torch.int32).to(dev)
-        idx = torch.empty((16, 3), dtype=torch.int32, device=dev)
-        dist = torch.empty((16, 3), dtype=torch.float32, device=dev)
-        L.links_chamfer_first_under(s.ctx, q, ml, order, 0.03, 3, idx, dist)
-        s.sync()
-    pb = I.paper_batch(1, B, 8, seed=108)
-    with Simulator(pb.B, 8) as s:
-        s.build(to_device(pb, dev))
-        s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)  # the generic screen, same samples
-        s.sync()
-        topo = L.links_topo_create(s.ctx, int(pb.n_joints[0]), pb.adj[0], pb.jtype[0], 16)
-        try:
-            s.simulate_topology(topo, T, L.OUT_VALID_ONLY, traj=False, path=False)
-            s.sync()
-        finally:
-            L.links_topo_free(topo)
-    print(json.dumps({"profile_kernels": "done", "batch": B, "valid_rows": nv}))
+            "budget_GiB": args.serve_budget, "loop_stats": stats}
 
 
 def make_batch(cfg, B, seed):

@@ -12,8 +12,9 @@
 // trajectories), normalisation -- separated by grid barriers, then reports the pass's
 // valid count and completion to mapped host memory.  Requests that arrive while a pass
 // runs are copied in meanwhile and published; the kernel takes them as soon as the
-// pass ends, without any host launch.  The feeder copies the finished passes' results
-// to the callers' buffers and completes their tickets.
+// pass ends, without any host launch.  The feeder copies the finished passes' flags
+// and row indices, then each request's rows straight from the device into its
+// buffers, and completes the tickets.
 //
 // Every wait is bounded: the kernel's poll for work ends after an idle limit (the
 // kernel exits; the feeder relaunches it when work is published), each grid barrier
@@ -40,6 +41,7 @@ namespace {
 
 constexpr int kSlots = 64;            // passes in flight (each owns a count slot)
 constexpr int kRing = 128;            // descriptor ring entries (> kSlots)
+constexpr int kAhead = 2;             // passes published and not finished (one runs, one waits)
 constexpr int kLoopWarps = 8;         // warps per block of the serving kernel
 constexpr int kLoopThreads = 32 * kLoopWarps;
 constexpr int kLoopPL = 8;            // normalisation: points per lane (T <= 256)
@@ -393,7 +395,7 @@ struct Pass {
   cudaEvent_t d2h_done = nullptr;
   unsigned long long seq = 0;
   int slot = 0;   // count slot
-  int stage = 0;  // 1 = published, 2 = results copy issued, 3 = failed
+  int stage = 0;  // 1 published, 2 flags and row indices being copied, 3 rows being copied, 4 failed
   int32_t n_valid = 0;
 };
 
@@ -442,10 +444,8 @@ struct ServeState {
   int32_t last_loop_err = 0;  // the kernel's error word when it last returned with one
   unsigned long long last_done = 0;
   int idle_launches = 0;       // launches since the finished-pass count last moved
-  // pinned host staging of the rows of a pass
+  // pinned host staging of the row indices of a pass
   int32_t* h_idx = nullptr;
-  float* h_path = nullptr;
-  float* h_traj = nullptr;
   // scheduling
   std::mutex mu;
   std::condition_variable cv;
@@ -546,30 +546,34 @@ int launch_loop(ServeState* s) {
   return LINKS_OK;
 }
 
-void finish_pass(ServeState* s, Pass* p) {
-  // rows [0, n) of the pass, in increasing arena index, split by request
-  const int n = p->stage == 3 ? 0 : p->n_valid;
-  int row = 0;
+// The pass's row indices are in host staging (increasing arena index): each request's
+// valid rows are one contiguous range of them.  Its indices go to valid_index, and its
+// paths (and trajectories) are copied from the device straight into its buffers.
+void copy_rows(ServeState* s, Pass* p) {
+  const int64_t n = std::min<int64_t>(p->n_valid, p->b - p->a);
+  int64_t row = 0;
   for (Req* r : p->reqs) {
     const int64_t lo = r->off - p->a, hi = lo + r->r.count;
-    int64_t k = 0;
-    while (row < n && s->h_idx[row] < hi) {
-      const int64_t i = s->h_idx[row] - lo;
-      if (k < r->r.out_capacity) {
-        if (r->r.valid_index) r->r.valid_index[k] = (int32_t)i;
-        if (r->r.paths) memcpy(r->r.paths + k * s->T * 2, s->h_path + (int64_t)row * s->T * 2, sizeof(float) * s->T * 2);
-        if (r->r.traj && s->h_traj)
-          memcpy(r->r.traj + k * s->n_max * s->T * 2, s->h_traj + (int64_t)row * s->n_max * s->T * 2,
-                 sizeof(float) * s->n_max * s->T * 2);
-      }
-      ++k;
-      ++row;
-    }
-    r->n_valid = k;
-    r->t_done = now_ms();
+    const int64_t first = row;
+    while (row < n && s->h_idx[row] < hi) ++row;
+    r->n_valid = row - first;
+    const int64_t k = std::min<int64_t>(r->n_valid, r->r.out_capacity);
+    if (r->r.valid_index)
+      for (int64_t q = 0; q < k; ++q) r->r.valid_index[q] = (int32_t)(s->h_idx[first + q] - lo);
+    if (k > 0 && r->r.paths)
+      cudaMemcpyAsync(r->r.paths, s->path + (p->a + first) * s->T * 2, k * s->T * 8, cudaMemcpyDeviceToHost, s->copy);
+    if (k > 0 && r->r.traj && s->traj)
+      cudaMemcpyAsync(r->r.traj, s->traj + (p->a + first) * s->n_max * s->T * 2, k * s->n_max * s->T * 8,
+                      cudaMemcpyDeviceToHost, s->copy);
   }
+}
+
+void finish_pass(ServeState* s, Pass* p) {
+  const double t = now_ms();
   std::lock_guard<std::mutex> lk(s->mu);
   for (Req* r : p->reqs) {
+    if (p->stage == 4) r->n_valid = 0;
+    r->t_done = t;
     r->done = true;
     ring_free(s, r->off, r->r.count);
   }
@@ -587,7 +591,7 @@ void loop_failed(ServeState* s, int32_t err) {
   const unsigned long long done = *reinterpret_cast<volatile unsigned long long*>(&s->mb->done);
   for (Pass* p : s->inflight)
     if (p->stage == 1 && p->seq > done) {
-      p->stage = 3;
+      p->stage = 4;
       for (Req* r : p->reqs) r->status = st;
     }
   // the copies of every published pass are complete before the control block changes
@@ -613,7 +617,11 @@ void worker_main(ServeState* s) {
       // the passes in flight plus those of this round leave a slot for one more.
       int64_t run_end = -1;
       int runs = 0;
-      while (!s->pending.empty() && !s->paused) {
+      // Continuous batching: at most kAhead passes wait for the kernel; requests that
+      // arrive meanwhile gather into the next pass.
+      const unsigned long long done_now = *reinterpret_cast<volatile unsigned long long*>(&s->mb->done);
+      const bool room = s->published - done_now < (unsigned long long)kAhead;
+      while (room && !s->pending.empty() && !s->paused) {
         Req* r = s->pending.front();
         if ((int)s->inflight.size() + runs + 1 > kSlots) break;
         int64_t off = ring_alloc(s, r->r.count);
@@ -695,39 +703,39 @@ void worker_main(ServeState* s) {
         s->worker_error = st;
         for (Pass* p : s->inflight)
           if (p->stage == 1) {
-            p->stage = 3;
+            p->stage = 4;
             for (Req* r : p->reqs) r->status = st;
           }
       }
       progressed = true;
     }
-    // Retire passes in order.
+    // Retire passes in order: flags and row indices, then the rows, then the tickets.
     while (!s->inflight.empty()) {
       Pass* p = s->inflight.front();
       if (p->stage == 1) {
         if (done < p->seq) break;
         p->n_valid = *reinterpret_cast<volatile int32_t*>(&s->mb->n_valid[p->slot]);
         const int64_t B = p->b - p->a, n = std::min<int64_t>(p->n_valid, B);
-        // flags straight into the callers' buffers, rows into pinned staging
-        for (Req* r : p->reqs) {
+        for (Req* r : p->reqs) {  // flags straight into the callers' buffers
           const int64_t o = r->off, m = r->r.count;
           cudaMemcpyAsync(r->r.valid, s->valid + o, m, cudaMemcpyDeviceToHost, s->copy);
           cudaMemcpyAsync(r->r.lock_step, s->lock + o, m * 2, cudaMemcpyDeviceToHost, s->copy);
           if (r->r.min_disc) cudaMemcpyAsync(r->r.min_disc, s->md + o, m * 4, cudaMemcpyDeviceToHost, s->copy);
         }
-        if (n > 0) {
-          cudaMemcpyAsync(s->h_idx, s->idx + p->a, n * 4, cudaMemcpyDeviceToHost, s->copy);
-          cudaMemcpyAsync(s->h_path, s->path + p->a * s->T * 2, n * s->T * 8, cudaMemcpyDeviceToHost, s->copy);
-          if (s->traj)
-            cudaMemcpyAsync(s->h_traj, s->traj + p->a * s->n_max * s->T * 2, n * s->n_max * s->T * 8,
-                            cudaMemcpyDeviceToHost, s->copy);
-        }
+        if (n > 0) cudaMemcpyAsync(s->h_idx, s->idx + p->a, n * 4, cudaMemcpyDeviceToHost, s->copy);
         cudaEventRecord(p->d2h_done, s->copy);
         p->stage = 2;
         progressed = true;
       }
-      if (p->stage == 2 && cudaEventQuery(p->d2h_done) != cudaSuccess) break;
-      finish_pass(s, p);  // stage 2 with its copies done, or 3 (failed)
+      if (p->stage == 2) {
+        if (cudaEventQuery(p->d2h_done) != cudaSuccess) break;
+        copy_rows(s, p);
+        cudaEventRecord(p->d2h_done, s->copy);
+        p->stage = 3;
+        progressed = true;
+      }
+      if (p->stage == 3 && cudaEventQuery(p->d2h_done) != cudaSuccess) break;
+      finish_pass(s, p);  // stage 3 with its copies done, or 4 (failed)
       cudaEventDestroy(p->d2h_done);
       s->inflight.pop_front();
       delete p;
@@ -776,8 +784,6 @@ void serve_free(ServeState* s) {
   cudaFree(d.ctrs);
   cudaFree(d.scan);
   cudaFreeHost(s->h_idx);
-  cudaFreeHost(s->h_path);
-  cudaFreeHost(s->h_traj);
   cudaFreeHost(s->h_desc);
   cudaFreeHost(s->h_head);
   cudaFreeHost(s->h_ctl);
@@ -814,8 +820,6 @@ int links_serve_start(links_ctx ctx, size_t mem_budget_bytes, int max_pending, i
   const int64_t cap = (int64_t)(mem_budget_bytes / per);
   if (cap < 1) return set_error(LINKS_EINVAL, "links_serve_start: memory budget below one candidate");
   if (cap > INT32_MAX) return set_error(LINKS_EINVAL, "links_serve_start: memory budget above 2^31 candidates");
-  if (with_traj && (size_t)cap * n_max * T * 8 > ((size_t)8 << 30))
-    return set_error(LINKS_EINVAL, "links_serve_start: with_traj needs a budget whose trajectories fit 8 GiB of staging");
   ServeState* s = new (std::nothrow) ServeState();
   if (!s) return set_error(LINKS_ENOMEM, "links_serve_start: host allocation");
   s->priv.device = ctx->device;
@@ -861,8 +865,6 @@ int links_serve_start(links_ctx ctx, size_t mem_budget_bytes, int max_pending, i
   if (e == cudaSuccess) e = cudaMemset(s->priv.d_err, 0, 4);
   if (e == cudaSuccess) e = cudaMemset(s->ctl, 0, sizeof(LoopCtl));
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_idx, cap * 4, 0);
-  if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_path, cap * T * 8, 0);
-  if (e == cudaSuccess && with_traj) e = cudaHostAlloc((void**)&s->h_traj, cap * n_max * T * 8, 0);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_desc, sizeof(PassDesc) * kRing, 0);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_head, sizeof(unsigned long long) * kRing, 0);
   if (e == cudaSuccess) e = cudaHostAlloc((void**)&s->h_ctl, 2 * sizeof(unsigned long long), 0);
