@@ -276,19 +276,40 @@ def paper_topologies(K: int, n: int, seed: int = 0, *, ground_max: int = 3, p_gr
 
 
 def paper_batch(n_topologies: int, samples: int, n: int, seed: int = 0) -> MechBatch:
-    """The paper's own candidates (Sec. "Dataset Features & Statistics"): ``n_topologies`` topologies of
-    n joints meeting the topology rules (``paper_topologies``), each with ``samples``
-    random initial positions standardised as the paper does: the actuator's ground
-    joint at (0.5, 0.5), the actuator arm of length 0.05 and horizontal (actuated joint
-    at (0.55, 0.5)), every other joint uniform in the unit square.  Candidates are
-    topology-major."""
+    """The paper's own candidates (Sec. "Dataset Features & Statistics"; Sec. "Finding
+    Valid Initial Positions"): ``n_topologies`` topologies of n joints meeting the topology
+    rules (``paper_topologies``), each with ``samples`` random initial positions: every
+    joint drawn uniformly in the unit square (bounding-box rule), then standardised as
+    the paper's invariance rules say -- the mechanism translated so that the actuator's
+    ground joint is at (0.5, 0.5), rotated so that the actuator arm points along +x and
+    scaled so that it has length 0.05 (actuated joint at (0.55, 0.5)).  A draw whose
+    standardised joints leave the unit square is drawn again (up to 16 times; the last
+    draw is kept).  The standardisation is a similarity, so it leaves each candidate's
+    validity as drawn.  Candidates are topology-major."""
     t = paper_topologies(n_topologies, n, seed)
     rep = np.repeat(np.arange(n_topologies), samples)
-    pos = _positions(Stream(seed, 900 + _T_POS), rep.size, n, t.n_joints[rep], np.float64)
-    pos[:, 0] = (0.5, 0.5)
-    pos[:, 1] = (0.55, 0.5)
+    B = rep.size
+    out = np.zeros((B, n, 2))
+    todo = np.arange(B)
+    for attempt in range(16):
+        p = _positions(Stream(seed, 900 + _T_POS + 1000 * attempt), B, n, t.n_joints[rep], np.float64)[todo]
+        c = p[:, 1] - p[:, 0]
+        ln = np.hypot(c[:, 0], c[:, 1])
+        ln = np.where(ln > 0, ln, 1.0)
+        cs, sn = c[:, 0] / ln, c[:, 1] / ln
+        d = p - p[:, :1]
+        x = (cs[:, None] * d[..., 0] + sn[:, None] * d[..., 1]) * (0.05 / ln)[:, None]
+        y = (-sn[:, None] * d[..., 0] + cs[:, None] * d[..., 1]) * (0.05 / ln)[:, None]
+        q = np.stack([0.5 + x, 0.5 + y], -1)
+        out[todo] = q
+        inside = ((q >= 0) & (q <= 1)).all(axis=(1, 2))
+        todo = todo[~inside]
+        if todo.size == 0:
+            break
+    out[:, 0] = (0.5, 0.5)
+    out[:, 1] = (0.55, 0.5)
     return MechBatch(t.n_joints[rep].copy(), np.ascontiguousarray(t.adj[rep]), np.ascontiguousarray(t.jtype[rep]),
-                     pos.astype(np.float32))
+                     out.astype(np.float32))
 
 
 def _permute(batch: MechBatch, st: Stream) -> MechBatch:
