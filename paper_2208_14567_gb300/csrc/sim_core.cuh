@@ -16,6 +16,12 @@ constexpr int kBatch = 16;  // work items taken per atomic by a warp
 constexpr int kEmitSlotBytes = 400;
 constexpr int kEmitSlotBytesDW = 656;
 constexpr int kEmitSharedDWMaxSlots = 12;
+
+// Shared memory of one emit warp: the slot arrays and the row's dyad records (48 B per
+// dyad).
+__host__ __device__ constexpr size_t emit_warp_bytes(int n_max, int max_dyads, bool dws) {
+  return (size_t)n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes) + (size_t)max_dyads * 48;
+}
 // Two steps per lane save record loads but double the slot arrays in shared memory;
 // they pay for small mechanisms only (4 CTAs per SM still fit).
 constexpr int kScreenTwoStepMaxSlots = 9;
@@ -233,7 +239,7 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
       if (RESCUE && amb) {
         dwp loc[kMaxJ];
         float qd;
-        locked = dw_chain<false>(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), LocLocal{loc}, &qd);
+        locked = dw_chain(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), LocLocal{loc}, &qd);
         qstep[u] = qd;
       }
       const unsigned lb = __ballot_sync(kFull, locked) & gmask;
@@ -274,13 +280,14 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
 // certified FP32 chain of the screen (shared-memory slot arrays); if every joint's
 // forward error bound is within the tolerance (kEmitBudget of the bounding-box
 // diagonal, less the output rounding) the FP32 positions are written, otherwise that
-// lane recomputes the step in double-word arithmetic (absolute coordinates) and
-// writes those.
+// lane recomputes the step in double-word arithmetic relative to the pivot, as the
+// screen's rescue does (so a step the screen rescued gets the same operations on the
+// same values, and the same lock decision), and writes those.
 // Shared memory per warp and slot: FP32 positions (256 B), error bounds (128 B),
-// absolute fixed joints (16 B, one per warp) and, with DWS, the double-word y of the
-// lane's slot positions (256 B; x reuses the FP32 positions, the fixed slots stay in
-// the warp's copy).  Larger mechanisms keep the double-word slots thread-local, which
-// costs less occupancy.
+// double-word fixed joints (16 B, one per warp) and, with DWS, the double-word y of
+// the lane's slot positions (256 B; x reuses the FP32 positions, the fixed slots stay
+// in the warp's copy).  Larger mechanisms keep the double-word slots thread-local,
+// which costs less occupancy.
 // With CENSUS the kernel writes nothing and only counts what the emit does: steps
 // computed, and steps (and dyad-steps) whose FP32 bound sends them to double-word
 // (the same FP32 chain on the same inputs, so the same decisions).
@@ -292,11 +299,11 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
                                           int64_t nw) {
   const int ns = p.n_max;
   const int slot_bytes = DWS ? kEmitSlotBytesDW : kEmitSlotBytes;
-  char* const region = smem + (size_t)warp * (ns * slot_bytes + p.max_dyads * 48);
+  char* const region = smem + (size_t)warp * emit_warp_bytes(ns, p.max_dyads, DWS);
   float4* const Rw = reinterpret_cast<float4*>(region + ns * slot_bytes);  // the row's dyad records
   char* const Pb = region + lane * 8;
   char* const Eb = region + ns * 256 + lane * 4;
-  float4* const Fb = reinterpret_cast<float4*>(region + ns * 384);  // absolute fixed joints (warp)
+  float4* const Fb = reinterpret_cast<float4*>(region + ns * 384);  // double-word fixed joints (warp)
   char* const Yb = region + ns * 400 + lane * 8;                    // DWS: double-word y
   int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
   const float nanf_ = __int_as_float(0x7fc00000);
@@ -325,19 +332,15 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
     for (int x = lane; x < 3 * nd; x += 32)
       Rw[x] = ldro<NC>(reinterpret_cast<const float4*>(p.dyad + b * p.max_dyads) + x);
     __syncwarp();
-    // fixed joints: FP32 relative (the lane's column) and double-word absolute (one
-    // copy per warp)
+    // fixed joints relative to the pivot: FP32 (the lane's column) and double-word
+    // (one copy per warp)
     if (ok) {
-      const dw px = {h.px_h, h.px_l}, py = {h.py_h, h.py_l};
       const float4* fr = p.fixpos + b * ns;
       for (int s = 0; s < nf; ++s) {
         float4 f = ldro<NC>(fr + s);
         *reinterpret_cast<float2*>(Pb + s * 256) = make_float2(f.x, f.z);
         *reinterpret_cast<float*>(Eb + s * 128) = h.e_fixed;
-        if (lane == s) {
-          dw x = dw_add(px, dw{f.x, f.y}), y = dw_add(py, dw{f.z, f.w});
-          Fb[s] = make_float4(x.h, x.l, y.h, y.l);
-        }
+        if (lane == s) Fb[s] = f;
       }
     }
     __syncwarp();
@@ -347,7 +350,8 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
       if (t < lock) {
         const float4 csv = __ldg(cs + t);
         *reinterpret_cast<float2*>(Pb + nf * 256) =
-            make_float2(csv.x * h.ux_h - csv.z * h.uy_h, csv.z * h.ux_h + csv.x * h.uy_h);
+            make_float2(__fsub_rn(__fmul_rn(csv.x, h.ux_h), __fmul_rn(csv.z, h.uy_h)),
+                        __fadd_rn(__fmul_rn(csv.z, h.ux_h), __fmul_rn(csv.x, h.uy_h)));  // as the screen
         *reinterpret_cast<float*>(Eb + nf * 128) = h.e_motor;
         float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f, emax = 0.0f;
         for (int d = 0; d < nd; ++d) fp32_dyad<true>(rec + d, Pb, Eb, lockw, zmin, isgmax, &emax);
@@ -373,11 +377,13 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
             else return LocLocal{lbuf};
           }();
           float qd;
-          bool lk = dw_chain<true>(h, Fb, rec, csv, loc, &qd);
+          bool lk = dw_chain(h, Fb, rec, csv, loc, &qd);
           if (lk) atomicOr(err, kErrEmitLock);
           for (int s = 0; s < nslot; ++s) {
             const dwp ls = slot_pos(loc, Fb, nf, s);
-            float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(ls.x.h, ls.y.h);
+            // the absolute coordinate as the FP32 path forms it, from the high parts
+            // (the low parts are below the output rounding the tolerance reserves)
+            const float2 v = lk ? make_float2(nanf_, nanf_) : make_float2(ls.x.h + h.px_h, ls.y.h + h.py_h);
             if (trow) trow[jofs[s] + t] = v;
             if (prow && s == h.coupler_slot) prow[t] = v;
           }

@@ -198,8 +198,7 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
   const EmitShape sh = shape ? *shape : emit_shape(ctx, plan->d.n_max);
   const bool dws = sh.dws;
   auto kern = dws ? emit_kernel<CENSUS, true> : emit_kernel<CENSUS, false>;
-  const size_t smem = (size_t)kWarps * (plan->d.n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes) +
-                                        plan->d.max_dyads * 48);
+  const size_t smem = (size_t)kWarps * emit_warp_bytes(plan->d.n_max, plan->d.max_dyads, dws);
   if (smem > 48 * 1024)
     LINKS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;

@@ -71,13 +71,12 @@ __device__ __forceinline__ dwp slot_pos(const Loc& loc, const float4* fix, int n
   return loc.get(s);
 }
 
-// Double-word chain of one step into loc[slot].  fix holds the fixed slots as
-// (x_h, x_l, y_h, y_l); with ABS the positions are absolute (fix absolute, the
-// actuated joint offset by the pivot), otherwise relative to the pivot.
+// Double-word chain of one step into loc[slot], relative to the pivot.  fix holds the
+// fixed slots as (x_h, x_l, y_h, y_l).
 // Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
 // Inlined: as a call it cost the emit 12% (argument passing and saved registers
 // around it).
-template <bool ABS, class Loc>
+template <class Loc>
 __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, const DyadRec* __restrict__ dy,
                                          float4 csv, Loc loc, float* qmin) {
   const int nf = h.nf, nd = h.nd;
@@ -89,10 +88,6 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
   dw c = {csv.x, csv.y}, s = {csv.z, csv.w};
   dw ux = {h.ux_h, h.ux_l}, uy = {h.uy_h, h.uy_l};
   dwp m = {dw_sub(dw_mul(c, ux), dw_mul(s, uy)), dw_add(dw_mul(s, ux), dw_mul(c, uy))};
-  if (ABS) {
-    m.x = dw_add(m.x, dw{h.px_h, h.px_l});
-    m.y = dw_add(m.y, dw{h.py_h, h.py_l});
-  }
   loc.set(nf, m);
   float q = __int_as_float(0x7f800000);  // +inf
   for (int d = 0; d < nd; ++d) {

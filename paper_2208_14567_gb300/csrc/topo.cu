@@ -68,7 +68,7 @@ std::string topo_source_step(int nf, int nd, const std::vector<int>& sa, const s
        "      if (act && !certain_lock && !(zmin >= 0.0f)) {  // uncertain: double-word decides\n"
        "        links::dwp loc[" << nf + 1 + nd << "];\n"
        "        float qd;\n"
-       "        locked = links::dw_chain<false>(h, fixpos + (long long)b * n_max, dyad + (long long)b * max_dyads,\n"
+       "        locked = links::dw_chain(h, fixpos + (long long)b * n_max, dyad + (long long)b * max_dyads,\n"
        "                                        __ldg(cs + t), links::LocLocal{loc}, &qd);\n"
        "        q = qd;\n"
        "      }\n"

@@ -358,10 +358,11 @@ def test_two_stage_screen(L, case):
 @pytest.mark.parametrize("n", [6, 8, 10, 12, 15, 20])
 def test_paper_generator_matches_oracle(L, n):
     """Candidates of the paper's own generator (topologies by the J operator under the
-    paper's rules; ground pivot at (0.5, 0.5), horizontal actuator arm of 0.05, the other
-    joints uniform in the unit box): eight topologies x 300 position samples of n joints,
-    LINKS_MIXED FULL against the oracle -- flags outside the margin, positions within
-    1e-5 L at every step, min_disc as in the generic tests."""
+    paper's rules; joints uniform in the unit box, then standardised by a similarity to
+    the ground pivot at (0.5, 0.5) and a horizontal actuator arm of 0.05): eight
+    topologies x 300 position samples of n joints, LINKS_MIXED FULL against the oracle --
+    flags outside the margin, positions within 1e-5 L at every step, min_disc as in the
+    generic tests."""
     batch = I.paper_batch(8, 300, n, seed=500 + n)
     T = 200
     ref = O.simulate(batch, T)
@@ -372,6 +373,38 @@ def test_paper_generator_matches_oracle(L, n):
     ok = (ref.lock_step != 0) & (res["lock_step"] == ref.lock_step)
     dq = np.abs(res["min_disc"][ok] - ref.min_disc[ok])
     assert (dq <= 1e-4 + 1e-3 * ref.min_disc[ok]).all()
+
+
+@pytest.mark.parametrize("n", [6, 8, 12])
+def test_paper_topology_million_samples_emit_agrees_with_screen(L, n):
+    """One topology of the paper's generator with 1M standardised position samples,
+    VALID_ONLY rows: the emit's double-word chain never finds a lock on a step the
+    screen passed (the device error word stays clear, so the sync succeeds), and 1500
+    sampled valid rows match the oracle within 1e-5 L at every step."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.paper_batch(1, 1_000_000, n, seed=100 + n)
+    T = 200
+    with Simulator(batch.B, batch.nmax) as s:
+        s.build(to_device(batch))
+        o = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY)
+        s.sync()
+        nv = int(o.n_out[0])
+        assert nv > 0
+        rng = np.random.default_rng(n)
+        pick = np.sort(rng.choice(nv, size=min(nv, 1500), replace=False))
+        idx = o.out_index[:nv].cpu().numpy()[pick]
+        traj = o.traj[:nv].cpu().numpy()[pick]
+        path = o.path[:nv].cpu().numpy()[pick]
+    sub = batch.take(idx)
+    ref = O.simulate(sub, T)
+    assert (ref.valid == 1).sum() >= len(idx) - 2  # margin cases only
+    Ld = bbox_diag(sub.pos, sub.n_joints)
+    keep = ref.valid == 1
+    e = np.abs(traj[:, :n].astype(np.float64) - ref.traj[:, :n]).max((1, 2, 3)) / Ld
+    ep = np.abs(path.astype(np.float64) - ref.path).max((1, 2)) / Ld
+    worst = max(e[keep].max(), ep[keep].max())
+    assert worst <= TOL_MIXED, worst
+    print(f"[paper topology n={n} 1M] valid {nv} max position error / L {worst:.2e}")
 
 
 @pytest.mark.parametrize("T", [1, 7, 33, 64])
