@@ -282,7 +282,8 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
 // diagonal, less the output rounding) the FP32 positions are written, otherwise that
 // lane recomputes the step in double-word arithmetic relative to the pivot, as the
 // screen's rescue does (so a step the screen rescued gets the same operations on the
-// same values, and the same lock decision), and writes those.
+// same values, and the same lock decision), and writes those.  A row whose first 32
+// steps all needed double-word computes the rest in double-word directly.
 // Shared memory per warp and slot: FP32 positions (256 B), error bounds (128 B),
 // double-word fixed joints (16 B, one per warp) and, with DWS, the double-word y of
 // the lane's slot positions (256 B; x reuses the FP32 positions, the fixed slots stay
@@ -344,33 +345,37 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
       }
     }
     __syncwarp();
+    bool dw_only = false;  // warp-uniform: the row goes straight to double-word
     for (int t0 = 0; t0 < T; t0 += 32) {
       const int t = t0 + lane;
-      if (t >= T) continue;
-      if (t < lock) {
+      const bool act = t < T && t < lock;
+      bool certified = false;
+      if (act) {
         const float4 csv = __ldg(cs + t);
-        *reinterpret_cast<float2*>(Pb + nf * 256) =
-            make_float2(__fsub_rn(__fmul_rn(csv.x, h.ux_h), __fmul_rn(csv.z, h.uy_h)),
-                        __fadd_rn(__fmul_rn(csv.z, h.ux_h), __fmul_rn(csv.x, h.uy_h)));  // as the screen
-        *reinterpret_cast<float*>(Eb + nf * 128) = h.e_motor;
-        float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f, emax = 0.0f;
-        for (int d = 0; d < nd; ++d) fp32_dyad<true>(rec + d, Pb, Eb, lockw, zmin, isgmax, &emax);
-        if (CENSUS) {
-          ++n_steps;
-          if (!(emax <= tol && zmin >= 0.0f)) {
-            ++n_dw;
-            n_dw_dyads += nd;
+        if (!dw_only) {
+          *reinterpret_cast<float2*>(Pb + nf * 256) =
+              make_float2(__fsub_rn(__fmul_rn(csv.x, h.ux_h), __fmul_rn(csv.z, h.uy_h)),
+                          __fadd_rn(__fmul_rn(csv.z, h.ux_h), __fmul_rn(csv.x, h.uy_h)));  // as the screen
+          *reinterpret_cast<float*>(Eb + nf * 128) = h.e_motor;
+          float lockw = INFINITY, zmin = INFINITY, isgmax = 0.0f, emax = 0.0f;
+          for (int d = 0; d < nd; ++d) fp32_dyad<true>(rec + d, Pb, Eb, lockw, zmin, isgmax, &emax);
+          certified = emax <= tol && zmin >= 0.0f;
+          if (CENSUS) {
+            ++n_steps;
+            if (!certified) {
+              ++n_dw;
+              n_dw_dyads += nd;
+            }
+          } else if (certified) {
+            for (int s = 0; s < nslot; ++s) {
+              const float2 q = *reinterpret_cast<const float2*>(Pb + s * 256);
+              const float2 v = make_float2(q.x + h.px_h, q.y + h.py_h);
+              if (trow) trow[jofs[s] + t] = v;
+              if (prow && s == h.coupler_slot) prow[t] = v;
+            }
           }
-          continue;
         }
-        if (emax <= tol && zmin >= 0.0f) {
-          for (int s = 0; s < nslot; ++s) {
-            const float2 q = *reinterpret_cast<const float2*>(Pb + s * 256);
-            const float2 v = make_float2(q.x + h.px_h, q.y + h.py_h);
-            if (trow) trow[jofs[s] + t] = v;
-            if (prow && s == h.coupler_slot) prow[t] = v;
-          }
-        } else {
+        if (!CENSUS && !certified) {
           dwp lbuf[DWS ? 1 : kMaxJ];
           const auto loc = [&] {
             if constexpr (DWS) return LocShared{Pb, Yb};
@@ -388,14 +393,21 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
             if (prow && s == h.coupler_slot) prow[t] = v;
           }
         }
-      } else if (!CENSUS) {
+      } else if (!CENSUS && t < T) {
         for (int s = 0; s < n; ++s)
           if (trow) trow[(int64_t)sj[s] * T + t] = make_float2(nanf_, nanf_);
         if (prow) prow[t] = make_float2(nanf_, nanf_);
       }
-      if (!CENSUS)
+      if (!CENSUS && t < T)
         for (int j = n; j < ns; ++j)
           if (trow) trow[(int64_t)j * T + t] = make_float2(nanf_, nanf_);
+      if (!CENSUS && t0 == 0) {
+        // A row whose first pass needed double-word on every step (at least half a pass)
+        // skips the FP32 chain from then on: its bounds stay above the budget along the
+        // turn, as the census shows for deep chains.
+        const unsigned am = __ballot_sync(kFull, act), dm = __ballot_sync(kFull, act && !certified);
+        dw_only = dm == am && __popc(am) >= 16;
+      }
     }
   }
   if (CENSUS) {

@@ -21,6 +21,15 @@ __device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-p
   return r;
 }
 
+// Reciprocal square root with subnormal inputs flushed to zero (one MUFU operation; the
+// same approximation as rsqrtf on normal inputs).  A subnormal distance or discriminant
+// then gives an infinite bound or a NaN, which the screens treat as uncertain.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // One FP32 dyad in product form, D = (d + R12)(R12 - d)(d - Rm)(d + Rm), for parents
 // (pix, piy), (pjx, pjy) with bounds ei, ej and the record's r0 = {., R12, Rm, c},
 // r1 = {2 r1 r2, local error constant, ., .}: the joint (kx, ky), its forward error
@@ -35,11 +44,11 @@ __device__ __forceinline__ void fp32_dyad_core(float pix, float piy, float pjx, 
   const float R12 = r0.y, Rm = r0.z;
   const float dx = __fsub_rn(pjx, pix), dy = __fsub_rn(pjy, piy);
   const float d2 = __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
-  const float rd = rsqrtf(d2);
+  const float rd = rsqrt_ftz(d2);
   const float dd = __fmul_rn(d2, rd);
   const float s2 = __fsub_rn(R12, dd), s3 = __fsub_rn(dd, Rm);
   const float D = __fmul_rn(__fmul_rn(__fadd_rn(dd, R12), s2), __fmul_rn(s3, __fadd_rn(dd, Rm)));
-  const float rD = rsqrtf(D);
+  const float rD = rsqrt_ftz(D);
   const float isg = __fmul_rn(r1.x, rD);
   const float del = __fadd_rn(__fadd_rn(ei, ej), r1.y);
   lockw = min3(lockw, __fadd_rn(s2, del), __fadd_rn(s3, del));
