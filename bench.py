@@ -667,16 +667,17 @@ CONFIGS = {
                     "point), positions U[0,1]^2 float64, T=200, plain FP64 kernel, full trajectories + flags",
         "l2": "inputs 1 MB fit L2; a 256 MB buffer is written between timed steps"},
     2: {"name": "config2_1M_6-8", "kind": "dyad", "B": 1_000_000, "n_lo": 6, "n_hi": 8, "n_max": 8,
-        "joints": "6-8", "precision_name": "mixed", "out_name": "valid_only", "graph": False,
+        "joints": "6-8", "precision_name": "mixed", "out_name": "valid_packed", "graph": False, "packed": True,
         "workload": "1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U[0,1]^2 float32, T=200, "
-                    "mixed precision, valid-only trajectories + paths + flags",
+                    "mixed precision, valid-only trajectories (packed by joint count) + paths + flags",
         "l2": "inputs 140 MB per step exceed the 126 MB L2; no flush"},
     3: {"name": "config3_4M_6-20", "kind": "dyad", "B": 4 * 1024 * 1024, "n_lo": 6, "n_hi": 20, "n_max": 20,
-        "joints": "6-20", "precision_name": "mixed", "out_name": "valid_only", "graph": True,
+        "joints": "6-20", "precision_name": "mixed", "out_name": "valid_packed", "graph": True, "packed": True,
         "workload": "4M (4,194,304) dyad-built 1-DOF candidates, joint count uniform in 6..20 (n_max 20), 2-3 "
                     "ground, positions U[0,1]^2 float32, T=200, mixed precision; one CUDA-graph step of device "
                     "plan build + persistent certified screen (lanes per mechanism autotuned) + compaction + "
-                    "emit; valid-only trajectories + paths + flags; the plain FP64 kernel on the same inputs",
+                    "emit; valid-only trajectories (packed by joint count) + paths + flags; the plain FP64 kernel "
+                    "on the same inputs",
         "l2": "inputs 2.4 GB per step exceed the 126 MB L2; no flush"},
 }
 
@@ -723,8 +724,14 @@ def accuracy(cfg, batch, out, T, full_mode, seed=99, rows_sample=2000):
     else:
         mech = out.out_index[torch.from_numpy(rows).to(out.out_index.device)].cpu().numpy()
     ridx = torch.from_numpy(rows).to(out.valid.device)
-    traj = out.traj[ridx].double().cpu().numpy()
     sub = batch.take(mech)
+    if out.row_offset is not None:  # packed rows: gather each row's joints, NaN for the padding
+        offs = out.row_offset[ridx].cpu().numpy()
+        traj = np.full((len(rows), batch.nmax, T, 2), np.nan)
+        for i, (o, nj) in enumerate(zip(offs, sub.n_joints)):
+            traj[i, :nj] = out.traj[int(o):int(o) + int(nj)].double().cpu().numpy()
+    else:
+        traj = out.traj[ridx].double().cpu().numpy()
     rs = O.simulate(sub, T)
     live = (np.arange(batch.nmax)[None, :] < sub.n_joints[:, None])
     p = np.asarray(sub.pos, np.float64)
@@ -740,6 +747,28 @@ def accuracy(cfg, batch, out, T, full_mode, seed=99, rows_sample=2000):
             "pos_err_max_over_L": float(err.max()) if len(rows) else 0.0,
             "pos_err_p99_over_L": float(np.percentile(err, 99)) if len(rows) else 0.0,
             "oracle_seconds": time.perf_counter() - t0}
+
+
+def alloc_out(sim, T, prec, mode, packed, caps):
+    """Outputs of a valid-rows step: caps = (rows, joint rows) capacities."""
+    if packed:
+        return sim.alloc_packed(T, prec, out_capacity=caps[0], traj_capacity=caps[1])
+    return sim.alloc(T, prec, mode, out_capacity=caps[0])
+
+
+def simulate(sim, T, prec, mode, packed, out):
+    if packed:
+        sim.simulate_packed(T, prec, out=out)
+    else:
+        sim.simulate(T, prec, mode, out=out)
+
+
+def capture_step(sim, db, status, T, prec, mode, packed, out, L):
+    """One step (plan build + simulation) captured as a CUDA graph."""
+    L.links_capture_begin(sim.ctx)
+    sim.build(db, status)
+    simulate(sim, T, prec, mode, packed, out)
+    return L.links_capture_end(sim.ctx)
 
 
 def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
@@ -762,14 +791,18 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     fourbar = cfg["kind"] == "fourbar"
     prec = L.PLAIN_F64 if fourbar else L.MIXED
     mode = L.OUT_FULL if fourbar else L.OUT_VALID_ONLY
+    packed = cfg.get("packed", False)
     sim.build(db, status)
     lanes = None
+    caps = None
     if not fourbar:
         if cfg["graph"]:
             lanes = L.links_autotune(sim.ctx, sim.plan, T)
         probe = sim.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)
         sim.sync()
-        out = sim.alloc(T, prec, mode, out_capacity=int(probe.n_out[0]) + 4096)
+        joints = int((db.n_joints.long() * probe.valid[:B].long()).sum())
+        caps = (int(probe.n_out[0]) + 4096, joints + 4096 * nmax)
+        out = alloc_out(sim, T, prec, mode, packed, caps)
         del probe
     else:
         out = sim.alloc(T, prec, mode)
@@ -778,10 +811,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     if cfg["graph"]:
         L.links_prepare(sim.ctx, T)
         c0 = L.links_launch_count(sim.ctx)
-        L.links_capture_begin(sim.ctx)
-        sim.build(db, status)
-        sim.simulate(T, prec, mode, out=out)
-        graph = L.links_capture_end(sim.ctx)
+        graph = capture_step(sim, db, status, T, prec, mode, packed, out, L)
         per_step_launches = L.links_launch_count(sim.ctx) - c0
 
     def step():
@@ -789,7 +819,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
             L.links_graph_launch(sim.ctx, graph)
         else:
             sim.build(db, status)
-            sim.simulate(T, prec, mode, out=out)
+            simulate(sim, T, prec, mode, packed, out)
 
     for _ in range(warmup):
         step()
@@ -846,7 +876,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     prof_steps = 3
     for _ in range(prof_steps):
         sim.build(db, status)
-        sim.simulate(T, prec, mode, out=out)
+        simulate(sim, T, prec, mode, packed, out)
     prof = L.links_profile_read(sim.ctx)
     L.links_profile(sim.ctx, False)
     total = sum(v[0] for v in prof.values())
@@ -864,6 +894,32 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     if not fourbar:
         res["roofline"], res["roofline_views"] = roofline(kernels, batch, out, lock_np, dyad_steps, n_valid, T,
                                                           nmax, sim, L)
+    if packed:  # the same step with padded valid rows ([rows, n_max, T, 2], NaN padding)
+        pad = alloc_out(sim, T, prec, mode, False, caps)
+        pgraph = capture_step(sim, db, status, T, prec, mode, False, pad, L) if cfg["graph"] else None
+        for _ in range(2):
+            if pgraph is not None:
+                L.links_graph_launch(sim.ctx, pgraph)
+            else:
+                sim.build(db, status)
+                simulate(sim, T, prec, mode, False, pad)
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        for _ in range(steps):
+            if pgraph is not None:
+                L.links_graph_launch(sim.ctx, pgraph)
+            else:
+                sim.build(db, status)
+                simulate(sim, T, prec, mode, False, pad)
+        p1.record(stream)
+        torch.cuda.synchronize(dev)
+        pms = max_over_ranks(p0.elapsed_time(p1) / steps, world, dev)
+        res["valid_only_padded"] = {"ms_per_step": pms, "value": world * B * T / (pms * 1e-3),
+                                    "same_rows": bool(torch.equal(pad.out_index[:n_valid], out.out_index[:n_valid]))}
+        if pgraph is not None:
+            L.links_graph_free(pgraph)
+        del pad
+        torch.cuda.empty_cache()
 
     # the plain FP64 kernel on the same inputs (the comparator the metric names)
     if not fourbar:
@@ -888,7 +944,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     if rank == 0 and not args.no_accuracy:
         res["accuracy_vs_oracle"] = accuracy(cfg, batch, out, T, fourbar)
     return res, {"sim": sim, "db": db, "out": out, "status": status, "batch": batch, "graph": graph,
-                 "prec": prec, "mode": mode, "n_valid": n_valid}
+                 "prec": prec, "mode": mode, "n_valid": n_valid, "packed": packed, "caps": caps}
 
 
 def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L):
@@ -910,7 +966,7 @@ def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L):
         n_valid_joints = batch.n_joints[valid_np].astype(np.int64)
         emit_steps, emit_dyads = rows * T, T * int(nd_valid.sum())
         work = L.links_emit_census(sim.ctx, sim.plan, T, L.OUT_VALID_ONLY, out.lock_step, out.out_index,
-                                   out.traj.shape[0])
+                                   out.out_index.shape[0])
         method_ops = int(METHOD_STEP_OPS * emit_steps + METHOD_DYAD_OPS * emit_dyads)
         design_ops = int(SCREEN_STEP_OPS * emit_steps + SCREEN_DYAD_OPS * emit_dyads
                          + DW_STEP_OPS * work["double_word_steps"] + DW_DYAD_OPS * work["double_word_dyads"])
@@ -971,16 +1027,13 @@ def e2e_run(state, args, world, local, full):
     prec, mode = state["prec"], state["mode"]
     host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
                for a in (batch.n_joints, batch.adj, batch.jtype, batch.pos)]
+    packed = state["packed"]
     if "dbs" not in state:
         state["dbs"] = [state["db"], to_device(batch, dev)]
-        rows_cap = state["out"].traj.shape[0]
-        state["outs"] = [state["out"], sim.alloc(T, prec, mode, out_capacity=rows_cap)]
+        state["outs"] = [state["out"], alloc_out(sim, T, prec, mode, packed, state["caps"])]
         graphs = [state["graph"], None]
         if state["graph"] is not None:
-            L.links_capture_begin(sim.ctx)
-            sim.build(state["dbs"][1], state["status"])
-            sim.simulate(T, prec, mode, out=state["outs"][1])
-            graphs[1] = L.links_capture_end(sim.ctx)
+            graphs[1] = capture_step(sim, state["dbs"][1], state["status"], T, prec, mode, packed, state["outs"][1], L)
         state["graphs"] = graphs
     dbs, outs, graphs = state["dbs"], state["outs"], state["graphs"]
     dev_in = [[d.n_joints, d.adj, d.jtype, d.pos] for d in dbs]
@@ -988,13 +1041,16 @@ def e2e_run(state, args, world, local, full):
     uploaded = [torch.cuda.Event() for _ in range(2)]
     computed = [torch.cuda.Event() for _ in range(2)]
     drained = [torch.cuda.Event() for _ in range(2)]
-    rows_cap = outs[0].traj.shape[0]
+    rows_cap = outs[0].out_index.shape[0]
     hb_rows = min(rows_cap, state["n_valid"] + 4096)
+    hb_traj = outs[0].traj.shape[0] if packed else hb_rows  # joint rows when packed
     hbuf = [dict(valid=torch.empty(B, dtype=torch.uint8).pin_memory(),
                  lock=torch.empty(B, dtype=torch.int16).pin_memory(),
                  md=torch.empty(B, dtype=torch.float32).pin_memory(),
                  n=torch.empty(1, dtype=torch.int32).pin_memory(),
-                 traj=torch.empty((hb_rows,) + tuple(outs[0].traj.shape[1:]), dtype=torch.float32).pin_memory()
+                 tot=torch.empty(1, dtype=torch.int64).pin_memory(),
+                 offs=torch.empty(hb_rows + 1, dtype=torch.int64).pin_memory() if full and packed else None,
+                 traj=torch.empty((hb_traj,) + tuple(outs[0].traj.shape[1:]), dtype=torch.float32).pin_memory()
                  if full else None,
                  path=torch.empty((hb_rows,) + tuple(outs[0].path.shape[1:]), dtype=torch.float32).pin_memory(),
                  idx=torch.empty(hb_rows, dtype=torch.int32).pin_memory()) for _ in range(2)]
@@ -1011,13 +1067,24 @@ def e2e_run(state, args, world, local, full):
             hb["n"].copy_(o.n_out, non_blocking=True)
         copy_stream.synchronize()
         n = min(int(hb["n"][0]), hb_rows)
+        extra = 0
+        if full and packed:  # the joint rows of the n rows: their total, then the rows and offsets
+            with torch.cuda.stream(copy_stream):
+                hb["tot"].copy_(o.row_offset[n:n + 1], non_blocking=True)
+            copy_stream.synchronize()
+            tot = int(hb["tot"][0])
+            extra = 8 + tot * T * 8 + (n + 1) * 8
         with torch.cuda.stream(copy_stream):
-            if full:
+            if full and packed:
+                hb["traj"][:tot].copy_(o.traj[:tot], non_blocking=True)
+                hb["offs"][:n + 1].copy_(o.row_offset[:n + 1], non_blocking=True)
+            elif full:
                 hb["traj"][:n].copy_(o.traj[:n], non_blocking=True)
+                extra = n * nmax * T * 8
             hb["path"][:n].copy_(o.path[:n], non_blocking=True)
             hb["idx"][:n].copy_(o.out_index[:n], non_blocking=True)
             drained[j].record(copy_stream)
-        return B * 7 + 4 + n * (T * 8 + 4) + (n * nmax * T * 8 if full else 0)
+        return B * 7 + 4 + n * (T * 8 + 4) + extra
 
     def upload(i):
         j = i % 2
@@ -1042,7 +1109,7 @@ def e2e_run(state, args, world, local, full):
             L.links_graph_launch(sim.ctx, graphs[j])
         else:
             sim.build(dbs[j], state["status"])
-            sim.simulate(T, prec, mode, out=outs[j])
+            simulate(sim, T, prec, mode, packed, outs[j])
         computed[j].record(stream)
         if i + 1 < args.e2e_steps:
             upload(i + 1)
@@ -1147,6 +1214,7 @@ def main():
         "screen_lanes_autotuned": res["screen_lanes_autotuned"],
         "kernel_shapes_autotuned": res.get("tuning"),
         "plain_f64": res.get("plain_f64"),
+        "valid_only_padded": res.get("valid_only_padded"),
         "accuracy_vs_oracle": res.get("accuracy_vs_oracle"),
         "algorithmic_dyad_steps_per_step": res["algorithmic_dyad_steps_per_step"],
         "kernels": res["kernels"],
@@ -1179,7 +1247,8 @@ def main():
 
 def two_stage(state, args, local):
     """The paper's two-stage screen on the headline inputs: T/4 positions, then T for the
-    mechanisms valid on the coarse grid (same valid flags and rows)."""
+    mechanisms valid on the coarse grid (same valid flags and rows; padded valid rows, so
+    its time compares with the headline's valid_only_padded step)."""
     import torch
 
     from paper_2208_14567_gb300 import links as L
@@ -1187,7 +1256,7 @@ def two_stage(state, args, local):
     stream = torch.cuda.current_stream(dev)
     sim, db, out, T = state["sim"], state["db"], state["out"], args.T
     n_low = torch.zeros(1, dtype=torch.int32, device=dev)
-    out2 = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=out.traj.shape[0])
+    out2 = sim.alloc(T, L.MIXED, L.OUT_VALID_ONLY, out_capacity=out.out_index.shape[0])
     sim.build(db, state["status"])
     sim.simulate_two_stage(T, T // 4, out=out2, n_low_valid=n_low)
     sim.sync()

@@ -164,6 +164,23 @@ LINKS_API int links_simulate(links_ctx ctx, links_plan plan, int T, int precisio
                    void* traj, void* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
                    int32_t* out_index, int64_t out_capacity, int32_t* n_out);
 
+/* links_simulate in LINKS_OUT_VALID_ONLY mode with the rows' trajectories packed by
+ * joint count (no counterpart in the paper: the valid rows without their padding
+ * joints).  Row r (mechanism out_index[r], n_r joints) holds joint j < n_r at
+ * traj[(row_offset[r] + j) * T + t] (float32 pairs for LINKS_MIXED, float64 pairs for
+ * LINKS_PLAIN_F64; the values those of links_simulate's row r, joint j).
+ * row_offset [out_capacity + 1] int64 (device) receives the exclusive prefix of n_r
+ * over the rows and, at index rows = min(*n_out, out_capacity), their total.  traj
+ * (device, may be NULL) holds traj_capacity joint rows of T points; a row that does not
+ * fit entirely is not written (its path is).  path [out_capacity, T, 2], out_index,
+ * *n_out, valid, lock_step and min_disc as in links_simulate.  Nothing is written for
+ * joints >= n_r.  Asynchronous (graph-capturable).  LINKS_EINVAL for bad arguments
+ * (row_offset is required). */
+LINKS_API int links_simulate_packed(links_ctx ctx, links_plan plan, int T, int precision, void* traj,
+                                    int64_t traj_capacity, void* path, uint8_t* valid, int16_t* lock_step,
+                                    float* min_disc, int32_t* out_index, int64_t* row_offset,
+                                    int64_t out_capacity, int32_t* n_out);
+
 /* Two-stage screen (Sec. "Finding Valid Initial Positions", paragraph on low fidelity
  * evaluations): LINKS_MIXED simulation of every OK mechanism on the coarse grid of
  * T_low actuator positions, then on the full grid of T positions only for the

@@ -43,6 +43,7 @@ class SimOut:
     out_index: "object" = None
     n_out: "object" = None
     status: "object" = None
+    row_offset: "object" = None  # packed rows: joint offset of each row (int64 [rows + 1])
 
 
 class Simulator:
@@ -114,6 +115,33 @@ class Simulator:
                                                (out.path.shape[0] if out.path is not None else out.out_index.shape[0]))
         L.links_simulate(self.ctx, self.plan, T, precision, out_mode, out.traj, out.path, out.valid, out.lock_step,
                          out.min_disc, out.out_index, cap, out.n_out)
+        return out
+
+    def alloc_packed(self, T: int, precision: int = L.MIXED, out_capacity=None, traj_capacity=None,
+                     traj=True, path=True) -> SimOut:
+        """Outputs of simulate_packed: traj [traj_capacity, T, 2] (joint rows; by default
+        out_capacity * n_max, room for any rows), path [out_capacity, T, 2], out_index,
+        row_offset [out_capacity + 1] int64, n_out."""
+        import torch
+        o = self.alloc(T, precision, L.OUT_VALID_ONLY, traj=False, path=path, out_capacity=out_capacity)
+        rows = o.out_index.shape[0]
+        fdt = torch.float64 if precision == L.PLAIN_F64 else torch.float32
+        if traj:
+            tc = rows * self.n_max if traj_capacity is None else traj_capacity
+            o.traj = torch.empty((tc, T, 2), dtype=fdt, device=self.device)
+        o.row_offset = torch.empty(rows + 1, dtype=torch.int64, device=self.device)
+        return o
+
+    def simulate_packed(self, T: int, precision: int = L.MIXED, out: SimOut | None = None, traj=True, path=True,
+                        out_capacity=None, traj_capacity=None) -> SimOut:
+        """Valid rows with the trajectories packed by joint count (links_simulate_packed):
+        row r's joint j at out.traj[out.row_offset[r] + j]."""
+        if out is None:
+            out = self.alloc_packed(T, precision, out_capacity, traj_capacity, traj, path)
+        cap = out.row_offset.shape[0] - 1
+        tc = 0 if out.traj is None else out.traj.shape[0]
+        L.links_simulate_packed(self.ctx, self.plan, T, precision, out.traj, tc, out.path, out.valid, out.lock_step,
+                                out.min_disc, out.out_index, out.row_offset, cap, out.n_out)
         return out
 
     def simulate_topology(self, topo, T: int, out_mode: int = L.OUT_FULL, out: SimOut | None = None, traj=True,

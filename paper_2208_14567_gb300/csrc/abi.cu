@@ -234,6 +234,7 @@ int links_plan_create(links_ctx ctx, int64_t capacity, int n_max, links_plan* ou
   alloc((void**)&d.rescue, sizeof(int32_t) * c);
   alloc((void**)&d.ctrs, sizeof(int32_t) * kCtrs);
   alloc((void**)&d.scan, sizeof(int32_t) * (c / 1024 + 2));
+  alloc((void**)&d.scan64, sizeof(int64_t) * (c / 1024 + 2));
   if (e == cudaSuccess) e = cudaMemset(d.ctrs, 0, sizeof(int32_t) * kCtrs);
   if (e != cudaSuccess) {
     links_plan_free(p);
@@ -256,6 +257,7 @@ int links_plan_free(links_plan plan) {
   cudaFree(d.rescue);
   cudaFree(d.ctrs);
   cudaFree(d.scan);
+  cudaFree(d.scan64);
   delete plan;
   return LINKS_OK;
 }
@@ -373,6 +375,31 @@ int links_simulate(links_ctx ctx, links_plan plan, int T, int precision, int out
                         out_index, out_capacity, n_out);
   return simulate_mixed(ctx, plan, tab, out_mode, (float*)traj, (float*)path, valid, lock_step, min_disc,
                         out_index, out_capacity, n_out);
+}
+
+int links_simulate_packed(links_ctx ctx, links_plan plan, int T, int precision, void* traj, int64_t traj_capacity,
+                          void* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
+                          int64_t* row_offset, int64_t out_capacity, int32_t* n_out) {
+  if (!ctx || !plan) return set_error(LINKS_EINVAL, "links_simulate_packed: NULL ctx or plan");
+  if (plan->ctx != ctx) return set_error(LINKS_EINVAL, "links_simulate_packed: plan belongs to another context");
+  if (T < 1 || T > LINKS_MAX_T) return set_error(LINKS_EINVAL, "links_simulate_packed: T out of [1, 32767]");
+  if (precision != LINKS_PLAIN_F64 && precision != LINKS_MIXED)
+    return set_error(LINKS_EINVAL, "links_simulate_packed: unknown precision");
+  if (plan->B > 0 && (!valid || !lock_step || !min_disc))
+    return set_error(LINKS_EINVAL, "links_simulate_packed: valid, lock_step and min_disc are required");
+  if (out_capacity < 0 || traj_capacity < 0)
+    return set_error(LINKS_EINVAL, "links_simulate_packed: negative capacity");
+  if (!row_offset) return set_error(LINKS_EINVAL, "links_simulate_packed: row_offset is required");
+  if (out_capacity > 0 && !out_index) return set_error(LINKS_EINVAL, "links_simulate_packed: rows need out_index");
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  int st = LINKS_OK;
+  const TTable* tab = get_table(ctx, T, &st);
+  if (!tab) return st;
+  if (precision == LINKS_PLAIN_F64)
+    return simulate_f64(ctx, plan, tab, LINKS_OUT_VALID_ONLY, (double*)traj, (double*)path, valid, lock_step,
+                        min_disc, out_index, out_capacity, n_out, row_offset, traj_capacity);
+  return simulate_mixed(ctx, plan, tab, LINKS_OUT_VALID_ONLY, (float*)traj, (float*)path, valid, lock_step,
+                        min_disc, out_index, out_capacity, n_out, row_offset, traj_capacity);
 }
 
 int links_simulate_two_stage(links_ctx ctx, links_plan plan, int T, int T_low, float* traj, float* path,

@@ -49,6 +49,7 @@ struct PlanDev {
   int32_t* rescue;       // [cap]          mechanisms the screen left to its double-word pass
   int32_t* ctrs;         // [kCtrs]        histogram / cursors / work counters
   int32_t* scan;         // [cap/1024 + 2] block sums of the valid-row scan
+  int64_t* scan64;       // [cap/1024 + 2] block sums of the packed rows' joint offsets
   int32_t* row_of;       // [cap]          output row of each mechanism (VALID_ONLY), or -1
   int n_max;
   int max_dyads;
@@ -178,9 +179,12 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
 int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                     const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
                     int32_t* status_out);
+// row_offset (device [out_capacity + 1], VALID_ONLY only): packed rows, see
+// links_simulate_packed; traj_capacity in joint rows of T points.
 int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, double* traj,
                  double* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
-                 int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+                 int32_t* out_index, int64_t out_capacity, int32_t* n_out, int64_t* row_offset = nullptr,
+                 int64_t traj_capacity = 0);
 int simulate_two_stage(links_ctx ctx, links_plan plan, const TTable* tab_lo, const TTable* tab, float* traj,
                        float* path, uint8_t* valid, int16_t* lock_step, float* min_disc, int32_t* out_index,
                        int64_t out_capacity, int32_t* n_out, int32_t* n_low_valid);
@@ -188,7 +192,8 @@ int emit_census(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode,
                 const int32_t* out_index, int64_t out_capacity, int64_t* out);
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
-                   int32_t* out_index, int64_t out_capacity, int32_t* n_out);
+                   int32_t* out_index, int64_t out_capacity, int32_t* n_out, int64_t* row_offset = nullptr,
+                   int64_t traj_capacity = 0);
 // The kernel shapes for plans of n_max joints (defaults where none were set).
 Tuning tuning_of(links_ctx ctx, int n_max);
 // Times the screen's and the emit's shapes on the built plan and keeps the fastest for
@@ -206,6 +211,10 @@ int plan_one_host(int n, int n_max, const uint8_t* adj, const int8_t* type, cons
                   DyadRec* dyad);
 int compact_valid(links_ctx ctx, links_plan plan, const uint8_t* valid, int32_t* out_index,
                   int64_t out_capacity, int32_t* n_out);
+// Joint offsets of the packed valid rows (after compact_valid): row_offset[r] = sum of
+// the joint counts of rows < r, row_offset[rows] = the total.
+int pack_offsets(links_ctx ctx, links_plan plan, const int32_t* out_index, int64_t out_capacity,
+                 int64_t* row_offset);
 int fill_unsimulated(links_ctx ctx, links_plan plan, uint8_t* valid, int16_t* lock_step,
                      float* min_disc);
 

@@ -297,7 +297,8 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
                                           const int16_t* __restrict__ lock_step, const int32_t* __restrict__ out_index,
                                           int64_t out_capacity, float* __restrict__ traj, float* __restrict__ path,
                                           int32_t* err, char* smem, int* jofs, int warp, int lane, int64_t gw,
-                                          int64_t nw) {
+                                          int64_t nw, const int64_t* __restrict__ row_off = nullptr,
+                                          int64_t traj_cap = 0) {
   const int ns = p.n_max;
   const int slot_bytes = DWS ? kEmitSlotBytesDW : kEmitSlotBytes;
   char* const region = smem + (size_t)warp * emit_warp_bytes(ns, p.max_dyads, DWS);
@@ -323,7 +324,11 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
     if (full) lock = ok ? (lock_step[b] < 0 ? T : lock_step[b]) : 0;
     const uint8_t* sj = p.slot_joint + b * kMaxJ;
     const DyadRec* const rec = reinterpret_cast<const DyadRec*>(Rw);
-    float2* trow = traj ? reinterpret_cast<float2*>(traj) + r * ns * T : nullptr;
+    float2* trow = nullptr;  // packed rows (row_off): the row's own joints only
+    if (traj) {
+      if (!row_off) trow = reinterpret_cast<float2*>(traj) + r * ns * T;
+      else if (row_off[r] >= 0 && row_off[r] + n <= traj_cap) trow = reinterpret_cast<float2*>(traj) + row_off[r] * T;
+    }
     float2* prow = path ? reinterpret_cast<float2*>(path) + r * T : nullptr;
     // FP32 tolerance: the budget minus the rounding of the absolute output coordinates
     const float tol = fmaf(-2.0f * kU, fabsf(h.px_h) + fabsf(h.py_h) + h.bmax, kEmitBudget * h.lbox);
@@ -398,7 +403,7 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
           if (trow) trow[(int64_t)sj[s] * T + t] = make_float2(nanf_, nanf_);
         if (prow) prow[t] = make_float2(nanf_, nanf_);
       }
-      if (!CENSUS && t < T)
+      if (!CENSUS && t < T && !row_off)
         for (int j = n; j < ns; ++j)
           if (trow) trow[(int64_t)j * T + t] = make_float2(nanf_, nanf_);
       if (!CENSUS && t0 == 0) {

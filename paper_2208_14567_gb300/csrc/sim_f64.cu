@@ -26,12 +26,15 @@ __device__ __forceinline__ double2 nan2() {
 // mode 0: flags (+ FULL traj/path rows = mechanism index) for all B mechanisms
 // mode 1: flags only
 // mode 2: rows of valid mechanisms (out_index), traj/path only
+// mode 2 with row_off: packed rows, row r's joints at traj rows row_off[r] + j (the
+// row is left out when it does not fit in traj_cap joint rows), no padding joints
 __global__ void __launch_bounds__(kBlock) f64_kernel(PlanDev p, int64_t B, int T, const double2* __restrict__ cs,
                                                      int mode, double* __restrict__ traj, double* __restrict__ path,
                                                      uint8_t* __restrict__ valid, int16_t* __restrict__ lock_step,
                                                      float* __restrict__ min_disc,
                                                      const int32_t* __restrict__ out_index, int64_t out_capacity,
-                                                     int32_t* err) {
+                                                     int32_t* err, const int64_t* __restrict__ row_off,
+                                                     int64_t traj_cap) {
   const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t rows = mode == 2 ? min((int64_t)p.ctrs[kNValid], out_capacity) : B;
   if (r >= rows) return;
@@ -43,7 +46,11 @@ __global__ void __launch_bounds__(kBlock) f64_kernel(PlanDev p, int64_t B, int T
   const int ns = p.n_max;
   const MechHdr h = p.hdr[b];
   const bool write = mode != 1 && (traj || path);
-  double2* trow = traj ? reinterpret_cast<double2*>(traj) + r * ns * T : nullptr;
+  double2* trow = nullptr;
+  if (traj) {
+    if (!row_off) trow = reinterpret_cast<double2*>(traj) + r * ns * T;
+    else if (row_off[r] >= 0 && row_off[r] + h.n <= traj_cap) trow = reinterpret_cast<double2*>(traj) + row_off[r] * T;
+  }
   double2* prow = path ? reinterpret_cast<double2*>(path) + r * T : nullptr;
   if (h.status != LINKS_MECH_OK) {  // only reached in mode 0
     if (write) {
@@ -72,7 +79,7 @@ __global__ void __launch_bounds__(kBlock) f64_kernel(PlanDev p, int64_t B, int T
   }
   const double2 pv = p0[h.pad0];
   const double ux = p0[nf].x - pv.x, uy = p0[nf].y - pv.y;
-  if (write && trow)
+  if (write && trow && !row_off)
     for (int j = n; j < ns; ++j)
       for (int t = 0; t < T; ++t) trow[(int64_t)j * T + t] = nan2();
   int lock = -1;
@@ -192,6 +199,47 @@ __global__ void __launch_bounds__(kScanBlock) scan_write(int64_t B, const uint8_
   if (v && ex < cap && out_index) out_index[ex] = (int32_t)b;
 }
 
+// Packed rows: the exclusive prefix of the rows' joint counts, in the same three passes
+// over blocks of 1024 rows (rows = min(valid count, capacity), known on the device).
+__device__ __forceinline__ int row_joints(const PlanDev& p, int64_t B, const int32_t* out_index, int64_t r,
+                                          int64_t rows) {
+  if (r >= rows) return 0;
+  const int64_t b = out_index[r];
+  return b >= 0 && b < B ? (int)p.hdr[b].n : 0;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pack_count(PlanDev p, int64_t B, const int32_t* out_index,
+                                                         int64_t cap, int64_t* sums) {
+  const int64_t rows = min((int64_t)p.ctrs[kNValid], cap);
+  const int v = row_joints(p, B, out_index, (int64_t)blockIdx.x * kScanBlock + threadIdx.x, rows);
+  int tot;
+  block_excl_scan(v, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pack_top(PlanDev p, int nblk, int64_t cap, int64_t* sums,
+                                                       int64_t* row_offset) {
+  int64_t carry = 0;
+  for (int base = 0; base < nblk; base += kScanBlock) {  // a round sums <= 1024 * 32 * 1024 joints
+    const int i = base + threadIdx.x;
+    const int v = i < nblk ? (int)sums[i] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, &tot);
+    if (i < nblk) sums[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) row_offset[min((int64_t)p.ctrs[kNValid], cap)] = carry;
+}
+
+__global__ void __launch_bounds__(kScanBlock) pack_write(PlanDev p, int64_t B, const int32_t* out_index,
+                                                         int64_t cap, const int64_t* sums, int64_t* row_offset) {
+  const int64_t rows = min((int64_t)p.ctrs[kNValid], cap);
+  const int64_t r = (int64_t)blockIdx.x * kScanBlock + threadIdx.x;
+  const int v = row_joints(p, B, out_index, r, rows);
+  const int ex = block_excl_scan(v, nullptr);
+  if (r < rows) row_offset[r] = sums[blockIdx.x] + ex;
+}
+
 }  // namespace
 
 int fill_unsimulated(links_ctx ctx, links_plan plan, uint8_t* valid, int16_t* lock_step, float* min_disc) {
@@ -225,9 +273,34 @@ int compact_valid(links_ctx ctx, links_plan plan, const uint8_t* valid, int32_t*
   return LINKS_OK;
 }
 
+int pack_offsets(links_ctx ctx, links_plan plan, const int32_t* out_index, int64_t out_capacity,
+                 int64_t* row_offset) {
+  const int64_t B = plan->B;
+  const int64_t rmax = std::min<int64_t>(B, out_capacity);
+  const int nblk = (int)((rmax + kScanBlock - 1) / kScanBlock);
+  if (nblk > 0) {
+    KernelScope ks(ctx, "pack_count");
+    pack_count<<<nblk, kScanBlock, 0, ctx->stream>>>(plan->d, B, out_index, out_capacity, plan->d.scan64);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  {
+    KernelScope ks(ctx, "pack_top");
+    pack_top<<<1, kScanBlock, 0, ctx->stream>>>(plan->d, nblk, out_capacity, plan->d.scan64, row_offset);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  if (nblk > 0) {
+    KernelScope ks(ctx, "pack_write");
+    pack_write<<<nblk, kScanBlock, 0, ctx->stream>>>(plan->d, B, out_index, out_capacity, plan->d.scan64,
+                                                     row_offset);
+  }
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
+}
+
 int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, double* traj,
                  double* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
-                 int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
+                 int32_t* out_index, int64_t out_capacity, int32_t* n_out, int64_t* row_offset,
+                 int64_t traj_capacity) {
   const int64_t B = plan->B;
   const int T = tab->T;
   const bool full = out_mode == LINKS_OUT_FULL;
@@ -236,19 +309,24 @@ int simulate_f64(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode
   if (B > 0) {
     KernelScope ks(ctx, "f64_sim");
     f64_kernel<<<(unsigned)((B + kBlock - 1) / kBlock), kBlock, 0, ctx->stream>>>(
-        plan->d, B, T, tab->cs64, full ? 0 : 1, traj, path, valid, lock_step, min_disc, nullptr, 0, ctx->d_err);
+        plan->d, B, T, tab->cs64, full ? 0 : 1, traj, path, valid, lock_step, min_disc, nullptr, 0, ctx->d_err,
+        nullptr, 0);
     LINKS_CUDA(cudaGetLastError());
   }
   if (!full) {
     int st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
     if (st) return st;
+    if (row_offset) {
+      st = pack_offsets(ctx, plan, out_index, out_capacity, row_offset);
+      if (st) return st;
+    }
     if ((traj || path) && out_capacity > 0) {
       int64_t rows = std::min<int64_t>(B, out_capacity);
       if (rows > 0) {
         KernelScope ks(ctx, "f64_emit");
         f64_kernel<<<(unsigned)((rows + kBlock - 1) / kBlock), kBlock, 0, ctx->stream>>>(
             plan->d, B, T, tab->cs64, 2, traj, path, valid, lock_step, min_disc, out_index, out_capacity,
-            ctx->d_err);
+            ctx->d_err, row_offset, traj_capacity);
         LINKS_CUDA(cudaGetLastError());
       }
     }

@@ -46,14 +46,15 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
                                                       int full, const int16_t* __restrict__ lock_step,
                                                       const int32_t* __restrict__ out_index,
                                                       int64_t out_capacity, float* __restrict__ traj,
-                                                      float* __restrict__ path, int32_t* err) {
+                                                      float* __restrict__ path, int32_t* err,
+                                                      const int64_t* __restrict__ row_off, int64_t traj_cap) {
   extern __shared__ float4 smem4[];
   __shared__ int s_jofs[kWarps][kMaxJ];  // per warp: offset of each slot's joint row in the output row
   const int warp = threadIdx.x >> 5;
   emit_body<CENSUS, DWS>(p, B, T, cs, full, lock_step, out_index, out_capacity, traj, path, err,
                          reinterpret_cast<char*>(smem4), s_jofs[warp], warp, threadIdx.x & 31,
                          ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                         ((int64_t)gridDim.x * blockDim.x) >> 5);
+                         ((int64_t)gridDim.x * blockDim.x) >> 5, row_off, traj_cap);
 }
 
 // Shapes of the screen: lanes per mechanism G, steps per lane S, CTAs per SM (0 = as many
@@ -194,7 +195,7 @@ EmitShape emit_shape(links_ctx ctx, int n_max) {
 template <bool CENSUS>
 int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, const int16_t* lock_step,
                 const int32_t* out_index, int64_t out_capacity, float* traj, float* path, const char* name,
-                const EmitShape* shape = nullptr) {
+                const EmitShape* shape = nullptr, const int64_t* row_off = nullptr, int64_t traj_cap = 0) {
   const EmitShape sh = shape ? *shape : emit_shape(ctx, plan->d.n_max);
   const bool dws = sh.dws;
   auto kern = dws ? emit_kernel<CENSUS, true> : emit_kernel<CENSUS, false>;
@@ -208,7 +209,7 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
   KernelScope ks(ctx, name);
   kern<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, plan->B, tab->T, tab->cs, full ? 1 : 0,
                                                             lock_step, out_index, out_capacity, traj, path,
-                                                            ctx->d_err);
+                                                            ctx->d_err, row_off, traj_cap);
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
 }
@@ -324,7 +325,8 @@ Tuning tuning_of(links_ctx ctx, int n_max) {
 
 int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mode, float* traj,
                    float* path, uint8_t* valid, int16_t* lock_step, float* min_disc,
-                   int32_t* out_index, int64_t out_capacity, int32_t* n_out) {
+                   int32_t* out_index, int64_t out_capacity, int32_t* n_out, int64_t* row_offset,
+                   int64_t traj_capacity) {
   const int T = tab->T;
   int st = fill_unsimulated(ctx, plan, valid, lock_step, min_disc);
   if (st) return st;
@@ -334,9 +336,14 @@ int simulate_mixed(links_ctx ctx, links_plan plan, const TTable* tab, int out_mo
   if (!full) {
     st = compact_valid(ctx, plan, valid, out_index, out_capacity, n_out);
     if (st) return st;
+    if (row_offset) {
+      st = pack_offsets(ctx, plan, out_index, out_capacity, row_offset);
+      if (st) return st;
+    }
   }
   if (traj || path)
-    return launch_emit<false>(ctx, plan, tab, full, lock_step, out_index, out_capacity, traj, path, "mixed_emit");
+    return launch_emit<false>(ctx, plan, tab, full, lock_step, out_index, out_capacity, traj, path, "mixed_emit",
+                              nullptr, full ? nullptr : row_offset, traj_capacity);
   return LINKS_OK;
 }
 

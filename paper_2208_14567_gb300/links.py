@@ -70,6 +70,7 @@ def lib():
             "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
             "links_emit_census": ([P, P, i32, i32, P, P, i64, P], i32),
             "links_simulate_two_stage": ([P, P, i32, i32, P, P, P, P, P, P, i64, P, P], i32),
+            "links_simulate_packed": ([P, P, i32, i32, P, i64, P, P, P, P, P, P, i64, P], i32),
             "links_normalize": ([P, i64, i32, P, P], i32),
             "links_normalize_maxline": ([P, i64, i32, P, P, P, P], i32),
             "links_chamfer_topk": ([P, i32, i64, i32, P, P, i32, P, P], i32),
@@ -248,6 +249,19 @@ def links_simulate(ctx, plan, T: int, precision: int, out_mode: int, traj, path,
                                 _dev(lock_step, torch.int16, "lock_step"), _dev(min_disc, torch.float32, "min_disc"),
                                 _dev(out_index, torch.int32, "out_index"), int(out_capacity),
                                 _dev(n_out, torch.int32, "n_out")), "links_simulate")
+
+
+def links_simulate_packed(ctx, plan, T: int, precision: int, traj, traj_capacity: int, path, valid, lock_step,
+                          min_disc, out_index, row_offset, out_capacity: int, n_out=None):
+    import torch
+    fdt = torch.float64 if precision == PLAIN_F64 else torch.float32
+    _check(lib().links_simulate_packed(ctx, plan, int(T), int(precision), _dev(traj, fdt, "traj"), int(traj_capacity),
+                                       _dev(path, fdt, "path"), _dev(valid, torch.uint8, "valid"),
+                                       _dev(lock_step, torch.int16, "lock_step"),
+                                       _dev(min_disc, torch.float32, "min_disc"),
+                                       _dev(out_index, torch.int32, "out_index"),
+                                       _dev(row_offset, torch.int64, "row_offset"), int(out_capacity),
+                                       _dev(n_out, torch.int32, "n_out")), "links_simulate_packed")
 
 
 def links_topo_create(ctx, n: int, adj, jtype, lanes: int = 0):

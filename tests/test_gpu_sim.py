@@ -407,6 +407,74 @@ def test_paper_topology_million_samples_emit_agrees_with_screen(L, n):
     print(f"[paper topology n={n} 1M] valid {nv} max position error / L {worst:.2e}")
 
 
+@pytest.mark.parametrize("precision", ["mixed", "f64"])
+def test_packed_rows_equal_valid_only_rows(L, precision):
+    """links_simulate_packed against LINKS_OUT_VALID_ONLY on the same plan: the same
+    rows, n_out, out_index and paths; each packed row's n joints bit-identical to the
+    padded row's first n joints, at joint offsets equal to the prefix sums of n with the
+    total at row_offset[rows]; nothing written past the rows' joints."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.dyad_batch(6000, 6, 12, seed=31)
+    T = 77
+    prec = L.MIXED if precision == "mixed" else L.PLAIN_F64
+    with Simulator(batch.B, batch.nmax) as s:
+        s.build(to_device(batch))
+        a = s.simulate(T, prec, L.OUT_VALID_ONLY)
+        p = s.alloc_packed(T, prec)
+        p.traj.fill_(123.0)
+        s.simulate_packed(T, prec, out=p)
+        s.sync()
+        n = int(a.n_out[0])
+        assert int(p.n_out[0]) == n and n > 0
+        idx = a.out_index[:n].cpu().numpy()
+        assert np.array_equal(p.out_index[:n].cpu().numpy(), idx)
+        assert np.array_equal(p.path[:n].cpu().numpy(), a.path[:n].cpu().numpy(), equal_nan=True)
+        for k in ("valid", "lock_step", "min_disc"):
+            assert np.array_equal(getattr(p, k).cpu().numpy(), getattr(a, k).cpu().numpy(), equal_nan=True), k
+        nj = batch.n_joints[idx].astype(np.int64)
+        offs = np.concatenate([[0], np.cumsum(nj)])
+        assert np.array_equal(p.row_offset[:n + 1].cpu().numpy(), offs)
+        tp, ta = p.traj.cpu().numpy(), a.traj[:n].cpu().numpy()
+    want = np.concatenate([ta[r, :nj[r]] for r in range(n)])
+    assert np.array_equal(tp[:offs[n]], want)
+    assert (tp[offs[n]:] == 123.0).all()
+    print(f"[packed {precision}] rows {n} joint rows {offs[n]} of {n * batch.nmax} padded")
+
+
+def test_packed_rows_capacities(L):
+    """Row capacity below the valid count (rows = out_capacity, the total over those rows)
+    and a trajectory capacity that ends inside a row: rows that fit entirely are written,
+    the others keep the sentinel, and every row's path is written."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = I.dyad_batch(5000, 6, 8, seed=32)
+    T = 40
+    with Simulator(batch.B, batch.nmax) as s:
+        s.build(to_device(batch))
+        a = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY)
+        s.sync()
+        nv = int(a.n_out[0])
+        cap = nv // 2
+        idx = a.out_index[:cap].cpu().numpy()
+        nj = batch.n_joints[idx].astype(np.int64)
+        offs = np.concatenate([[0], np.cumsum(nj)])
+        k = cap // 3
+        tcap = int(offs[k]) + 1  # ends inside row k
+        p = s.alloc_packed(T, L.MIXED, out_capacity=cap, traj_capacity=tcap)
+        p.traj.fill_(123.0)
+        s.simulate_packed(T, L.MIXED, out=p)
+        s.sync()
+        assert int(p.n_out[0]) == nv
+        assert np.array_equal(p.row_offset.cpu().numpy(), offs)
+        tp, ta = p.traj.cpu().numpy(), a.traj[:cap].cpu().numpy()
+        assert np.array_equal(p.path.cpu().numpy(), a.path[:cap].cpu().numpy(), equal_nan=True)
+    want = np.concatenate([ta[r, :nj[r]] for r in range(k)])
+    assert np.array_equal(tp[:offs[k]], want)
+    assert (tp[offs[k]:] == 123.0).all()
+    with Simulator(4, 8) as s:
+        with pytest.raises(L.LinksError):
+            L.links_simulate_packed(s.ctx, s.plan, T, L.MIXED, None, 0, None, None, None, None, None, None, 0)
+
+
 @pytest.mark.parametrize("T", [1, 7, 33, 64])
 def test_ragged_steps_and_statuses(L, T):
     batch = planted_bad(I.dyad_batch(700, 6, 12, seed=6, permute=True))
