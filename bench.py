@@ -613,6 +613,62 @@ def serve_stage(args, local, stream):
             "budget_GiB": args.serve_budget, "loop_stats": stats}
 
 
+def profile_kernels(args):
+    """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
+    (no timing): plan build, screen and emit (packed valid rows) of args.batch dyad-built
+    candidates of 6 to args.profile_nmax joints, with the kernel shapes the autotuner
+    picks on the full configuration of that n_max (set explicitly, so no tuning launches
+    come first); then, for n_max 8, max-line normalisation of their valid coupler paths,
+    curation of their trajectories, a first-3 scan of 16 queries over those paths, and
+    the generic screen and the screen compiled for one topology of the paper's generator
+    on args.batch samples."""
+    import torch
+
+    from paper_2208_14567_gb300 import inputs as I
+    from paper_2208_14567_gb300 import links as L
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    T, B, nm = args.T, args.batch, args.profile_nmax
+    dev = torch.device("cuda", 0)
+    batch = I.dyad_batch(B, 6, nm, seed=0, nmax=nm)
+    db = to_device(batch, dev)
+    shapes = {20: {"screen_lanes": 16, "screen_steps": 1, "screen_defer": 1}}.get(nm, {})
+    with Simulator(B, nm) as s:
+        for k, v in shapes.items():
+            L.links_set_tuning(s.ctx, nm, L.TUNE_KEYS[k], v)
+        s.build(db)
+        o = s.simulate_packed(T, L.MIXED, out_capacity=B // 3)
+        s.sync()
+        nv = min(int(o.n_out[0]), B // 3)
+        if nm == 8:
+            full = s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=True, path=True, out_capacity=B // 3)
+            s.sync()
+            paths, traj, rows = full.path[:nv], full.traj[:nv], full.out_index[:nv]
+            ml = torch.empty_like(paths)
+            L.links_normalize_maxline(s.ctx, paths, ml)
+            flags = torch.empty((nv, 8), dtype=torch.uint8, device=dev)
+            nk = torch.empty(1, dtype=torch.int32, device=dev)
+            L.links_curate_paths(s.ctx, traj, rows, db.n_joints, db.adj, db.jtype, flags, nk)
+            q = ml[:16].clone()
+            order = torch.randperm(nv, generator=torch.Generator().manual_seed(5)).to(torch.int32).to(dev)
+            idx = torch.empty((16, 3), dtype=torch.int32, device=dev)
+            dist = torch.empty((16, 3), dtype=torch.float32, device=dev)
+            L.links_chamfer_first_under(s.ctx, q, ml, order, 0.03, 3, idx, dist)
+            s.sync()
+    if nm == 8:
+        pb = I.paper_batch(1, B, 8, seed=108)
+        with Simulator(pb.B, 8) as s:
+            s.build(to_device(pb, dev))
+            s.simulate(T, L.MIXED, L.OUT_VALID_ONLY, traj=False, path=False)  # the generic screen, same samples
+            s.sync()
+            topo = L.links_topo_create(s.ctx, int(pb.n_joints[0]), pb.adj[0], pb.jtype[0], 16)
+            try:
+                s.simulate_topology(topo, T, L.OUT_VALID_ONLY, traj=False, path=False)
+                s.sync()
+            finally:
+                L.links_topo_free(topo)
+    print(json.dumps({"profile_kernels": "done", "batch": B, "n_max": nm, "valid_rows": nv}))
+
+
 def make_batch(cfg, B, seed):
     """The seeded synthetic candidates of a configuration (B of them)."""
     from paper_2208_14567_gb300 import inputs as I
@@ -1156,6 +1212,8 @@ def main():
     ap.add_argument("--serve-pool", type=int, default=600_000)
     ap.add_argument("--serve-budget", type=int, default=8, help="GiB of device arena")
     ap.add_argument("--batch", type=int, default=300_000, help="candidates of --profile-kernels")
+    ap.add_argument("--profile-nmax", type=int, default=8, choices=[8, 20],
+                    help="joints 6..n of the --profile-kernels candidates")
     ap.add_argument("--profile-kernels", action="store_true",
                     help="launch each hot kernel once on a mid-size case (for a profiler) and exit")
     args = ap.parse_args()

@@ -26,6 +26,11 @@ __host__ __device__ constexpr size_t emit_warp_bytes(int n_max, int max_dyads, b
 // they pay for small mechanisms only (4 CTAs per SM still fit).
 constexpr int kScreenTwoStepMaxSlots = 9;
 
+// Starts moving the 128-byte line holding p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // Adds a per-lane count to a 64-bit counter (one atomic per warp).
 __device__ __forceinline__ void add_stat(int32_t* ctrs, int slot, unsigned v) {
 #pragma unroll
@@ -126,16 +131,27 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
   const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (g * G));
   constexpr int CH = G * S;  // steps per chunk
 
-  int n_ok = 0;
+  // The work list: n_list items of order, or p.order, the OK mechanisms sorted by dyad
+  // count (bucket d of p.ctrs[kHist + d] entries from the exclusive prefix hpre of lane d),
+  // taken from its end: the mechanisms with the most dyads first, so that the last work
+  // of the launch is the lightest.
+  int n_ok = 0, hpre = 0;
   if (n_list) {
     n_ok = *n_list;
   } else {
-    n_ok = p.ctrs[kHist + lane];
+    const int h = p.ctrs[kHist + lane];
+    int incl = h;
 #pragma unroll
-    for (int o = 16; o; o >>= 1) n_ok += __shfl_xor_sync(kFull, n_ok, o);
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += y;
+    }
+    hpre = incl - h;
+    n_ok = __shfl_sync(kFull, incl, 31);
   }
 
-  int qhead = 0, qend = 0;
+  int qhead = 0, qend = 0, qbase = 0;
+  int32_t qb = 0;  // lane i < kBatch: the mechanism of the batch's item i (item qbase + i)
   bool exhausted = false;
   int item = -1, chunk = 0;
   int64_t b = 0;
@@ -155,19 +171,41 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
         if (lane == 0) base = atomicAdd(&p.ctrs[kWork], kBatch);
         base = __shfl_sync(kFull, base, 0);
         if (base >= n_ok) { exhausted = true; break; }
-        qhead = base;
+        qhead = qbase = base;
         qend = min(base + kBatch, n_ok);
+        // the batch's mechanisms, a lane each, and their header, dyad records and fixed
+        // joints on their way to L2 (the groups take them over the next chunks).  On the
+        // sorted list an item's dyad count is its bucket: the last lane whose prefix
+        // does not exceed the item's position.
+        int ndq = p.max_dyads;
+        if (!n_list) {
+          const int q = n_ok - 1 - (qbase + lane);
+          int lo = 0;
+#pragma unroll
+          for (int step = 16; step; step >>= 1) {
+            const int v = __shfl_sync(kFull, hpre, lo + step);
+            if (v <= q) lo += step;
+          }
+          ndq = lo;
+        }
+        if (lane < qend - qbase) {
+          qb = ldro<NC>(order + (n_list ? qbase + lane : n_ok - 1 - (qbase + lane)));
+          prefetch_l2(p.hdr + qb);
+          const char* r0 = reinterpret_cast<const char*>(p.dyad + (int64_t)qb * p.max_dyads);
+          for (int o = 0; o < ndq * (int)sizeof(DyadRec); o += 128) prefetch_l2(r0 + o);
+          prefetch_l2(p.fixpos + (int64_t)qb * ns);
+        }
       }
       int leader = __ffs(need) - 1;
       need &= need - 1;
-      if (g == leader / G) { item = qhead; fresh = true; }
+      const int32_t bsel = __shfl_sync(kFull, qb, qhead - qbase);
+      if (g == leader / G) { item = qhead; b = bsel; fresh = true; }
       ++qhead;
     }
     if (__ballot_sync(kFull, item >= 0) == 0) break;
     __syncwarp();  // the previous mechanism's records are no longer read
 
     if (fresh) {
-      b = order[item];
       const MechHdr* hp = p.hdr + b;
       const int4 w0 = ldro<NC>(reinterpret_cast<const int4*>(hp));
       nd = (w0.y >> 8) & 0xff;

@@ -38,3 +38,18 @@ def test_bench_line_contract():
     assert e2e["unit"] == d["unit"] and e2e["value"] > 0
     assert e2e["h2d_bytes_per_step"] > 0 and e2e["d2h_bytes_per_step"] > 0
     assert d["gpu_launches"] > 0
+
+
+@pytest.mark.parametrize("nmax", [8, 20])
+def test_bench_profiling_mode(nmax):
+    """bench.py --profile-kernels (the launches the committed ncu summaries capture) runs
+    to completion on a small case."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--profile-kernels", "--batch", "20000",
+           "--profile-nmax", str(nmax)]
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads([ln for ln in r.stdout.splitlines() if ln.startswith("{")][-1])
+    assert d["profile_kernels"] == "done" and d["n_max"] == nmax and d["valid_rows"] > 0
