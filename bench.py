@@ -49,15 +49,22 @@ SCREEN_STEP_OPS = 6    # FP32 crank rotation, per step
 # The bound each hot kernel's ncu counters show (profiles/), and where it is read.
 BINDING = {"mixed_emit": "hbm", "mixed_screen": "alu", "plan_build": "hbm"}
 BINDING_EVIDENCE = {
-    "mixed_emit": "profiles/: emit issue active 71% vs DRAM 30% of peak on 6-8 joints; the HBM view counts "
-                  "only the real joints' bytes, the ALU view beside it",
-    "mixed_screen": "profiles/: screen DRAM 4% of peak, issue active 74%",
-    "plan_build": "profiles/: latency-bound, 12 of 32 lanes active",
+    "mixed_emit": "profiles/screen_emit_build_300k_6-8_full.md: emit issue active 73% vs DRAM 31-35% of peak "
+                  "(packed rows); the HBM view counts only the real joints' bytes, the ALU view beside it",
+    "mixed_screen": "profiles/screen_emit_build_300k_6-20_full.md: screen issue active 71%, DRAM 8.7% of peak, "
+                    "FMA 32% / ALU 37% pipe: instruction issue binds",
+    "plan_build": "profiles/screen_emit_build_300k_6-20_full.md: issue 45%, 29% of warps active (shared-memory "
+                  "limit), long-scoreboard 2.7 per issue: latency-bound",
 }
 # DRAM bytes per unit (per valid row for the emit, per candidate otherwise) from a committed
-# ncu capture of the same kernel on the same configuration, scaled to the launch; empty
-# where no capture of the current kernels exists for the configuration.
-TRAFFIC_PER_UNIT = {}
+# ncu capture of the same kernel and shapes on the same recipe (300,000 candidates,
+# `bench.py --profile-kernels`), scaled to the launch by the units it processes.
+TRAFFIC_PER_UNIT = {
+    ("config3_4M_6-20", "mixed_screen"): ((230.391 + 4.051 + 18.461 + 0.215) * 1e6 / 300000, "candidate"),
+    ("config3_4M_6-20", "mixed_emit"): ((19.811 + 364.924) * 1e6 / 24132, "row"),
+    ("config2_1M_6-8", "mixed_screen"): ((144.411 + 4.927) * 1e6 / 300000, "candidate"),
+    ("config2_1M_6-8", "mixed_emit"): ((45.407 + 865.231) * 1e6 / 74163, "row"),
+}
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, scaled per unit"
 
 
@@ -949,7 +956,10 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
         res["tuning"] = L.tuning_table(sim.ctx, nmax)
     if not fourbar:
         res["roofline"], res["roofline_views"] = roofline(kernels, batch, out, lock_np, dyad_steps, n_valid, T,
-                                                          nmax, sim, L)
+                                                          nmax, sim, L, cfg["name"])
+        for k, v in res["roofline_views"].items():
+            for view in v.values():
+                view["traffic"] = traffic(cfg["name"], k, n_valid, B)
     if packed:  # the same step with padded valid rows ([rows, n_max, T, 2], NaN padding)
         pad = alloc_out(sim, T, prec, mode, False, caps)
         pgraph = capture_step(sim, db, status, T, prec, mode, False, pad, L) if cfg["graph"] else None
@@ -1003,7 +1013,16 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
                  "prec": prec, "mode": mode, "n_valid": n_valid, "packed": packed, "caps": caps}
 
 
-def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L):
+def traffic(cfg_name, kernel, rows, candidates):
+    """DRAM bytes of one launch of `kernel` on this configuration, from the committed
+    capture's bytes per unit; None where there is none."""
+    per = TRAFFIC_PER_UNIT.get((cfg_name, kernel))
+    if per is None:
+        return None
+    return per[0] * (rows if per[1] == "row" else candidates)
+
+
+def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L, cfg_name=""):
     """Roofline views of the hot kernels (algorithmic work of one launch / its event
     time) and the binding one of the dominant kernel."""
     import numpy as np
@@ -1059,8 +1078,7 @@ def roofline(kernels, batch, out, lock_np, dyad_steps, rows, T, nmax, sim, L):
     roof = dict(views[top][bind])
     roof.update({"kernel": top, "share_of_step": kernels[top]["share"], "peak_source": pk["src"],
                  "binding_evidence": BINDING_EVIDENCE.get(top, ""),
-                 "traffic": TRAFFIC_PER_UNIT[top][0] * (rows if TRAFFIC_PER_UNIT[top][1] == "row" else len(lock_np))
-                 if top in TRAFFIC_PER_UNIT else None,
+                 "traffic": traffic(cfg_name, top, rows, len(lock_np)),
                  "traffic_source": TRAFFIC_SOURCE})
     return roof, views
 

@@ -462,9 +462,9 @@ LINKS_API int links_compact_valid_static(const uint8_t* valid, int64_t B, int32_
 
 /* Autotuner: on the plan as last built, over T steps, times the screen with every shape
  * (lanes 8/16/32 x steps per lane 1/2 x CTAs per SM all/2/1 x inline or deferred
- * rescue), then the emit (shared or
- * thread-local double-word slots x CTAs per SM all/2/1) on up to 16384 valid rows of
- * that screen's result, and keeps the fastest of each in the context's table for this
+ * rescue), then the emit (shared or thread-local double-word slots x CTAs per SM
+ * all/2/1) on up to 262144 packed valid rows of that screen's result (each shape once
+ * to warm up, three times timed), and keeps the fastest of each in the context's table for this
  * n_max (*lanes receives the screen's lanes; may be NULL).  Each shape gives the same
  * outputs; only the time differs.  Allocates scratch and synchronizes: call it before
  * capturing a graph.  Without it the defaults above apply. */

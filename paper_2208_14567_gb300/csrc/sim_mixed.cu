@@ -215,11 +215,12 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
 }
 
 // Autotuner: times the screen over its shapes (lanes per mechanism 8/16/32, one or two
-// steps per lane, CTAs per SM) on the built plan, then the emit over its shapes
-// (double-word slots in shared memory or thread-local, CTAs per SM) on up to
-// kTuneRows valid rows of that screen's result, and keeps the fastest of each in the
-// context's table for this n_max.  Each shape runs once to warm up and twice timed.
-constexpr int64_t kTuneRows = 16384;
+// steps per lane, CTAs per SM, inline or deferred rescue) on the built plan, then the
+// emit over its shapes (double-word slots in shared memory or thread-local, CTAs per
+// SM) on up to kTuneRows packed valid rows of that screen's result, and keeps the
+// fastest of each in the context's table for this n_max.  Each shape runs once to warm
+// up and three times timed.
+constexpr int64_t kTuneRows = 262144;
 
 int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) {
   const int64_t B = std::max<int64_t>(plan->B, 1);
@@ -228,6 +229,7 @@ int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) 
   int16_t* l = nullptr;
   float *q = nullptr, *traj = nullptr, *path = nullptr;
   int32_t *idx = nullptr, *nout = nullptr;
+  int64_t* row_off = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   int st = LINKS_OK;
   cudaError_t e = cudaMalloc(&v, B);
@@ -238,9 +240,9 @@ int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) 
   if (e == cudaSuccess) e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);
   if (e != cudaSuccess) st = cuda_status(e, "links_autotune");
-  auto timed = [&](auto&& run) -> float {  // warm-up + 2 timed runs, ms (huge on failure)
+  auto timed = [&](auto&& run) -> float {  // warm-up + 3 timed runs, ms (huge on failure)
     float total = 0.f;
-    for (int rep = 0; rep < 3 && !st; ++rep) {
+    for (int rep = 0; rep < 4 && !st; ++rep) {
       cudaEventRecord(e0, ctx->stream);
       st = run();
       cudaEventRecord(e1, ctx->stream);
@@ -282,17 +284,27 @@ int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) 
     if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
       st = set_error(LINKS_ECUDA, "links_autotune: screen failed");
     const int64_t R = std::min<int64_t>(nv, kTuneRows);
-    if (!st && R > 0) {
-      e = cudaMalloc(&traj, sizeof(float) * 2 * R * n_max * T);
-      if (e == cudaSuccess) e = cudaMalloc(&path, sizeof(float) * 2 * R * T);
+    if (!st && R > 0) {  // packed rows (their joints only), as links_simulate_packed writes them
+      e = cudaMalloc(&row_off, sizeof(int64_t) * (R + 1));
       if (e != cudaSuccess) st = cuda_status(e, "links_autotune");
+      if (!st) st = pack_offsets(ctx, plan, idx, R, row_off);
+      int64_t J = 0;
+      if (!st && cudaMemcpyAsync(&J, row_off + R, 8, cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
+        st = set_error(LINKS_ECUDA, "links_autotune: copy failed");
+      if (!st && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+        st = set_error(LINKS_ECUDA, "links_autotune: offsets failed");
+      if (!st) {
+        e = cudaMalloc(&traj, sizeof(float) * 2 * std::max<int64_t>(J, 1) * T);
+        if (e == cudaSuccess) e = cudaMalloc(&path, sizeof(float) * 2 * R * T);
+        if (e != cudaSuccess) st = cuda_status(e, "links_autotune");
+      }
       float emit_best = 1e30f;
       for (int dws : {1, 0})
         for (int ctas : {0, 2, 1}) {
           if (st) break;
           EmitShape es{dws != 0, ctas};
           const float ms = timed([&] {
-            return launch_emit<false>(ctx, plan, tab, false, l, idx, R, traj, path, "mixed_emit", &es);
+            return launch_emit<false>(ctx, plan, tab, false, l, idx, R, traj, path, "mixed_emit", &es, row_off, J);
           });
           if (ms < emit_best) {
             emit_best = ms;
@@ -313,6 +325,7 @@ int autotune(links_ctx ctx, links_plan plan, const TTable* tab, int* lanes_out) 
   cudaFree(nout);
   cudaFree(traj);
   cudaFree(path);
+  cudaFree(row_off);
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   return st;
