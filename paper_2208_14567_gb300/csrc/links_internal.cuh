@@ -26,6 +26,11 @@ __device__ __forceinline__ T ldro(const T* p) {
   else return __ldcg(p);
 }
 
+// Starts moving the 128-byte line holding p into L2 (no register result, no wait).
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 constexpr int kMaxJ = LINKS_MAX_JOINTS;  // joints per mechanism (bit masks are uint32)
 constexpr unsigned kFull = 0xffffffffu;  // every lane of a warp
 constexpr float kEmitBudget = 9.5e-6f;

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
 
 // Warp-flat builder kernel: each warp builds the 32 mechanisms from b0 = 32 x its global
 // warp index (build_flat_warp in plan_core.cuh).
-template <typename PT>
+template <typename PT, bool STAGE>
 __global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, const int32_t* __restrict__ n_joints,
                                                                       const uint8_t* __restrict__ adj,
                                                                       const int8_t* __restrict__ type,
@@ -298,8 +298,9 @@ __global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, 
   if (threadIdx.x < 32) hist[threadIdx.x] = 0;
   __syncthreads();
   const int64_t b0 = ((int64_t)blockIdx.x * kFlatWarps + warp) * 32;
-  const FlatResult r = build_flat_warp<PT>(B, b0, n_joints, adj, type, pos, p, flags,
-                                           flat_smem + warp * FlatSmem<PT>::bytes(p.n_max, p.max_dyads), lane);
+  const FlatResult r = build_flat_warp<PT, true, STAGE>(
+      B, b0, n_joints, adj, type, pos, p, flags, flat_smem + warp * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, STAGE),
+      lane);
   if (r.status >= 0) {
     if (status_out) status_out[b0 + lane] = r.status;
     if (r.status == LINKS_MECH_OK) atomicAdd(&hist[r.nd], 1);
@@ -333,6 +334,28 @@ __global__ void __launch_bounds__(256) scatter_kernel(int64_t B, PlanDev p) {
   if (threadIdx.x < 32 && cnt[threadIdx.x]) base[threadIdx.x] = atomicAdd(&p.ctrs[kCursor + threadIdx.x], cnt[threadIdx.x]);
   __syncthreads();
   if (nd >= 0) p.order[off[nd] + base[nd] + rank] = (int32_t)b;
+}
+
+// The warp-flat builder with its positions staged in shared memory unless staging them
+// would lower the resident blocks per SM (then they are read through the cache).
+template <typename PT>
+int launch_flat(links_ctx ctx, unsigned fgrid, int64_t B, const int32_t* n_joints, const uint8_t* adj,
+                const int8_t* type, const PT* ps, const PlanDev& p, int32_t* status_out, int flags) {
+  const size_t sm1 = kFlatWarps * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, true);
+  const size_t sm0 = kFlatWarps * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, false);
+  LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<PT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
+  LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<PT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm0));
+  int occ1 = 0, occ0 = 0;
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, build_flat_kernel<PT, true>, 32 * kFlatWarps, sm1));
+  LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, build_flat_kernel<PT, false>, 32 * kFlatWarps, sm0));
+  if (occ1 >= occ0)
+    build_flat_kernel<PT, true><<<fgrid, 32 * kFlatWarps, sm1, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+                                                                             status_out, flags);
+  else
+    build_flat_kernel<PT, false><<<fgrid, 32 * kFlatWarps, sm0, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+                                                                              status_out, flags);
+  LINKS_CUDA(cudaGetLastError());
+  return LINKS_OK;
 }
 
 }  // namespace
@@ -370,20 +393,16 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
       if (small) {
         build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
       } else {
-        const size_t sm = kFlatWarps * FlatSmem<float>::bytes(p.n_max, p.max_dyads);
-        LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        build_flat_kernel<float><<<fgrid, 32 * kFlatWarps, sm, ctx->stream>>>(B, n_joints, adj, type, ps, p,
-                                                                            status_out, flags);
+        int st = launch_flat<float>(ctx, fgrid, B, n_joints, adj, type, ps, p, status_out, flags);
+        if (st) return st;
       }
     } else {
       const double* ps = (const double*)pos0;
       if (small) {
         build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
       } else {
-        const size_t sm = kFlatWarps * FlatSmem<double>::bytes(p.n_max, p.max_dyads);
-        LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        build_flat_kernel<double><<<fgrid, 32 * kFlatWarps, sm, ctx->stream>>>(B, n_joints, adj, type, ps, p,
-                                                                             status_out, flags);
+        int st = launch_flat<double>(ctx, fgrid, B, n_joints, adj, type, ps, p, status_out, flags);
+        if (st) return st;
       }
     }
   }

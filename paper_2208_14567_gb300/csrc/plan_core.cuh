@@ -124,7 +124,10 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
 // ---------------------------------------------------------------------------------------
 // Warp-flat builder: each warp builds 32 mechanisms.  The lanes first stage the warp's
 // neighbour masks (a lane per adjacency row, word loads issued in batches), joint types
-// and initial positions (vector loads) in shared memory; then lane m runs mechanism m's
+// and (with STAGE) initial positions (vector loads) in shared memory; without STAGE the
+// positions are sent to L2 and the later phases read them through the cache, which
+// halves the warp's shared memory where staged positions would limit the resident warps
+// (n_max 20: 11 KB per warp, 20 warps per SM, against 32 unstaged); then lane m runs mechanism m's
 // checks, solve-order search and slot assignment (the decisions of build_one, on bit
 // masks); then the warp computes the geometry of all its mechanisms' dyads as one flat
 // list, a dyad per lane, so that mechanisms of different sizes keep every lane busy;
@@ -136,7 +139,7 @@ constexpr int kFlatWarps = 4;  // warps per block
 // One warp's shared memory, per-mechanism arrays column-major ([e * 32 + m]) unless noted.
 template <typename PT>
 struct FlatSmem {
-  PT* pos;        // [32][2 NM + 1]  initial positions, odd row stride (row-major)
+  PT* pos;        // [32][2 NM + 1]  initial positions, odd row stride (row-major; with staging)
   uint32_t* nb;   // [NM]            neighbour masks; after the search, the slot bounds (float)
   int* pfx;       // [33]            exclusive prefix of the dyad counts
   uint8_t* type;  // [32][NM]        joint types as stored in global memory (row-major)
@@ -149,14 +152,14 @@ struct FlatSmem {
     return (sizeof(PT) * 32 * (2 * NM + 1) + 15) & ~size_t(15);
   }
   __host__ __device__ static size_t type_bytes(int NM) { return (32 * (size_t)NM + 15) & ~size_t(15); }
-  __host__ __device__ static size_t bytes(int NM, int MD) {
-    const size_t b = pos_bytes(NM) + type_bytes(NM) + 4 * 32 * NM + 4 * 36 + 32 * NM + 3 * 32 * MD + 32;
+  __host__ __device__ static size_t bytes(int NM, int MD, bool stage) {
+    const size_t b = (stage ? pos_bytes(NM) : 0) + type_bytes(NM) + 4 * 32 * NM + 4 * 36 + 32 * NM + 3 * 32 * MD + 32;
     return (b + 15) & ~size_t(15);
   }
-  __device__ FlatSmem(char* base, int NM, int MD) {
+  __device__ FlatSmem(char* base, int NM, int MD, bool stage) {
     size_t o = 0;
-    pos = reinterpret_cast<PT*>(base);
-    o += pos_bytes(NM);
+    pos = stage ? reinterpret_cast<PT*>(base) : nullptr;
+    o += stage ? pos_bytes(NM) : 0;
     type = reinterpret_cast<uint8_t*>(base + o);
     o += type_bytes(NM);
     nb = reinterpret_cast<uint32_t*>(base + o);
@@ -199,18 +202,23 @@ struct FlatResult {
   int status, nd;
 };
 
-template <typename PT, bool NC = true>
+template <typename PT, bool NC = true, bool STAGE = true>
 __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, const int32_t* __restrict__ n_joints,
                                                       const uint8_t* __restrict__ adj,
                                                       const int8_t* __restrict__ type, const PT* __restrict__ pos,
                                                       const PlanDev& p, int flags, char* wsmem, int lane) {
   const int NM = p.n_max, MD = p.max_dyads;
-  FlatSmem<PT> S(wsmem, NM, MD);
+  FlatSmem<PT> S(wsmem, NM, MD, STAGE);
   const int mc = b0 < B ? (int)min((int64_t)32, B - b0) : 0;
   const int prow = 2 * NM + 1;
   const int m = lane;
   const int64_t b = b0 + m;
   const int n = m < mc ? ldro<NC>(n_joints + b) : 0;
+  // coordinate x of mechanism mm's initial positions
+  const auto posv = [&](int mm, int x) -> PT {
+    if constexpr (STAGE) return S.pos[mm * prow + x];
+    else return ldro<NC>(pos + (b0 + mm) * 2 * NM + x);
+  };
 
   // 1. staging
   const int nrows = mc * NM;
@@ -251,34 +259,41 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       S.nb[(r - mm * NM) * 32 + mm] = mask;
     }
   }
+  if constexpr (!STAGE) {  // the warp's positions on their way to L2
+    const char* pb = reinterpret_cast<const char*>(pos + b0 * 2 * NM);
+    const int nbytes = mc * 2 * NM * (int)sizeof(PT);
+    for (int o = lane * 128; o < nbytes; o += 32 * 128) prefetch_l2(pb + o);
+  }
   {
     const int per = 2 * NM, ne = mc * per;
     const PT* src = pos + b0 * per;
-    if (flags & 2) {  // positions as 16-byte vectors, eight per lane in flight
-      using V = typename Vec16<PT>::T;
-      constexpr int kN = Vec16<PT>::kN;
-      const V* vs = reinterpret_cast<const V*>(src);
-      const int nv = ne / kN;
-      for (int x0 = 0; x0 < nv; x0 += 256) {
-        V v[8];
+    if constexpr (STAGE) {
+      if (flags & 2) {  // positions as 16-byte vectors, eight per lane in flight
+        using V = typename Vec16<PT>::T;
+        constexpr int kN = Vec16<PT>::kN;
+        const V* vs = reinterpret_cast<const V*>(src);
+        const int nv = ne / kN;
+        for (int x0 = 0; x0 < nv; x0 += 256) {
+          V v[8];
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const int x = x0 + h * 32 + lane;
-          if (x < nv) v[h] = ldro<NC>(vs + x);
-        }
+          for (int h = 0; h < 8; ++h) {
+            const int x = x0 + h * 32 + lane;
+            if (x < nv) v[h] = ldro<NC>(vs + x);
+          }
 #pragma unroll
-        for (int h = 0; h < 8; ++h) {
-          const int x = x0 + h * 32 + lane;
-          if (x < nv) {
-            const int e = x * kN, mm = e / per;
-            Vec16<PT>::put(S.pos + mm * prow + (e - mm * per), v[h]);
+          for (int h = 0; h < 8; ++h) {
+            const int x = x0 + h * 32 + lane;
+            if (x < nv) {
+              const int e = x * kN, mm = e / per;
+              Vec16<PT>::put(S.pos + mm * prow + (e - mm * per), v[h]);
+            }
           }
         }
-      }
-    } else {
-      for (int x = lane; x < ne; x += 32) {
-        const int mm = x / per;
-        S.pos[mm * prow + (x - mm * per)] = ldro<NC>(src + x);
+      } else {
+        for (int x = lane; x < ne; x += 32) {
+          const int mm = x / per;
+          S.pos[mm * prow + (x - mm * per)] = ldro<NC>(src + x);
+        }
       }
     }
     const int nt = mc * NM;  // types: 16-byte vectors over whole chunks, then bytes
@@ -295,7 +310,6 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
   __syncwarp();
 
   // 2. lane m: checks, solve order and slots of mechanism m (build_one's decisions)
-  const PT* P = S.pos + m * prow;
   int status = LINKS_MECH_OK, nd = 0, nf = 0, motor = -1, pivot = -1;
   uint32_t fixm = 0, simm = 0, motm = 0;
   if (m < mc) {
@@ -377,7 +391,8 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       const int a = ffs32(q);
       S.slot[a * 32 + m] = (uint8_t)nf;
       o.slot_joint[nf] = (uint8_t)a;
-      const dw2 r = rel(P, a, pivot);
+      const PT pa[4] = {posv(m, 2 * a), posv(m, 2 * a + 1), posv(m, 2 * pivot), posv(m, 2 * pivot + 1)};
+      const dw2 r = rel(pa, 0, 1);
       o.fixpos[nf] = make_float4(r.x.h, r.x.l, r.y.h, r.y.l);
       const float bs = hyp_up(r.x.h, r.y.h);
       bnd[nf * 32 + m] = bs;
@@ -391,7 +406,8 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       S.slot[k * 32 + m] = (uint8_t)(nf + 1 + d);
       o.slot_joint[nf + 1 + d] = (uint8_t)k;
     }
-    u = rel(P, motor, pivot);
+    const PT pm[4] = {posv(m, 2 * motor), posv(m, 2 * motor + 1), posv(m, 2 * pivot), posv(m, 2 * pivot + 1)};
+    u = rel(pm, 0, 1);
     crank = hyp_up(u.x.h, u.y.h);
     bnd[nf * 32 + m] = crank;
     bmax = fmaxf(bmax, crank);
@@ -429,7 +445,12 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
     }
     const int mm = lo, d = f - S.pfx[mm];
     const int k = S.dk[d * 32 + mm], sk = S.nfv[mm] + 1 + d;
-    const DyadGeo g = dyad_geo(S.pos + mm * prow, k, (int)S.di[d * 32 + mm], (int)S.dj[d * 32 + mm]);
+    const int ji = S.di[d * 32 + mm], jj = S.dj[d * 32 + mm];
+    const PT q[6] = {posv(mm, 2 * ji), posv(mm, 2 * ji + 1), posv(mm, 2 * jj), posv(mm, 2 * jj + 1),
+                     posv(mm, 2 * k), posv(mm, 2 * k + 1)};
+    DyadGeo g = dyad_geo(q, 2, 0, 1);  // the parents as local joints 0 and 1, k as 2
+    g.i = g.i == 0 ? ji : jj;
+    g.j = g.j == 0 ? ji : jj;
     const int si = S.slot[g.i * 32 + mm], sj = S.slot[g.j * 32 + mm];
     p.dyad[(b0 + mm) * MD + d] = dyad_record(g, si, sj, k, sk);
     S.di[d * 32 + mm] = (uint8_t)si;
@@ -447,7 +468,7 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       bmax = fmaxf(bmax, bk);
     }
     for (int a = 0; a < n; ++a)
-      o.pos64[S.slot[a * 32 + m]] = make_double2((double)P[2 * a], (double)P[2 * a + 1]);
+      o.pos64[S.slot[a * 32 + m]] = make_double2((double)posv(m, 2 * a), (double)posv(m, 2 * a + 1));
     MechHdr h{};
     h.n = (uint8_t)n;
     h.status = status;
@@ -458,12 +479,13 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
     h.pad0 = S.slot[pivot * 32 + m];  // pivot slot
     h.coupler_slot = (uint8_t)(nd > 0 ? nf + nd : nf);
     h.ux_h = u.x.h; h.ux_l = u.x.l; h.uy_h = u.y.h; h.uy_l = u.y.l;
-    const dw px = abs_dw(P, 2 * pivot), py = abs_dw(P, 2 * pivot + 1);
+    const PT pv[2] = {posv(m, 2 * pivot), posv(m, 2 * pivot + 1)};
+    const dw px = abs_dw(pv, 0), py = abs_dw(pv, 1);
     h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
     h.bmax = bmax;
-    float lo_x = (float)P[0], hi_x = lo_x, lo_y = (float)P[1], hi_y = lo_y;
+    float lo_x = (float)posv(m, 0), hi_x = lo_x, lo_y = (float)posv(m, 1), hi_y = lo_y;
     for (int a = 1; a < n; ++a) {
-      const float x = (float)P[2 * a], y = (float)P[2 * a + 1];
+      const float x = (float)posv(m, 2 * a), y = (float)posv(m, 2 * a + 1);
       lo_x = fminf(lo_x, x);
       hi_x = fmaxf(hi_x, x);
       lo_y = fminf(lo_y, y);

@@ -203,7 +203,7 @@ __host__ __device__ PlanDev plan_view(const PlanDev& p, int64_t a) {
 }
 
 size_t loop_smem_bytes(int nm, int md, int G, bool dws) {
-  const size_t build = (size_t)kLoopWarps * FlatSmem<float>::bytes(nm, md);
+  const size_t build = (size_t)kLoopWarps * FlatSmem<float>::bytes(nm, md, true);
   const size_t screen = (size_t)kLoopWarps * ((size_t)nm * 384 + (32 / G) * (2 * md + 1) * 16);
   const size_t emit = (size_t)kLoopWarps * emit_warp_bytes(nm, md, dws);
   return std::max(build, std::max(screen, emit));
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) serve_loop_kernel(LoopArgs A)
     {
       const int flags = ((nm % 4 == 0 && ((uintptr_t)adj & 3u) == 0) ? 1 : 0) |
                         ((((uintptr_t)pos & 15u) == 0 && ((uintptr_t)type & 15u) == 0 && nm % 2 == 0) ? 2 : 0);
-      char* wsm = smem + warp * FlatSmem<float>::bytes(nm, md);
+      char* wsm = smem + warp * FlatSmem<float>::bytes(nm, md, true);
       for (int64_t t = gw; t < (B + 31) / 32; t += nw) {
         const FlatResult r = build_flat_warp<float, false>(B, t * 32, nj, adj, type, pos, p, flags, wsm, lane);
         if (r.status >= 0) {

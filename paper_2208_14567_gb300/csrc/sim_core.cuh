@@ -26,11 +26,6 @@ __host__ __device__ constexpr size_t emit_warp_bytes(int n_max, int max_dyads, b
 // they pay for small mechanisms only (4 CTAs per SM still fit).
 constexpr int kScreenTwoStepMaxSlots = 9;
 
-// Starts moving the 128-byte line holding p into L2 (no register result, no wait).
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-}
-
 // Adds a per-lane count to a 64-bit counter (one atomic per warp).
 __device__ __forceinline__ void add_stat(int32_t* ctrs, int slot, unsigned v) {
 #pragma unroll
