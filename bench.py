@@ -65,6 +65,7 @@ TRAFFIC_PER_UNIT = {
     ("config2_1M_6-8", "mixed_screen"): ((144.411 + 4.927) * 1e6 / 300000, "candidate"),
     ("config2_1M_6-8", "mixed_emit"): ((45.407 + 865.231) * 1e6 / 74163, "row"),
 }
+E2E_WARMUP = 3  # untimed pipelined steps before the end-to-end timing
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, scaled per unit"
 
 
@@ -688,6 +689,7 @@ def config_dict(cfg, args, world):
     """The `config` object of a bench line (the same for both arms)."""
     d = {"workload": cfg["workload"], "batch": cfg["B"], "T": args.T, "joints": cfg["joints"],
          "n_max": cfg["n_max"], "precision": cfg["precision_name"], "out_mode": cfg["out_name"],
+         "adjacency": "neighbour bit masks" if cfg.get("masks") else "uint8 matrix",
          "graph": cfg["graph"], "l2": cfg["l2"], "parallelism": f"replicas x{world}"}
     return d
 
@@ -731,17 +733,22 @@ CONFIGS = {
         "l2": "inputs 1 MB fit L2; a 256 MB buffer is written between timed steps"},
     2: {"name": "config2_1M_6-8", "kind": "dyad", "B": 1_000_000, "n_lo": 6, "n_hi": 8, "n_max": 8,
         "joints": "6-8", "precision_name": "mixed", "out_name": "valid_packed", "graph": False, "packed": True,
-        "workload": "1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U[0,1]^2 float32, T=200, "
-                    "mixed precision, valid-only trajectories (packed by joint count) + paths + flags",
-        "l2": "inputs 140 MB per step exceed the 126 MB L2; no flush"},
+        "masks": True,
+        "workload": "1M dyad-built 1-DOF candidates, 6-8 joints, 2-3 ground, positions U[0,1]^2 float32, adjacency "
+                    "as neighbour bit masks, T=200, mixed precision, valid-only trajectories (packed by joint count) "
+                    "+ paths + flags",
+        "l2": "inputs 108 MB per step fit the 126 MB L2; a 256 MB buffer is written between timed steps",
+        "flush": True},
     3: {"name": "config3_4M_6-20", "kind": "dyad", "B": 4 * 1024 * 1024, "n_lo": 6, "n_hi": 20, "n_max": 20,
         "joints": "6-20", "precision_name": "mixed", "out_name": "valid_packed", "graph": True, "packed": True,
+        "masks": True,
         "workload": "4M (4,194,304) dyad-built 1-DOF candidates, joint count uniform in 6..20 (n_max 20), 2-3 "
-                    "ground, positions U[0,1]^2 float32, T=200, mixed precision; one CUDA-graph step of device "
+                    "ground, positions U[0,1]^2 float32, adjacency as neighbour bit masks, T=200, mixed precision; "
+                    "one CUDA-graph step of device "
                     "plan build + persistent certified screen (lanes per mechanism autotuned) + compaction + "
                     "emit; valid-only trajectories (packed by joint count) + paths + flags; the plain FP64 kernel "
                     "on the same inputs",
-        "l2": "inputs 2.4 GB per step exceed the 126 MB L2; no flush"},
+        "l2": "inputs 1.1 GB per step exceed the 126 MB L2; no flush"},
 }
 
 
@@ -812,6 +819,35 @@ def accuracy(cfg, batch, out, T, full_mode, seed=99, rows_sample=2000):
             "oracle_seconds": time.perf_counter() - t0}
 
 
+def time_step_variant(sim, db, status, T, prec, mode, packed, out, cfg, steps, L):
+    """Device time per step (ms, max over ranks) of a variant of the step: two untimed
+    steps, then `steps` timed ones, under a graph when the configuration uses one."""
+    import torch
+    dev = out.valid.device
+    stream = torch.cuda.current_stream(dev)
+    graph = capture_step(sim, db, status, T, prec, mode, packed, out, L) if cfg["graph"] else None
+
+    def one():
+        if graph is not None:
+            L.links_graph_launch(sim.ctx, graph)
+        else:
+            sim.build(db, status)
+            simulate(sim, T, prec, mode, packed, out)
+
+    for _ in range(2):
+        one()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if graph is not None:
+        L.links_graph_free(graph)
+    world = torch.distributed.get_world_size() if torch.distributed.is_initialized() else 1
+    return max_over_ranks(e0.elapsed_time(e1) / steps, world, dev)
+
+
 def alloc_out(sim, T, prec, mode, packed, caps):
     """Outputs of a valid-rows step: caps = (rows, joint rows) capacities."""
     if packed:
@@ -848,7 +884,8 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     stream = torch.cuda.current_stream(dev)
     T, B, nmax = args.T, cfg["B"], cfg["n_max"]
     batch = make_batch(cfg, B, seed=rank)
-    db = to_device(batch, dev)
+    masks = cfg.get("masks", False)
+    db = to_device(batch, dev, masks=masks)
     sim = Simulator(B, nmax, device=local, stream=stream)
     status = torch.empty(B, dtype=torch.int32, device=dev)
     fourbar = cfg["kind"] == "fourbar"
@@ -888,7 +925,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
         step()
     sim.sync()
     launches0 = L.links_launch_count(sim.ctx)
-    flush = fourbar  # a small working set: write a buffer larger than L2 between timed steps
+    flush = cfg.get("flush", fourbar)  # a small working set: write a buffer larger than L2 between timed steps
     barrier(world)
     torch.cuda.synchronize(dev)
     clk = Clocks(local) if headline else None
@@ -962,29 +999,18 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
                 view["traffic"] = traffic(cfg["name"], k, n_valid, B)
     if packed:  # the same step with padded valid rows ([rows, n_max, T, 2], NaN padding)
         pad = alloc_out(sim, T, prec, mode, False, caps)
-        pgraph = capture_step(sim, db, status, T, prec, mode, False, pad, L) if cfg["graph"] else None
-        for _ in range(2):
-            if pgraph is not None:
-                L.links_graph_launch(sim.ctx, pgraph)
-            else:
-                sim.build(db, status)
-                simulate(sim, T, prec, mode, False, pad)
-        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        p0.record(stream)
-        for _ in range(steps):
-            if pgraph is not None:
-                L.links_graph_launch(sim.ctx, pgraph)
-            else:
-                sim.build(db, status)
-                simulate(sim, T, prec, mode, False, pad)
-        p1.record(stream)
-        torch.cuda.synchronize(dev)
-        pms = max_over_ranks(p0.elapsed_time(p1) / steps, world, dev)
+        pms = time_step_variant(sim, db, status, T, prec, mode, False, pad, cfg, steps, L)
         res["valid_only_padded"] = {"ms_per_step": pms, "value": world * B * T / (pms * 1e-3),
                                     "same_rows": bool(torch.equal(pad.out_index[:n_valid], out.out_index[:n_valid]))}
-        if pgraph is not None:
-            L.links_graph_free(pgraph)
         del pad
+        torch.cuda.empty_cache()
+    if masks:  # the same step with the adjacency as the uint8 matrix
+        dbb = to_device(batch, dev)
+        alt = alloc_out(sim, T, prec, mode, packed, caps)
+        ams = time_step_variant(sim, dbb, status, T, prec, mode, packed, alt, cfg, steps, L)
+        res["adjacency_uint8"] = {"ms_per_step": ams, "value": world * B * T / (ams * 1e-3),
+                                  "same_rows": bool(torch.equal(alt.out_index[:n_valid], out.out_index[:n_valid]))}
+        del alt, dbb
         torch.cuda.empty_cache()
 
     # the plain FP64 kernel on the same inputs (the comparator the metric names)
@@ -1010,7 +1036,7 @@ def run_config(cfg, args, world, rank, local, steps, warmup, headline=False):
     if rank == 0 and not args.no_accuracy:
         res["accuracy_vs_oracle"] = accuracy(cfg, batch, out, T, fourbar)
     return res, {"sim": sim, "db": db, "out": out, "status": status, "batch": batch, "graph": graph,
-                 "prec": prec, "mode": mode, "n_valid": n_valid, "packed": packed, "caps": caps}
+                 "prec": prec, "mode": mode, "n_valid": n_valid, "packed": packed, "caps": caps, "masks": masks}
 
 
 def traffic(cfg_name, kernel, rows, candidates):
@@ -1099,18 +1125,19 @@ def e2e_run(state, args, world, local, full):
     sim, batch, T = state["sim"], state["batch"], args.T
     B = batch.B
     prec, mode = state["prec"], state["mode"]
+    masks = state["masks"]
     host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-               for a in (batch.n_joints, batch.adj, batch.jtype, batch.pos)]
+               for a in (batch.n_joints, batch.masks().view(np.int32) if masks else batch.adj, batch.jtype, batch.pos)]
     packed = state["packed"]
     if "dbs" not in state:
-        state["dbs"] = [state["db"], to_device(batch, dev)]
+        state["dbs"] = [state["db"], to_device(batch, dev, masks=masks)]
         state["outs"] = [state["out"], alloc_out(sim, T, prec, mode, packed, state["caps"])]
         graphs = [state["graph"], None]
         if state["graph"] is not None:
             graphs[1] = capture_step(sim, state["dbs"][1], state["status"], T, prec, mode, packed, state["outs"][1], L)
         state["graphs"] = graphs
     dbs, outs, graphs = state["dbs"], state["outs"], state["graphs"]
-    dev_in = [[d.n_joints, d.adj, d.jtype, d.pos] for d in dbs]
+    dev_in = [[d.n_joints, d.nbr if masks else d.adj, d.jtype, d.pos] for d in dbs]
     h2d_stream, copy_stream = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
     uploaded = [torch.cuda.Event() for _ in range(2)]
     computed = [torch.cuda.Event() for _ in range(2)]
@@ -1169,29 +1196,35 @@ def e2e_run(state, args, world, local, full):
                 d.copy_(h, non_blocking=True)
             uploaded[j].record(h2d_stream)
 
-    total = 0
+    def run(steps):
+        """`steps` pipelined steps from the first upload to the last drain; D2H bytes."""
+        total = 0
+        upload(0)
+        for i in range(steps):
+            j = i % 2
+            if i >= 2:
+                stream.wait_event(drained[j])  # output buffer j is free again
+            stream.wait_event(uploaded[j])
+            if graphs[j] is not None:
+                L.links_graph_launch(sim.ctx, graphs[j])
+            else:
+                sim.build(dbs[j], state["status"])
+                simulate(sim, T, prec, mode, packed, outs[j])
+            computed[j].record(stream)
+            if i + 1 < steps:
+                upload(i + 1)
+            if i >= 1:
+                total += drain(1 - j)
+        total += drain((steps - 1) % 2)
+        copy_stream.synchronize()
+        torch.cuda.synchronize(dev)
+        return total
+
+    run(E2E_WARMUP)  # untimed: the first copies between fresh pinned and device buffers run slower
     barrier(world)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    upload(0)
-    for i in range(args.e2e_steps):
-        j = i % 2
-        if i >= 2:
-            stream.wait_event(drained[j])  # output buffer j is free again
-        stream.wait_event(uploaded[j])
-        if graphs[j] is not None:
-            L.links_graph_launch(sim.ctx, graphs[j])
-        else:
-            sim.build(dbs[j], state["status"])
-            simulate(sim, T, prec, mode, packed, outs[j])
-        computed[j].record(stream)
-        if i + 1 < args.e2e_steps:
-            upload(i + 1)
-        if i >= 1:
-            total += drain(1 - j)
-    total += drain((args.e2e_steps - 1) % 2)
-    copy_stream.synchronize()
-    torch.cuda.synchronize(dev)
+    total = run(args.e2e_steps)
     el = max_over_ranks((time.perf_counter() - t0) / args.e2e_steps, world, dev)
     barrier(world)
     del hbuf
@@ -1210,7 +1243,7 @@ def main():
     ap.add_argument("--T", type=int, default=200)
     ap.add_argument("--headline-batch", type=int, default=0,
                     help="candidates of the headline configuration (0: the configuration's own, for small test runs)")
-    ap.add_argument("--e2e-steps", type=int, default=12)
+    ap.add_argument("--e2e-steps", type=int, default=24)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-sample", type=int, default=65536, help="candidates per step of the reference arm")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -1251,7 +1284,8 @@ def main():
     res, state = run_config(head, args, world, rank, local, args.steps, args.warmup, headline=True)
     e2e = e2e_run(state, args, world, local, full=False)
     e2e["result"] = "flags, lock steps, min_disc, valid indices and valid coupler paths to pinned host memory"
-    e2e["pipelined"] = "two input and two output buffers; step i computes while step i+1 uploads and step i-1 drains"
+    e2e["pipelined"] = ("two input and two output buffers; step i computes while step i+1 uploads and step i-1 "
+                        "drains; timed from the first upload to the last drain, after 3 untimed steps")
     e2e_full = None
     if not args.no_e2e_full:
         e2e_full = e2e_run(state, args, world, local, full=True)
@@ -1291,6 +1325,7 @@ def main():
         "kernel_shapes_autotuned": res.get("tuning"),
         "plain_f64": res.get("plain_f64"),
         "valid_only_padded": res.get("valid_only_padded"),
+        "adjacency_uint8": res.get("adjacency_uint8"),
         "accuracy_vs_oracle": res.get("accuracy_vs_oracle"),
         "algorithmic_dyad_steps_per_step": res["algorithmic_dyad_steps_per_step"],
         "kernels": res["kernels"],

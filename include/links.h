@@ -121,6 +121,17 @@ LINKS_API int links_plan_build(links_ctx ctx, links_plan plan, int64_t B, const 
                      const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
                      int32_t* status_out);
 
+/* links_plan_build with the adjacency given as neighbour bit masks (the same matrix,
+ * one bit per entry): nbr [B, n_max] uint32 (device), bit c of nbr[b][a] set when
+ * joints a and c are linked; bits at c >= n_joints[b] are ignored.  The other inputs,
+ * the rules and the plan are those of links_plan_build (the same plan to the bit); the
+ * masks are a fifth of the bytes of the uint8 matrix at n_max 20 and need no
+ * conversion on the device.  Asynchronous.  LINKS_EINVAL / LINKS_ECAPACITY as
+ * links_plan_build. */
+LINKS_API int links_plan_build_masks(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                                     const uint32_t* nbr, const int8_t* type, const void* pos0, int pos_dtype,
+                                     int32_t* status_out);
+
 /* Same rules, same result, computed by host threads from HOST inputs; the plan
  * is uploaded on the context's stream.  status_out [B] is host memory.
  * Synchronous (returns after the upload completed). */

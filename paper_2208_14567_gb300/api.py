@@ -13,23 +13,27 @@ from . import links as L
 @dataclass
 class DeviceBatch:
     n_joints: "object"  # torch int32 [B]
-    adj: "object"       # torch uint8 [B, n, n]
+    adj: "object"       # torch uint8 [B, n, n], or None with nbr
     jtype: "object"     # torch int8  [B, n]
     pos: "object"       # torch float32/float64 [B, n, 2]
+    nbr: "object" = None  # torch int32 [B, n]: the adjacency as neighbour bit masks
 
     @property
     def B(self):
         return int(self.n_joints.shape[0])
 
 
-def to_device(batch, device="cuda", non_blocking=False) -> DeviceBatch:
-    """Copy a MechBatch (numpy) to torch tensors on `device`."""
+def to_device(batch, device="cuda", non_blocking=False, masks=False) -> DeviceBatch:
+    """Copy a MechBatch (numpy) to torch tensors on `device`; with masks=True the
+    adjacency goes as neighbour bit masks (a fifth of the bytes at n_max 20)."""
     import torch
 
     def t(a):
         x = torch.from_numpy(np.ascontiguousarray(a))
         return x.to(device, non_blocking=non_blocking)
 
+    if masks:
+        return DeviceBatch(t(batch.n_joints), None, t(batch.jtype), t(batch.pos), t(batch.masks().view(np.int32)))
     return DeviceBatch(t(batch.n_joints), t(batch.adj), t(batch.jtype), t(batch.pos))
 
 
@@ -77,7 +81,10 @@ class Simulator:
         import torch
         if status is None:
             status = torch.empty(db.B, dtype=torch.int32, device=self.device)
-        L.links_plan_build(self.ctx, self.plan, db.n_joints, db.adj, db.jtype, db.pos, status)
+        if db.nbr is not None:
+            L.links_plan_build_masks(self.ctx, self.plan, db.n_joints, db.nbr, db.jtype, db.pos, status)
+        else:
+            L.links_plan_build(self.ctx, self.plan, db.n_joints, db.adj, db.jtype, db.pos, status)
         self.B = db.B
         return status
 

@@ -283,6 +283,16 @@ int links_plan_build(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n
   return plan_build_device(ctx, plan, B, n_joints, adj, type, pos0, pos_dtype, status_out);
 }
 
+int links_plan_build_masks(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
+                           const uint32_t* nbr, const int8_t* type, const void* pos0, int pos_dtype,
+                           int32_t* status_out) {
+  int st = check_build(ctx, plan, B, n_joints, reinterpret_cast<const uint8_t*>(nbr), type, pos0, pos_dtype,
+                       "links_plan_build_masks");
+  if (st) return st;
+  LINKS_CUDA(cudaSetDevice(ctx->device));
+  return plan_build_device(ctx, plan, B, n_joints, nullptr, type, pos0, pos_dtype, status_out, nbr);
+}
+
 int links_plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                           const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
                           int32_t* status_out) {

@@ -178,9 +178,10 @@ constexpr int32_t kErrEmitLock = 1;   // emit found a lock in a mechanism the sc
 constexpr int32_t kErrBadIndex = 2;   // an index outside its buffer was skipped
 
 // Entry points implemented per translation unit.
+// nbr (device [B, n_max] neighbour masks, may be NULL) replaces adj when given.
 int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                       const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
-                      int32_t* status_out);
+                      int32_t* status_out, const uint32_t* nbr = nullptr);
 int plan_build_host(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                     const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
                     int32_t* status_out);

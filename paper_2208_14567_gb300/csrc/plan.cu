@@ -289,6 +289,7 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
 template <typename PT, bool STAGE>
 __global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, const int32_t* __restrict__ n_joints,
                                                                       const uint8_t* __restrict__ adj,
+                                                                      const uint32_t* __restrict__ nbr,
                                                                       const int8_t* __restrict__ type,
                                                                       const PT* __restrict__ pos, PlanDev p,
                                                                       int32_t* __restrict__ status_out, int flags) {
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, 
   __syncthreads();
   const int64_t b0 = ((int64_t)blockIdx.x * kFlatWarps + warp) * 32;
   const FlatResult r = build_flat_warp<PT, true, STAGE>(
-      B, b0, n_joints, adj, type, pos, p, flags, flat_smem + warp * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, STAGE),
+      B, b0, n_joints, adj, nbr, type, pos, p, flags, flat_smem + warp * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, STAGE),
       lane);
   if (r.status >= 0) {
     if (status_out) status_out[b0 + lane] = r.status;
@@ -340,7 +341,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(int64_t B, PlanDev p) {
 // would lower the resident blocks per SM (then they are read through the cache).
 template <typename PT>
 int launch_flat(links_ctx ctx, unsigned fgrid, int64_t B, const int32_t* n_joints, const uint8_t* adj,
-                const int8_t* type, const PT* ps, const PlanDev& p, int32_t* status_out, int flags) {
+                const uint32_t* nbr, const int8_t* type, const PT* ps, const PlanDev& p, int32_t* status_out,
+                int flags) {
   const size_t sm1 = kFlatWarps * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, true);
   const size_t sm0 = kFlatWarps * FlatSmem<PT>::bytes(p.n_max, p.max_dyads, false);
   LINKS_CUDA(cudaFuncSetAttribute(build_flat_kernel<PT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
@@ -349,10 +351,10 @@ int launch_flat(links_ctx ctx, unsigned fgrid, int64_t B, const int32_t* n_joint
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, build_flat_kernel<PT, true>, 32 * kFlatWarps, sm1));
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ0, build_flat_kernel<PT, false>, 32 * kFlatWarps, sm0));
   if (occ1 >= occ0)
-    build_flat_kernel<PT, true><<<fgrid, 32 * kFlatWarps, sm1, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+    build_flat_kernel<PT, true><<<fgrid, 32 * kFlatWarps, sm1, ctx->stream>>>(B, n_joints, adj, nbr, type, ps, p,
                                                                              status_out, flags);
   else
-    build_flat_kernel<PT, false><<<fgrid, 32 * kFlatWarps, sm0, ctx->stream>>>(B, n_joints, adj, type, ps, p,
+    build_flat_kernel<PT, false><<<fgrid, 32 * kFlatWarps, sm0, ctx->stream>>>(B, n_joints, adj, nbr, type, ps, p,
                                                                               status_out, flags);
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
@@ -371,7 +373,7 @@ int plan_one_host(int n, int n_max, const uint8_t* adj, const int8_t* type, cons
 
 int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* n_joints,
                       const uint8_t* adj, const int8_t* type, const void* pos0, int pos_dtype,
-                      int32_t* status_out) {
+                      int32_t* status_out, const uint32_t* nbr) {
   PlanDev& p = plan->d;
   LINKS_CUDA(cudaMemsetAsync(p.ctrs, 0, kCtrs * sizeof(int32_t), ctx->stream));
   plan->B = B;
@@ -383,7 +385,7 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
     // geometry; measured faster at every n_max), or on request for n_max <= 8 a thread
     // per mechanism with its scratch in registers
     const int builder = tuning_of(ctx, p.n_max).builder;
-    const bool small = p.n_max <= 8 && builder == 1;
+    const bool small = p.n_max <= 8 && builder == 1 && !nbr;
     const bool vec = ((uintptr_t)pos0 & 15u) == 0 && ((uintptr_t)type & 15u) == 0 &&
                      (pos_dtype == LINKS_F64 || p.n_max % 2 == 0);
     const int flags = ((p.n_max % 4 == 0 && ((uintptr_t)adj & 3u) == 0) ? 1 : 0) | (vec ? 2 : 0);
@@ -393,7 +395,7 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
       if (small) {
         build_kernel<float, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
       } else {
-        int st = launch_flat<float>(ctx, fgrid, B, n_joints, adj, type, ps, p, status_out, flags);
+        int st = launch_flat<float>(ctx, fgrid, B, n_joints, adj, nbr, type, ps, p, status_out, flags);
         if (st) return st;
       }
     } else {
@@ -401,7 +403,7 @@ int plan_build_device(links_ctx ctx, links_plan plan, int64_t B, const int32_t* 
       if (small) {
         build_kernel<double, 8><<<grid, 256, 0, ctx->stream>>>(B, n_joints, adj, type, ps, p, status_out);
       } else {
-        int st = launch_flat<double>(ctx, fgrid, B, n_joints, adj, type, ps, p, status_out, flags);
+        int st = launch_flat<double>(ctx, fgrid, B, n_joints, adj, nbr, type, ps, p, status_out, flags);
         if (st) return st;
       }
     }

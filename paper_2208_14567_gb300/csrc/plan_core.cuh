@@ -123,7 +123,8 @@ LINKS_HD BuildOut out_of(const PlanDev& p, int64_t b) {
 
 // ---------------------------------------------------------------------------------------
 // Warp-flat builder: each warp builds 32 mechanisms.  The lanes first stage the warp's
-// neighbour masks (a lane per adjacency row, word loads issued in batches), joint types
+// neighbour masks (given as masks, or a lane per adjacency row, word loads issued in
+// batches), joint types
 // and (with STAGE) initial positions (vector loads) in shared memory; without STAGE the
 // positions are sent to L2 and the later phases read them through the cache, which
 // halves the warp's shared memory where staged positions would limit the resident warps
@@ -205,6 +206,7 @@ struct FlatResult {
 template <typename PT, bool NC = true, bool STAGE = true>
 __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, const int32_t* __restrict__ n_joints,
                                                       const uint8_t* __restrict__ adj,
+                                                      const uint32_t* __restrict__ nbr,
                                                       const int8_t* __restrict__ type, const PT* __restrict__ pos,
                                                       const PlanDev& p, int flags, char* wsmem, int lane) {
   const int NM = p.n_max, MD = p.max_dyads;
@@ -222,7 +224,13 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
 
   // 1. staging
   const int nrows = mc * NM;
-  if (flags & 1) {  // neighbour masks from whole words, two rows per lane in flight
+  if (nbr) {  // neighbour masks given: one coalesced word per (mechanism, joint)
+    const uint32_t* src = nbr + b0 * NM;
+    for (int r = lane; r < nrows; r += 32) {
+      const int mm = r / NM;
+      S.nb[(r - mm * NM) * 32 + mm] = ldro<NC>(src + r);
+    }
+  } else if (flags & 1) {  // neighbour masks from whole words, two rows per lane in flight
     const int W = NM >> 2;
     const uint8_t* blk = adj + b0 * NM * NM;
     for (int r0 = 0; r0 < nrows; r0 += 64) {

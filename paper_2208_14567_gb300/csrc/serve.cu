@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(kLoopThreads, 2) serve_loop_kernel(LoopArgs A)
                         ((((uintptr_t)pos & 15u) == 0 && ((uintptr_t)type & 15u) == 0 && nm % 2 == 0) ? 2 : 0);
       char* wsm = smem + warp * FlatSmem<float>::bytes(nm, md, true);
       for (int64_t t = gw; t < (B + 31) / 32; t += nw) {
-        const FlatResult r = build_flat_warp<float, false>(B, t * 32, nj, adj, type, pos, p, flags, wsm, lane);
+        const FlatResult r = build_flat_warp<float, false>(B, t * 32, nj, adj, nullptr, type, pos, p, flags, wsm, lane);
         if (r.status >= 0) {
           A.status[a + t * 32 + lane] = r.status;
           if (r.status == LINKS_MECH_OK) atomicAdd(&p.ctrs[kHist + r.nd], 1);

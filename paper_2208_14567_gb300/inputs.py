@@ -105,6 +105,18 @@ class MechBatch:
         idx = np.asarray(idx)
         return MechBatch(self.n_joints[idx], self.adj[idx], self.jtype[idx], self.pos[idx])
 
+    def masks(self, chunk: int = 1 << 18) -> np.ndarray:
+        """The adjacency as neighbour bit masks, uint32 [B, nmax]: bit c of row a set
+        when adj[a, c] is nonzero (the input of links_plan_build_masks)."""
+        B, n = self.B, self.nmax
+        out = np.zeros((B, n), dtype=np.uint32)
+        for lo in range(0, B, chunk):
+            bits = np.packbits(self.adj[lo:lo + chunk] != 0, axis=-1, bitorder="little")  # [b, n, ceil(n/8)]
+            words = np.zeros(bits.shape[:2] + (4,), dtype=np.uint8)
+            words[..., :bits.shape[-1]] = bits
+            out[lo:lo + chunk] = words.view("<u4")[..., 0]
+        return out
+
 
 def _positions(st: Stream, B: int, nmax: int, n_joints: np.ndarray, dtype) -> np.ndarray:
     b = np.arange(B, dtype=np.uint64)[:, None, None]

@@ -65,6 +65,7 @@ def lib():
             "links_plan_free": ([P], i32),
             "links_plan_build": ([P, P, i64, P, P, P, P, i32, P], i32),
             "links_plan_build_host": ([P, P, i64, P, P, P, P, i32, P], i32),
+            "links_plan_build_masks": ([P, P, i64, P, P, P, P, i32, P], i32),
             "links_plan_info": ([P, P, P, P], i32),
             "links_plan_export": ([P, i64, i64, P, P], i32),
             "links_simulate": ([P, P, i32, i32, i32, P, P, P, P, P, P, i64, P], i32),
@@ -211,6 +212,17 @@ def links_plan_build(ctx, plan, n_joints, adj, jtype, pos0, status_out=None):
                                   _dev(adj, torch.uint8, "adj"), _dev(jtype, torch.int8, "type"),
                                   _dev(pos0, None, "pos0"), _pos_dtype(pos0),
                                   _dev(status_out, torch.int32, "status_out")), "links_plan_build")
+
+
+def links_plan_build_masks(ctx, plan, n_joints, nbr, jtype, pos0, status_out=None):
+    """Device build from neighbour bit masks: nbr int32 [B, n] (bit c of row a: joints a
+    and c linked; the uint32 words viewed as int32), the rest as links_plan_build."""
+    import torch
+    B = n_joints.shape[0]
+    _check(lib().links_plan_build_masks(ctx, plan, int(B), _dev(n_joints, torch.int32, "n_joints"),
+                                        _dev(nbr, torch.int32, "nbr"), _dev(jtype, torch.int8, "type"),
+                                        _dev(pos0, None, "pos0"), _pos_dtype(pos0),
+                                        _dev(status_out, torch.int32, "status_out")), "links_plan_build_masks")
 
 
 def links_plan_build_host(ctx, plan, n_joints, adj, jtype, pos0, status_out=None):

@@ -152,6 +152,28 @@ def test_device_and_host_plans_simulate_identically(L, n_lo, n_hi, nmax, f64, bu
           f"statuses {sorted(set(a['status'].tolist()))}")
 
 
+@pytest.mark.parametrize("n_lo,n_hi,nmax,f64", [(6, 8, 8, False), (6, 20, 20, True), (6, 20, 20, False),
+                                              (3, 6, 32, False), (5, 15, 15, False)])
+def test_mask_build_equals_byte_build(L, n_lo, n_hi, nmax, f64):
+    """links_plan_build_masks (the adjacency as neighbour bit masks) and links_plan_build
+    (uint8 matrix) give the same plans: statuses and every output of a mixed simulation
+    identical to the bit, the planted ill-formed mechanisms included."""
+    from paper_2208_14567_gb300.api import Simulator, to_device
+    batch = planted_bad(I.dyad_batch(4000, n_lo, n_hi, seed=7 * nmax, permute=True, nmax=nmax,
+                                     pos_dtype=np.float64 if f64 else np.float32))
+    res = []
+    for masks in (False, True):
+        with Simulator(batch.B, batch.nmax) as s:
+            st = s.build(to_device(batch, masks=masks))
+            o = s.simulate(64, L.MIXED, L.OUT_FULL)
+            s.sync()
+            res.append({"status": st.cpu().numpy(),
+                        **{k: getattr(o, k).cpu().numpy() for k in ("valid", "lock_step", "min_disc", "traj", "path")}})
+    for k in res[0]:
+        assert np.array_equal(res[0][k], res[1][k], equal_nan=True), k
+    assert len(set(res[0]["status"].tolist())) >= 7
+
+
 def test_plan_matches_oracle_device_and_host(L):
     from paper_2208_14567_gb300.api import Simulator, to_device
     batch = planted_bad(I.dyad_batch(3000, 6, 16, seed=2, permute=True, nmax=20))

@@ -156,3 +156,15 @@ def test_paper_batch_reproduces_the_papers_infeasibility_scale(oracle_lib):
     arm = b.pos[:, 1].astype(np.float64) - b.pos[:, 0]
     assert np.allclose(arm, [0.05, 0.0], atol=1e-7)
     assert np.ptp(b.pos[:, 2:].reshape(-1, 2), axis=0).min() > 0.2  # the other joints spread over the box
+
+
+def test_adjacency_masks_are_the_adjacency_bits():
+    """MechBatch.masks(): bit c of row a is set exactly where adj[a, c] is nonzero, for
+    n_max 8, 20 and 32 (the top bit), across chunk boundaries."""
+    for lo, hi, nmax in ((6, 8, 8), (6, 20, 20), (3, 6, 32)):
+        b = I.dyad_batch(700, lo, hi, seed=nmax, nmax=nmax)
+        b.adj[3, 0, nmax - 1] = 7  # any nonzero byte is a link
+        m = b.masks(chunk=256)
+        want = ((b.adj != 0).astype(np.uint64) << np.arange(nmax, dtype=np.uint64)).sum(-1)
+        assert m.dtype == np.uint32 and m.shape == (b.B, nmax)
+        assert np.array_equal(m.astype(np.uint64), want)
