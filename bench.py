@@ -588,7 +588,11 @@ def serve_stage(args, local, stream):
     try:
         L.links_serve_start(ctx, args.serve_budget << 30, 256, NM, T)
         poisson = run(True)
-        saturation = run(False)
+        # back-to-back offers depend on host thread scheduling from run to run: three runs,
+        # the one with the median wall time reported, every run's figures beside it
+        sats = sorted((run(False) for _ in range(3)), key=lambda r: r["wall_s"])
+        saturation = dict(sats[1])
+        saturation["runs"] = [{k: r[k] for k in ("wall_s", "p50_ms", "p99_ms", "mechanism_steps_per_s")} for r in sats]
         stats = L.links_serve_stats(ctx)
         L.links_serve_stop(ctx)
     finally:
