@@ -419,8 +419,7 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
             if constexpr (DWS) return LocShared{Pb, Yb};
             else return LocLocal{lbuf};
           }();
-          float qd;
-          bool lk = dw_chain(h, Fb, rec, csv, loc, &qd);
+          bool lk = dw_chain(h, Fb, rec, csv, loc, nullptr);  // no minimum q: the screen has it
           if (lk) atomicOr(err, kErrEmitLock);
           for (int s = 0; s < nslot; ++s) {
             const dwp ls = slot_pos(loc, Fb, nf, s);

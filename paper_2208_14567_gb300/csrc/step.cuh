@@ -82,7 +82,8 @@ __device__ __forceinline__ dwp slot_pos(const Loc& loc, const float4* fix, int n
 
 // Double-word chain of one step into loc[slot], relative to the pivot.  fix holds the
 // fixed slots as (x_h, x_l, y_h, y_l).
-// Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before.
+// Returns true if a dyad locks (D <= 0); *qmin = min q over the dyads solved before
+// (qmin may be NULL: the emit needs no q).
 // Inlined: as a call it cost the emit 12% (argument passing and saved registers
 // around it).
 template <class Loc>
@@ -109,10 +110,10 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
     dw e = dw_add(d2, dw{c_h, r2.z});
     dw D = dw_4ab_minus_sq(d2, dw{r2.x, r2.y}, e);
     if (!(dw_sign(D) > 0.0f)) {
-      *qmin = q;
+      if (qmin) *qmin = q;
       return true;
     }
-    q = fminf(q, __fdividef(D.h, w2 * w2));
+    if (qmin) q = fminf(q, __fdividef(D.h, w2 * w2));
     dw sq = dw_sqrt(D);
     dw hinv = dw_scale2(dw_rcp(d2), 0.5f);
     dw a = dw_mul(e, hinv), bq = dw_mul(sq, hinv);
@@ -121,7 +122,7 @@ __device__ __forceinline__ bool dw_chain(const MechHdr& h, const float4* fix, co
     pk.y = dw_axpby(pi.y, a, dy_, bq, dx, 1.0f);
     loc.set(sl >> 24, pk);
   }
-  *qmin = q;
+  if (qmin) *qmin = q;
   return false;
 }
 
