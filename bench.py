@@ -627,8 +627,8 @@ def serve_stage(args, local, stream):
 
 def profile_kernels(args):
     """One launch of each hot kernel on a mid-size case, in a fixed order, for a profiler
-    (no timing): plan build, screen and emit (packed valid rows) of args.batch dyad-built
-    candidates of 6 to args.profile_nmax joints, with the kernel shapes the autotuner
+    (no timing): plan build (from neighbour masks), screen and emit (packed valid rows) of
+    args.batch dyad-built candidates of 6 to args.profile_nmax joints, with the kernel shapes the autotuner
     picks on the full configuration of that n_max (set explicitly, so no tuning launches
     come first); then, for n_max 8, max-line normalisation of their valid coupler paths,
     curation of their trajectories, a first-3 scan of 16 queries over those paths, and
@@ -642,7 +642,7 @@ def profile_kernels(args):
     T, B, nm = args.T, args.batch, args.profile_nmax
     dev = torch.device("cuda", 0)
     batch = I.dyad_batch(B, 6, nm, seed=0, nmax=nm)
-    db = to_device(batch, dev)
+    db = to_device(batch, dev, masks=True)  # as the headline configurations
     shapes = {20: {"screen_lanes": 16, "screen_steps": 1, "screen_defer": 1}}.get(nm, {})
     with Simulator(B, nm) as s:
         for k, v in shapes.items():
@@ -659,7 +659,8 @@ def profile_kernels(args):
             L.links_normalize_maxline(s.ctx, paths, ml)
             flags = torch.empty((nv, 8), dtype=torch.uint8, device=dev)
             nk = torch.empty(1, dtype=torch.int32, device=dev)
-            L.links_curate_paths(s.ctx, traj, rows, db.n_joints, db.adj, db.jtype, flags, nk)
+            adj = torch.from_numpy(batch.adj).to(dev)  # curation reads the uint8 matrix
+            L.links_curate_paths(s.ctx, traj, rows, db.n_joints, adj, db.jtype, flags, nk)
             q = ml[:16].clone()
             order = torch.randperm(nv, generator=torch.Generator().manual_seed(5)).to(torch.int32).to(dev)
             idx = torch.empty((16, 3), dtype=torch.int32, device=dev)
