@@ -475,8 +475,17 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       bnd[(nf + 1 + d) * 32 + m] = bk;
       bmax = fmaxf(bmax, bk);
     }
-    for (int a = 0; a < n; ++a)
-      o.pos64[S.slot[a * 32 + m]] = make_double2((double)posv(m, 2 * a), (double)posv(m, 2 * a + 1));
+    // the FP64 positions by slot and, from the same loads, the bounding box
+    float lo_x = INFINITY, hi_x = -INFINITY, lo_y = INFINITY, hi_y = -INFINITY;
+    for (int a = 0; a < n; ++a) {
+      const PT px = posv(m, 2 * a), py = posv(m, 2 * a + 1);
+      o.pos64[S.slot[a * 32 + m]] = make_double2((double)px, (double)py);
+      const float x = (float)px, y = (float)py;
+      lo_x = fminf(lo_x, x);
+      hi_x = fmaxf(hi_x, x);
+      lo_y = fminf(lo_y, y);
+      hi_y = fmaxf(hi_y, y);
+    }
     MechHdr h{};
     h.n = (uint8_t)n;
     h.status = status;
@@ -491,14 +500,6 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
     const dw px = abs_dw(pv, 0), py = abs_dw(pv, 1);
     h.px_h = px.h; h.px_l = px.l; h.py_h = py.h; h.py_l = py.l;
     h.bmax = bmax;
-    float lo_x = (float)posv(m, 0), hi_x = lo_x, lo_y = (float)posv(m, 1), hi_y = lo_y;
-    for (int a = 1; a < n; ++a) {
-      const float x = (float)posv(m, 2 * a), y = (float)posv(m, 2 * a + 1);
-      lo_x = fminf(lo_x, x);
-      hi_x = fmaxf(hi_x, x);
-      lo_y = fminf(lo_y, y);
-      hi_y = fmaxf(hi_y, y);
-    }
     h.lbox = hyp_up(fsub(hi_x, lo_x), fsub(hi_y, lo_y));
     h.e_motor = fmul(4.0f * kU, crank);
     h.e_fixed = fmul(kU, bmax);
