@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(256) build_kernel(int64_t B, const int32_t* __
 // Warp-flat builder kernel: each warp builds the 32 mechanisms from b0 = 32 x its global
 // warp index (build_flat_warp in plan_core.cuh).
 template <typename PT, bool STAGE>
-__global__ void __launch_bounds__(32 * kFlatWarps) build_flat_kernel(int64_t B, const int32_t* __restrict__ n_joints,
+__global__ void __launch_bounds__(32 * kFlatWarps, 8) build_flat_kernel(int64_t B, const int32_t* __restrict__ n_joints,
                                                                       const uint8_t* __restrict__ adj,
                                                                       const uint32_t* __restrict__ nbr,
                                                                       const int8_t* __restrict__ type,

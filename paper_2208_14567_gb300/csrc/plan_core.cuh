@@ -469,11 +469,22 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
 
   // 4. lane m: the bound chain in solve order, the FP64 positions, the header
   if (status == LINKS_MECH_OK) {
-    for (int d = 0; d < nd; ++d) {
-      const float2 rr = *reinterpret_cast<const float2*>(o.pos64 + nf + 1 + d);
-      const float bk = dyad_bound(bnd[S.di[d * 32 + m] * 32 + m], bnd[S.dj[d * 32 + m] * 32 + m], rr.x, rr.y);
-      bnd[(nf + 1 + d) * 32 + m] = bk;
-      bmax = fmaxf(bmax, bk);
+    // the link lengths four dyads at a time, their loads issued before the chain uses them
+    for (int d0 = 0; d0 < nd; d0 += 4) {
+      float2 rr[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (d0 + u < nd) rr[u] = *reinterpret_cast<const float2*>(o.pos64 + nf + 1 + d0 + u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int d = d0 + u;
+        if (d < nd) {
+          const float bk = dyad_bound(bnd[S.di[d * 32 + m] * 32 + m], bnd[S.dj[d * 32 + m] * 32 + m], rr[u].x,
+                                      rr[u].y);
+          bnd[(nf + 1 + d) * 32 + m] = bk;
+          bmax = fmaxf(bmax, bk);
+        }
+      }
     }
     // the FP64 positions by slot and, from the same loads, the bounding box
     float lo_x = INFINITY, hi_x = -INFINITY, lo_y = INFINITY, hi_y = -INFINITY;
