@@ -637,7 +637,7 @@ int links_get_tuning(links_ctx ctx, int n_max, int key, int* value) {
   return LINKS_OK;
 }
 
-// Text file: a header naming the device, then one line per n_max with the six keys.
+// Text file: a header naming the device, then one line per n_max with its seven keys.
 int links_tuning_save(links_ctx ctx, const char* path) {
   if (!ctx || !path) return set_error(LINKS_EINVAL, "links_tuning_save: NULL argument");
   cudaDeviceProp prop;
