@@ -335,12 +335,26 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
   }
   const uint32_t live = n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
   auto nbm = [&](int a) { return S.nb[a * 32 + m] & live; };
-  if (status == LINKS_MECH_OK) {  // no self-loop, and every link listed both ways
+  // One pass over the masks: no self-loop and every link listed both ways; the link
+  // count (e2 / 2, less the ground-ground links, ff2 / 2) for the mobility check below;
+  // and the running counts of known neighbours (has1 / has2 / has3, see the search) from
+  // the fixed and actuated joints.
+  const uint32_t known0 = fixm | motm;
+  uint32_t has1 = 0, has2 = 0, has3 = 0;
+  int e2 = 0, ff2 = 0;
+  if (status == LINKS_MECH_OK) {
     uint32_t asym = 0;
     for (int a = 0; a < n; ++a) {
       const uint32_t na = nbm(a);
       asym |= na & (1u << a);
       for (uint32_t q = na; q; q &= q - 1) asym |= ~nbm(ffs32(q)) & (1u << a);
+      e2 += popc32(na);
+      if ((fixm >> a) & 1u) ff2 += popc32(na & fixm);
+      if ((known0 >> a) & 1u) {
+        has3 |= has2 & na;
+        has2 |= has1 & na;
+        has1 |= na;
+      }
     }
     if (asym) status = LINKS_MECH_BAD_ADJ;
   }
@@ -355,13 +369,7 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
     // The search of build_one (the lowest-index unknown joint with >= 2 known neighbours;
     // > 2 is over-constraint) on running counts: has1 / has2 / has3 mark the joints with
     // at least 1 / 2 / 3 known neighbours, updated from each newly known joint's mask.
-    uint32_t known = fixm | motm, unknown = simm, has1 = 0, has2 = 0, has3 = 0;
-    for (uint32_t q = known; q; q &= q - 1) {
-      const uint32_t nbq = nbm(ffs32(q));
-      has3 |= has2 & nbq;
-      has2 |= has1 & nbq;
-      has1 |= nbq;
-    }
+    uint32_t known = known0, unknown = simm;
     while (unknown) {
       const uint32_t ready = has2 & unknown;
       if (!ready) { status = LINKS_MECH_NOT_DYAD_SOLVABLE; break; }
@@ -380,14 +388,7 @@ __device__ __forceinline__ FlatResult build_flat_warp(int64_t B, int64_t b0, con
       has1 |= nbp;
     }
   }
-  if (status == LINKS_MECH_OK) {
-    int e2 = 0, ff2 = 0;
-    for (int a = 0; a < n; ++a) {
-      e2 += popc32(nbm(a));
-      if ((fixm >> a) & 1u) ff2 += popc32(nbm(a) & fixm);
-    }
-    if ((e2 - ff2) / 2 - 1 != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
-  }
+  if (status == LINKS_MECH_OK && (e2 - ff2) / 2 - 1 != 2 * popc32(simm)) status = LINKS_MECH_OVERCONSTRAINED;
   // every lane reads only its own column of the masks, whose words now hold slot bounds
   float* const bnd = reinterpret_cast<float*>(S.nb);
   const BuildOut o = out_of(p, b);
