@@ -331,7 +331,7 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
                                           int64_t out_capacity, float* __restrict__ traj, float* __restrict__ path,
                                           int32_t* err, char* smem, int* jofs, int warp, int lane, int64_t gw,
                                           int64_t nw, const int64_t* __restrict__ row_off = nullptr,
-                                          int64_t traj_cap = 0) {
+                                          int64_t traj_cap = 0, int32_t* work = nullptr) {
   const int ns = p.n_max;
   const int slot_bytes = DWS ? kEmitSlotBytesDW : kEmitSlotBytes;
   char* const region = smem + (size_t)warp * emit_warp_bytes(ns, p.max_dyads, DWS);
@@ -343,7 +343,16 @@ __device__ __forceinline__ void emit_body(const PlanDev& p, int64_t B, int T, co
   int64_t rows = full ? B : min((int64_t)p.ctrs[kNValid], out_capacity);
   const float nanf_ = __int_as_float(0x7fc00000);
   unsigned n_steps = 0, n_dw = 0, n_dw_dyads = 0;  // census counts of this lane
-  for (int64_t r = gw; r < rows; r += nw) {
+  // rows taken one at a time from the work counter (rows that go to double-word cost a few
+  // times more, and a fixed assignment leaves the launch waiting on the unluckiest warp),
+  // or, without one, every nw-th row
+  const auto next_row = [&](int64_t r) -> int64_t {
+    if (!work) return r + nw;
+    int v = 0;
+    if (lane == 0) v = atomicAdd(work, 1);
+    return (int64_t)__shfl_sync(kFull, v, 0);
+  };
+  for (int64_t r = work ? next_row(0) : gw; r < rows; r = next_row(r)) {
     const int64_t b = full ? r : (int64_t)out_index[r];
     if (b < 0 || b >= B) {
       if (lane == 0) atomicOr(err, kErrBadIndex);

@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kBlock) emit_kernel(PlanDev p, int64_t B, int 
   emit_body<CENSUS, DWS>(p, B, T, cs, full, lock_step, out_index, out_capacity, traj, path, err,
                          reinterpret_cast<char*>(smem4), s_jofs[warp], warp, threadIdx.x & 31,
                          ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5,
-                         ((int64_t)gridDim.x * blockDim.x) >> 5, row_off, traj_cap);
+                         ((int64_t)gridDim.x * blockDim.x) >> 5, row_off, traj_cap, p.ctrs + kWork2);
 }
 
 // Shapes of the screen: lanes per mechanism G, steps per lane S, CTAs per SM (0 = as many
@@ -206,6 +206,7 @@ int launch_emit(links_ctx ctx, links_plan plan, const TTable* tab, bool full, co
   LINKS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBlock, smem));
   if (sh.ctas > 0 && sh.ctas < per_sm) per_sm = sh.ctas;
   if (per_sm < 1) per_sm = 1;
+  LINKS_CUDA(cudaMemsetAsync(plan->d.ctrs + kWork2, 0, sizeof(int32_t), ctx->stream));
   KernelScope ks(ctx, name);
   kern<<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(plan->d, plan->B, tab->T, tab->cs, full ? 1 : 0,
                                                             lock_step, out_index, out_capacity, traj, path,
