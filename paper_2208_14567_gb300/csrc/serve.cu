@@ -357,7 +357,8 @@ __global__ void __launch_bounds__(kLoopThreads, 2) serve_loop_kernel(LoopArgs A)
     if (!grid_wait(c, nb, 0, wait, A.mb)) return;
     // 5. the coupler paths (and trajectories) of the valid rows
     emit_body<false, DWS, false>(p, B, T, A.cs, 0, lock, idx, B, A.traj ? A.traj + a * nm * T * 2 : nullptr, path,
-                                 &c->emit_err, smem, s_jofs[warp], warp, lane, gw, nw);
+                                 &c->emit_err, smem, s_jofs[warp], warp, lane, gw, nw, nullptr, 0,
+                                 p.ctrs + kWork2);  // rows from a counter (the setup cleared it)
     if (!grid_wait(c, nb, 0, wait, A.mb)) return;
     // 6. their normalisation
     {
