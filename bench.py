@@ -49,10 +49,10 @@ SCREEN_STEP_OPS = 6    # FP32 crank rotation, per step
 # The bound each hot kernel's ncu counters show (profiles/), and where it is read.
 BINDING = {"mixed_emit": "hbm", "mixed_screen": "alu", "plan_build": "hbm"}
 BINDING_EVIDENCE = {
-    "mixed_emit": "profiles/screen_emit_build_300k_6-8_full.md: emit issue active 73% vs DRAM 31-35% of peak "
+    "mixed_emit": "profiles/screen_emit_build_300k_6-8_full.md: emit issue active 83% vs DRAM 39% of peak "
                   "(packed rows); the HBM view counts only the real joints' bytes, the ALU view beside it",
-    "mixed_screen": "profiles/screen_emit_build_300k_6-20_full.md: screen issue active 71%, DRAM 8.7% of peak, "
-                    "FMA 32% / ALU 37% pipe: instruction issue binds",
+    "mixed_screen": "profiles/screen_emit_build_300k_6-20_full.md and ..._6-8_full.md: screen issue active "
+                    "71% / 76%, DRAM 9% / 5% of peak: instruction issue binds",
     "plan_build": "profiles/screen_emit_build_300k_6-20_full.md: issue 45%, 29% of warps active (shared-memory "
                   "limit), long-scoreboard 2.7 per issue: latency-bound",
 }
@@ -61,9 +61,9 @@ BINDING_EVIDENCE = {
 # `bench.py --profile-kernels`), scaled to the launch by the units it processes.
 TRAFFIC_PER_UNIT = {
     ("config3_4M_6-20", "mixed_screen"): ((230.391 + 4.051 + 18.461 + 0.215) * 1e6 / 300000, "candidate"),
-    ("config3_4M_6-20", "mixed_emit"): ((19.811 + 364.924) * 1e6 / 24132, "row"),
+    ("config3_4M_6-20", "mixed_emit"): ((19.815 + 370.823) * 1e6 / 24132, "row"),
     ("config2_1M_6-8", "mixed_screen"): ((144.411 + 4.927) * 1e6 / 300000, "candidate"),
-    ("config2_1M_6-8", "mixed_emit"): ((45.407 + 865.231) * 1e6 / 74163, "row"),
+    ("config2_1M_6-8", "mixed_emit"): ((44.602 + 865.002) * 1e6 / 74163, "row"),
 }
 E2E_WARMUP = 3  # untimed pipelined steps before the end-to-end timing
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of a smaller capture, scaled per unit"
