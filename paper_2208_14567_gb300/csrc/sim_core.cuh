@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kBatch = 16;  // work items taken per atomic by a warp
+constexpr int kBatch = 16;  // work items taken per atomic by a warp (up to 32)
 constexpr int kEmitSlotBytes = 400;
 constexpr int kEmitSlotBytesDW = 656;
 constexpr int kEmitSharedDWMaxSlots = 12;
@@ -109,7 +109,8 @@ template <int G, int S, bool RESCUE, bool NC = true>
 __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float4* __restrict__ cs,
                                             uint8_t* __restrict__ valid, int16_t* __restrict__ lock_step,
                                             float* __restrict__ min_disc, const int32_t* __restrict__ order,
-                                            const int32_t* __restrict__ n_list, char* smem, int warp, int lane) {
+                                            const int32_t* __restrict__ n_list, char* smem, int warp, int lane,
+                                            int batch = kBatch) {
   const int ns = p.n_max;
   const int g = lane / G, gl = lane % G;
   const int rstride = 2 * p.max_dyads + 1;  // float4 per group: (r0, r1) per dyad, padded
@@ -146,7 +147,7 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
   }
 
   int qhead = 0, qend = 0, qbase = 0;
-  int32_t qb = 0;  // lane i < kBatch: the mechanism of the batch's item i (item qbase + i)
+  int32_t qb = 0;  // lane i < batch: the mechanism of the batch's item i (item qbase + i)
   bool exhausted = false;
   int item = -1, chunk = 0;
   int64_t b = 0;
@@ -163,11 +164,11 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
       if (qhead >= qend) {
         if (exhausted) break;
         int base = 0;
-        if (lane == 0) base = atomicAdd(&p.ctrs[kWork], kBatch);
+        if (lane == 0) base = atomicAdd(&p.ctrs[kWork], batch);
         base = __shfl_sync(kFull, base, 0);
         if (base >= n_ok) { exhausted = true; break; }
         qhead = qbase = base;
-        qend = min(base + kBatch, n_ok);
+        qend = min(base + batch, n_ok);
         // the batch's mechanisms, a lane each, and their header, dyad records and fixed
         // joints on their way to L2 (the groups take them over the next chunks).  On the
         // sorted list an item's dyad count is its bucket: the last lane whose prefix

@@ -35,10 +35,10 @@ __global__ void __launch_bounds__(kBlock, 4) screen_kernel(PlanDev p, int T, con
                                                         int16_t* __restrict__ lock_step,
                                                         float* __restrict__ min_disc,
                                                         const int32_t* __restrict__ order,
-                                                        const int32_t* __restrict__ n_list) {
+                                                        const int32_t* __restrict__ n_list, int batch) {
   extern __shared__ float4 smem4[];
   screen_body<G, S, RESCUE>(p, T, cs, valid, lock_step, min_disc, order, n_list, reinterpret_cast<char*>(smem4),
-                            threadIdx.x >> 5, threadIdx.x & 31);
+                            threadIdx.x >> 5, threadIdx.x & 31, batch);
 }
 
 template <bool CENSUS, bool DWS>
@@ -84,7 +84,7 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   if (!defer) {
     KernelScope ks(ctx, "mixed_screen");
     screen_kernel<G, S, true><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
-        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list);
+        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list, kBatch);
     LINKS_CUDA(cudaGetLastError());
     return LINKS_OK;
   }
@@ -92,14 +92,15 @@ int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint
   {
     KernelScope ks(ctx, "mixed_screen");
     screen_kernel<G, S, false><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
-        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list);
+        p, T, tab->cs, valid, lock_step, min_disc, order ? order : p.order, n_list, kBatch);
   }
   LINKS_CUDA(cudaGetLastError());
   LINKS_CUDA(cudaMemsetAsync(p.ctrs + kWork, 0, sizeof(int32_t), ctx->stream));
   {
     KernelScope ks(ctx, "mixed_screen_rescue");
+    // The rescue list is short and unsorted: one item per atomic keeps the warps' tails even.
     screen_kernel<G, S, true><<<ctx->num_sms * per_sm, kBlock, smem, ctx->stream>>>(
-        p, T, tab->cs, valid, lock_step, min_disc, p.rescue, p.ctrs + kNRescue);
+        p, T, tab->cs, valid, lock_step, min_disc, p.rescue, p.ctrs + kNRescue, 1);
   }
   LINKS_CUDA(cudaGetLastError());
   return LINKS_OK;
