@@ -204,7 +204,7 @@ __host__ __device__ PlanDev plan_view(const PlanDev& p, int64_t a) {
 
 size_t loop_smem_bytes(int nm, int md, int G, bool dws) {
   const size_t build = (size_t)kLoopWarps * FlatSmem<float>::bytes(nm, md, true);
-  const size_t screen = (size_t)kLoopWarps * ((size_t)nm * 384 + (32 / G) * (2 * md + 1) * 16);
+  const size_t screen = (size_t)kLoopWarps * screen_warp_bytes(nm, md, G, 1);
   const size_t emit = (size_t)kLoopWarps * emit_warp_bytes(nm, md, dws);
   return std::max(build, std::max(screen, emit));
 }

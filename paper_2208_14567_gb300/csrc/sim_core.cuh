@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kBatch = 16;  // work items taken per atomic by a warp (up to 32)
+constexpr int kBatch = 16;  // work items taken per atomic by a warp (at most)
 constexpr int kEmitSlotBytes = 400;
 constexpr int kEmitSlotBytesDW = 656;
 constexpr int kEmitSharedDWMaxSlots = 12;
@@ -21,6 +21,11 @@ constexpr int kEmitSharedDWMaxSlots = 12;
 // dyad).
 __host__ __device__ constexpr size_t emit_warp_bytes(int n_max, int max_dyads, bool dws) {
   return (size_t)n_max * (dws ? kEmitSlotBytesDW : kEmitSlotBytes) + (size_t)max_dyads * 48;
+}
+// Shared memory of one screen warp: the slot arrays (384 B per slot and step of a lane)
+// and the dyad records of its groups.
+__host__ __device__ constexpr size_t screen_warp_bytes(int n_max, int max_dyads, int G, int S) {
+  return (size_t)n_max * 384 * S + (size_t)(32 / G) * (2 * max_dyads + 1) * 16;
 }
 // Two steps per lane save record loads but double the slot arrays in shared memory;
 // they pay for small mechanisms only (4 CTAs per SM still fit).
@@ -114,7 +119,7 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
   const int ns = p.n_max;
   const int g = lane / G, gl = lane % G;
   const int rstride = 2 * p.max_dyads + 1;  // float4 per group: (r0, r1) per dyad, padded
-  char* const region = smem + (size_t)warp * (ns * 384 * S + (32 / G) * rstride * 16);
+  char* const region = smem + (size_t)warp * screen_warp_bytes(ns, p.max_dyads, G, S);
   // one step per lane: positions (float2) at Pb + 256 * slot, bounds (float) at
   // Eb + 128 * slot; two steps per lane: both steps' positions (float4) at P2 + 512 *
   // slot, their bounds (float2) at E2 + 256 * slot
@@ -148,12 +153,12 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
 
   int qhead = 0, qend = 0, qbase = 0;
   int32_t qb = 0;  // lane i < batch: the mechanism of the batch's item i (item qbase + i)
+  int qw = 0;      // ... and its header's counts word (n, nd, nf, motor joint)
   bool exhausted = false;
   int item = -1, chunk = 0;
-  int64_t b = 0;
+  int32_t b = 0;
   int nd = 0, nf = 0;
   float ux = 0.f, uy = 0.f, e_motor = 0.f;
-  const DyadRec* rec = p.dyad;
   float qacc = INFINITY;
 
   while (true) {
@@ -169,10 +174,11 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
         if (base >= n_ok) { exhausted = true; break; }
         qhead = qbase = base;
         qend = min(base + batch, n_ok);
-        // the batch's mechanisms, a lane each, and their header, dyad records and fixed
-        // joints on their way to L2 (the groups take them over the next chunks).  On the
-        // sorted list an item's dyad count is its bucket: the last lane whose prefix
-        // does not exceed the item's position.
+        // the batch's mechanisms, a lane each, with their header's counts word in a register
+        // (a group that takes an item starts its record loads without waiting on the
+        // header), their dyad records and fixed joints on their way to L2.  On the sorted
+        // list an item's dyad count is its bucket: the last lane whose prefix does not
+        // exceed the item's position.
         int ndq = p.max_dyads;
         if (!n_list) {
           const int q = n_ok - 1 - (qbase + lane);
@@ -186,6 +192,7 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
         }
         if (lane < qend - qbase) {
           qb = ldro<NC>(order + (n_list ? qbase + lane : n_ok - 1 - (qbase + lane)));
+          qw = ldro<NC>(reinterpret_cast<const int*>(p.hdr + qb) + 1);
           prefetch_l2(p.hdr + qb);
           const char* r0 = reinterpret_cast<const char*>(p.dyad + (int64_t)qb * p.max_dyads);
           for (int o = 0; o < ndq * (int)sizeof(DyadRec); o += 128) prefetch_l2(r0 + o);
@@ -195,26 +202,31 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
       int leader = __ffs(need) - 1;
       need &= need - 1;
       const int32_t bsel = __shfl_sync(kFull, qb, qhead - qbase);
-      if (g == leader / G) { item = qhead; b = bsel; fresh = true; }
+      const int wsel = __shfl_sync(kFull, qw, qhead - qbase);
+      if (g == leader / G) {
+        item = qhead;
+        b = bsel;
+        fresh = true;
+        nd = (wsel >> 8) & 0xff;
+        nf = (wsel >> 16) & 0xff;
+      }
       ++qhead;
     }
     if (__ballot_sync(kFull, item >= 0) == 0) break;
     __syncwarp();  // the previous mechanism's records are no longer read
 
     if (fresh) {
-      const MechHdr* hp = p.hdr + b;
-      const int4 w0 = ldro<NC>(reinterpret_cast<const int4*>(hp));
-      nd = (w0.y >> 8) & 0xff;
-      nf = (w0.y >> 16) & 0xff;
-      ux = ldro<NC>(&hp->ux_h);
-      uy = ldro<NC>(&hp->uy_h);
-      e_motor = ldro<NC>(&hp->e_motor);
-      const float e_fixed = ldro<NC>(&hp->e_fixed);
-      rec = p.dyad + b * p.max_dyads;
+      const DyadRec* const rec = p.dyad + (int64_t)b * p.max_dyads;
       chunk = 0;
       qacc = INFINITY;
+      const MechHdr* hp = p.hdr + b;
+      ux = ldro<NC>(&hp->ux_h);
+      uy = ldro<NC>(&hp->uy_h);
+      const float2 eb = ldro<NC>(reinterpret_cast<const float2*>(&hp->e_motor));  // e_motor, e_fixed
+      e_motor = eb.x;
+      const float e_fixed = eb.y;
       for (int x = gl; x < 2 * nd; x += G) Rg[x] = ldro<NC>(x & 1 ? &rec[x >> 1].r1 : &rec[x >> 1].r0);
-      const float4* fix = p.fixpos + b * ns;
+      const float4* fix = p.fixpos + (int64_t)b * ns;
       for (int s = 0; s < nf; ++s) {
         float4 f = ldro<NC>(fix + s);
         if (S == 2) {
@@ -273,7 +285,8 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
       if (RESCUE && amb) {
         dwp loc[kMaxJ];
         float qd;
-        locked = dw_chain(p.hdr[b], p.fixpos + b * ns, rec, __ldg(cs + t), LocLocal{loc}, &qd);
+        locked = dw_chain(p.hdr[b], p.fixpos + (int64_t)b * ns, p.dyad + (int64_t)b * p.max_dyads, __ldg(cs + t),
+                          LocLocal{loc}, &qd);
         qstep[u] = qd;
       }
       const unsigned lb = __ballot_sync(kFull, locked) & gmask;
@@ -285,7 +298,7 @@ __device__ __forceinline__ void screen_body(const PlanDev& p, int T, const float
     }
     // an uncertain step that decides (group-uniform): leave the mechanism to the rescue
     const bool defer = !RESCUE && has && first_amb < first;
-    if (defer && gl == 0) p.rescue[atomicAdd(&p.ctrs[kNRescue], 1)] = (int32_t)b;
+    if (defer && gl == 0) p.rescue[atomicAdd(&p.ctrs[kNRescue], 1)] = b;
 #pragma unroll
     for (int u = 0; u < S; ++u) {
       const int t = chunk * CH + u * G + gl;

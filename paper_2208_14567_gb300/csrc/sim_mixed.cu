@@ -71,7 +71,7 @@ template <int G, int S>
 int launch_screen(links_ctx ctx, links_plan plan, int T, const TTable* tab, uint8_t* valid, int16_t* lock_step,
                   float* min_disc, const int32_t* order, const int32_t* n_list, int ctas, bool defer) {
   PlanDev& p = plan->d;
-  size_t smem = (size_t)kWarps * (p.n_max * 384 * S + (32 / G) * (2 * p.max_dyads + 1) * 16);
+  size_t smem = (size_t)kWarps * screen_warp_bytes(p.n_max, p.max_dyads, G, S);
   // a function attribute of the current device's context: set on every launch (a host
   // call, no stream work), so other devices and contexts get it too
   LINKS_CUDA(cudaFuncSetAttribute(screen_kernel<G, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
