@@ -60,9 +60,9 @@ BINDING_EVIDENCE = {
 # ncu capture of the same kernel and shapes on the same recipe (300,000 candidates,
 # `bench.py --profile-kernels`), scaled to the launch by the units it processes.
 TRAFFIC_PER_UNIT = {
-    ("config3_4M_6-20", "mixed_screen"): ((230.391 + 4.051 + 18.461 + 0.215) * 1e6 / 300000, "candidate"),
+    ("config3_4M_6-20", "mixed_screen"): ((229.991 + 3.142 + 39.917 + 2.173) * 1e6 / 300000, "candidate"),
     ("config3_4M_6-20", "mixed_emit"): ((19.815 + 370.823) * 1e6 / 24132, "row"),
-    ("config2_1M_6-8", "mixed_screen"): ((144.411 + 4.927) * 1e6 / 300000, "candidate"),
+    ("config2_1M_6-8", "mixed_screen"): ((143.398 + 3.921) * 1e6 / 300000, "candidate"),
     ("config2_1M_6-8", "mixed_emit"): ((44.602 + 865.002) * 1e6 / 74163, "row"),
 }
 E2E_WARMUP = 3  # untimed pipelined steps before the end-to-end timing
