@@ -8,9 +8,16 @@
 
 namespace links {
 
-__device__ __forceinline__ float min_nan(float a, float b) {  // NaN-propagating
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ float min3_nan(float a, float b, float c) {  // NaN-propagating
+  // two two-input minima: the three-input NaN-propagating form is not one instruction
   float r;
   asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(r), "f"(c));
   return r;
 }
 
@@ -44,13 +51,8 @@ __device__ __forceinline__ void fp32_dyad_core(float pix, float piy, float pjx, 
   const float rD = rsqrt_ftz(D);
   const float isg = __fmul_rn(r1.x, rD);
   const float del = __fadd_rn(__fadd_rn(ei, ej), r1.y);
-  // Rounding is monotone, so min(s2, s3) + del rounds to the smaller of the two rounded
-  // sums (and likewise with - del); s2 and s3 are NaN together (both come from dd).  One
-  // minimum therefore serves both running minima.  Where del is infinite zmin may come out
-  // -inf instead of NaN: either way it is not >= 0, the only use made of it.
-  const float m = fminf(s2, s3);
-  lockw = fminf(lockw, __fadd_rn(m, del));
-  zmin = min_nan(zmin, __fsub_rn(m, del));
+  lockw = min3(lockw, __fadd_rn(s2, del), __fadd_rn(s3, del));
+  zmin = min3_nan(zmin, __fsub_rn(s2, del), __fsub_rn(s3, del));
   isgmax = fmaxf(isgmax, isg);
   const float hinv = __fmul_rn(0.5f, __fmul_rn(rd, rd));
   const float a = __fmul_rn(__fadd_rn(d2, r0.w), hinv), bq = __fmul_rn(__fmul_rn(D, rD), hinv);
