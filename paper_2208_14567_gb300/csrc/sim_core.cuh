@@ -12,7 +12,7 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kBatch = 16;  // work items taken per atomic by a warp (at most)
+constexpr int kBatch = 16;  // work items taken per atomic by a warp of the main screen
 constexpr int kEmitSlotBytes = 400;
 constexpr int kEmitSlotBytesDW = 656;
 constexpr int kEmitSharedDWMaxSlots = 12;
@@ -103,7 +103,7 @@ __device__ __forceinline__ void fp32_dyad(const DyadRec* __restrict__ rec, char*
 // consecutive steps (step chunk * G * S + u * G + lane-in-group, u < S), so that one
 // load of a dyad record serves S steps.  The slot arrays hold S columns per lane.
 // The work list is order[0, n) with n = *n_list, or p.order and the number of OK
-// mechanisms when n_list is null.
+// mechanisms when n_list is null; a warp takes `batch` (1 to 32) items of it per atomic.
 // With RESCUE a step that the FP32 bounds leave uncertain is recomputed at once in
 // double-word arithmetic by its lane (the others of the warp wait).  Without it, a
 // mechanism whose first uncertain step of a chunk comes before the chunk's first
