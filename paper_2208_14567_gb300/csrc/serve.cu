@@ -615,7 +615,7 @@ void worker_main(ServeState* s) {
       if (s->stop && s->pending.empty() && s->inflight.empty()) break;
       // Each pass owns one of kSlots count slots until it retires.  A request may open
       // a new pass (one per contiguous run of the ring), so it is admitted only while
-      // the passes in flight plus those of this round leave a slot for one more.
+      // the passes in flight plus those this admission step opens leave a slot for one more.
       int64_t run_end = -1;
       int runs = 0;
       // Continuous batching: at most kAhead passes wait for the kernel; requests that
